@@ -1,0 +1,395 @@
+#!/usr/bin/env python3
+"""Benchmark: block-CGrQ time to solution per right-hand side on one GB300.
+
+Workload (default): 32^4 lattice, m = 0.01, N = 16 complex128 Gaussian
+sources, FP64-form block-CGrQ (double-float iterations, native-FP64 reliable
+updates) to a true relative residual <= 1e-10, seeded synthetic links
+(fat exp(0.3 i H), long -1/24 exp(0.3 i H')).  One step = one complete solve
+(every stage of the hot path: stencil, Grams, small dense algebra, fused
+streaming update, reliable updates).  Inputs (links 4.8 GB, block fields
+~3.6 GB) are far larger than the 129 MB L2, so no flush is needed between
+steps.
+
+Also reported on the same line: the N independent CG baseline on the same
+sources (Sec. 7.1), the mixed-precision form, the Dslash GB/s sweep over N
+(Fig. 1 analogue), the roofline of the dominant kernel measured with CUDA
+events inside the timed solves, the end-to-end time through the public API
+with host buffers, and the CPU oracle timed on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU: launched by torchrun, one independent replica per GPU (the
+workload partitions into independent right-hand-side blocks; no collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "block-CG time-to-solution per RHS & Dslash HBM GB/s vs N independent CG, 1 GB300"
+UNIT = "ms/RHS"
+LINK_SEED = 1001
+SRC_SEED = 2100
+SM_COUNT = 152
+FP32_LANES = 128
+SM_MAX_MHZ = 2070.0
+DF_INSTR_PER_FLOP = 6.0   # 12 FP32 instructions per double-float multiply-add (2 flops)
+STENCIL_FLOPS = 1158      # per site per right-hand side (Sec. 5.2)
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dims", type=int, nargs=4, default=[32, 32, 32, 32])
+    ap.add_argument("--mass", type=float, default=0.01)
+    ap.add_argument("--nrhs", type=int, default=16)
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--prec", default="f64")
+    ap.add_argument("--no-extras", action="store_true", help="skip CG/mixed/sweep/CPU legs")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+def workload_name(a):
+    d = "x".join(str(x) for x in a.dims)
+    return f"{d} m={a.mass} N={a.nrhs} {a.prec} block-CGrQ to {a.tol:g}"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                    power.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        # samples under load: the upper half of the power readings
+        pmed = statistics.median(power)
+        loaded = [s for s, p in zip(sm, power) if p >= pmed] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------- CPU oracle
+def oracle_sample(dims, mass, fat, lng, b0, budget_s=12.0):
+    """Seconds per textbook-CG iteration of the C oracle on one right-hand side,
+    measured on a bounded number of iterations (the oracle as it stands)."""
+    from oracle import hisq
+    t = time.time()
+    hisq.cg_iterates(dims, fat, lng, mass, b0, 2)
+    per = max((time.time() - t) / 2, 1e-6)
+    k = max(2, int(budget_s / per))
+    t = time.time()
+    hisq.cg_iterates(dims, fat, lng, mass, b0, k)
+    return (time.time() - t) / k, k
+
+
+def golden_cg_iterations(a):
+    p = os.path.join(ROOT, "tests", "golden", "cg_iters_32x4.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if list(d["dims"]) != list(a.dims) or abs(d["mass"] - a.mass) > 0 or abs(d["tol"] - a.tol) > 0:
+        return None
+    return d["iterations_mean"]
+
+
+def cpu_inputs(a):
+    import hisq_inputs as hi
+    fat, lng = hi.random_links_torch(tuple(a.dims), LINK_SEED, "cpu")
+    b = hi.gaussian_sources(tuple(a.dims), a.nrhs, SRC_SEED)
+    return fat, lng, b
+
+
+def run_reference(a):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+    from oracle import build as obuild
+    obuild.build()
+    fat, lng, b = cpu_inputs(a)
+    fat, lng = fat.numpy(), lng.numpy()
+    iters = golden_cg_iterations(a)
+    if iters is None:
+        print(json.dumps({"impl": "reference", "unavailable":
+                          "no oracle CG iteration count stored for this workload"}))
+        return
+    from oracle import hisq
+    dims = tuple(a.dims)
+    per_step = []
+    for i in range(a.warmup + a.steps):
+        t = time.time()
+        k = 4
+        hisq.cg_iterates(dims, fat, lng, a.mass, b[0], k)
+        sec_per_it = (time.time() - t) / k
+        if i >= a.warmup:
+            per_step.append(sec_per_it)
+    sec = statistics.mean(per_step)
+    value = sec * iters * 1e3
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = (f"{k} oracle textbook-CG iterations per step on 1 of the {a.nrhs} sources, "
+              f"extrapolated to the oracle's {iters:.0f} iterations to {a.tol:g}")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": sec * 1e3 * k,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": workload_name(a)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# -------------------------------------------------------------------- ours
+def main():
+    a = parse_args()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    world, rank, local = dist_env()
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1710_09745_gb300 import BlockCG
+
+    dims = tuple(a.dims)
+    V = int(np.prod(dims))
+    Vh = V // 2
+    N = a.nrhs
+    fat_c, lng_c, b_np = cpu_inputs(a)
+    if world > 1:  # independent replica per rank: its own sources
+        import hisq_inputs as hi
+        b_np = hi.gaussian_sources(dims, N, SRC_SEED + 1000 * rank)
+    fat = fat_c.to(dev)
+    lng = lng_c.to(dev)
+    B = torch.as_tensor(b_np).to(dev)
+    s = BlockCG(dims, fat, lng, a.mass, prec=a.prec, max_rhs=max(N, 32), profile=True, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(a.warmup):
+        X, info = s.solve(B, tol=a.tol)
+    barrier()
+    clk = ClockSampler()
+    clk.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    infos = []
+    e0.record(stream)
+    for _ in range(a.steps):
+        X, info = s.solve(B, tol=a.tol)
+        infos.append(info)
+    e1.record(stream)
+    barrier()
+    clocks = clk.stop()
+    elapsed = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed = float(t.item())
+    ms_per_step = elapsed / a.steps
+    value = elapsed / (a.steps * N * world)
+    ok = all(i["status"] == 0 and i["true_rel_res_max"] <= a.tol for i in infos)
+
+    # dominant kernel: the iteration's stencil, timed with events inside the solves
+    n_st = sum(i["n_stencil"] for i in infos)
+    ms_st = sum(i["ms_stencil"] for i in infos)
+    ms_total = sum(i["ms_total"] for i in infos)
+    avg_launch_ms = ms_st / max(n_st, 1)
+    hbm_peak, peak_src = load_peaks()
+    bytes_per_real = {"f64": 8, "f64_native": 8, "mixed_f32": 4}[a.prec]
+    alg_bytes = (288 + 12 * N) * bytes_per_real * Vh
+    alg_flops = STENCIL_FLOPS * N * Vh
+    if a.prec == "f64":
+        peak = SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6 / DF_INSTR_PER_FLOP / 1e12
+        achieved = alg_flops / (avg_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "k_dslash<StoreDF> (double-float stencil)",
+                "peak_note": "FP32 issue rate 152 SM x 128 lanes x 2070 MHz / 6 instr per "
+                             "FP64-equivalent flop (double-float); derived, not measured",
+                "hbm_view": {"achieved_gbs": alg_bytes / (avg_launch_ms * 1e-3) / 1e9,
+                             "peak_gbs": hbm_peak,
+                             "frac": alg_bytes / (avg_launch_ms * 1e-3) / 1e9 / hbm_peak},
+                "share_of_solve": ms_st / ms_total if ms_total else None,
+                "launches": n_st, "avg_launch_ms": avg_launch_ms}
+    else:
+        achieved = alg_bytes / (avg_launch_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
+                "share_of_solve": ms_st / ms_total if ms_total else None,
+                "launches": n_st, "avg_launch_ms": avg_launch_ms}
+
+    # end to end through the public API with host buffers
+    B_host = torch.as_tensor(b_np).pin_memory()
+    X_host = torch.empty_like(B_host).pin_memory()
+    B_dev = torch.empty_like(B)
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    e2.record(stream)
+    for _ in range(a.steps):
+        B_dev.copy_(B_host, non_blocking=True)
+        Xd, _ = s.solve(B_dev, tol=a.tol)
+        X_host.copy_(Xd, non_blocking=True)
+    e3.record(stream)
+    barrier()
+    e2e_ms = e2.elapsed_time(e3)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    nbytes = B_host.numel() * B_host.element_size()
+    e2e = {"value": e2e_ms / (a.steps * N * world), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"f64": "f64(double-float)", "f64_native": "f64", "mixed_f32": "f32+f64"}[a.prec],
+        "data": "synthetic",
+        "config": {"workload": workload_name(a), "dims": list(dims), "mass": a.mass, "n_rhs": N,
+                   "tol": a.tol, "prec": a.prec, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (no flush)",
+                   "links": f"torch-cpu seed {LINK_SEED}", "sources": f"numpy seed {SRC_SEED}"},
+        "clocks": clocks, "e2e": e2e,
+        "gpu_launches": int(sum(i["launches"] for i in infos)),
+        "roofline": roof,
+        "solve": {"iters": infos[-1]["iters"], "reliable_updates": infos[-1]["reliable_updates"],
+                  "true_rel_res_max": infos[-1]["true_rel_res_max"], "converged": ok},
+    }
+
+    if rank == 0 and not a.no_extras:
+        # N independent CG solves on the same sources (Sec. 7.1 baseline)
+        _, ic = s.solve_cg(B, tol=a.tol)
+        out["cg_baseline"] = {"ms_per_rhs": ic["ms_total"] / N, "iters_per_rhs": ic["iters"] / N,
+                              "true_rel_res_max": ic["true_rel_res_max"],
+                              "block_speedup": (ic["ms_total"] / N) / value,
+                              "stencil_avg_launch_ms": ic["ms_stencil"] / max(ic["n_stencil"], 1)}
+        # mixed-precision form
+        sm = BlockCG(dims, fat, lng, a.mass, prec="mixed_f32", max_rhs=max(N, 32), profile=True,
+                     device=dev)
+        sm.solve(B, tol=a.tol)
+        _, im = sm.solve(B, tol=a.tol)
+        _, imc = sm.solve_cg(B[:4], tol=a.tol)
+        out["mixed"] = {"ms_per_rhs": im["ms_total"] / N, "iters": im["iters"],
+                        "reliable_updates": im["reliable_updates"],
+                        "true_rel_res_max": im["true_rel_res_max"],
+                        "cg_ms_per_rhs": imc["ms_total"] / 4, "cg_iters_per_rhs": imc["iters"] / 4,
+                        "block_speedup": (imc["ms_total"] / 4) / (im["ms_total"] / N)}
+        # Dslash GB/s per N (Fig. 1 analogue): FP32 (mixed) and double-float stencils
+        sweep = {}
+        for n in (1, 4, 8, 16, 32):
+            row = {}
+            for name, h, bpr in (("f32", sm, 4), ("df", s, 8)):
+                ms = h.bench_dslash(n, reps=10)
+                gbs = (288 + 12 * n) * bpr * Vh / (ms * 1e-3) / 1e9
+                row[name] = {"ms": ms, "gbs": gbs, "hbm_frac": gbs / hbm_peak,
+                             "gflops": STENCIL_FLOPS * n * Vh / (ms * 1e-3) / 1e9}
+            sweep[str(n)] = row
+        out["dslash"] = sweep
+        del sm
+        # CPU oracle on a bounded sample (rank 0, one GPU)
+        if world == 1:
+            os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+            from oracle import build as obuild
+            obuild.build()
+            sec_it, k = oracle_sample(dims, a.mass, fat_c.numpy(), lng_c.numpy(), b_np[0])
+            iters = ic["iters"] / N
+            cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+            out["cpu_baseline"] = {
+                "value": sec_it * iters * 1e3, "unit": UNIT, "cores": cores, "kind": "oracle",
+                "sample": f"{k} oracle textbook-CG iterations on 1 source of the workload "
+                          f"({sec_it * 1e3:.1f} ms each), extrapolated to {iters:.0f} iterations "
+                          f"(the GPU CG baseline's count to {a.tol:g})"}
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

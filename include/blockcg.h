@@ -1,0 +1,207 @@
+/*
+ * blockcg.h -- C ABI of libblockcg.so: block-CGrQ on one GPU for the even-odd
+ * improved-staggered (HISQ-type) normal operator.
+ *
+ * Method: Clark, Strelchenko, Vaquero, Wagner, Weinberg, "Pushing memory
+ * bandwidth limitations through efficient implementations of Block-Krylov
+ * space solvers on GPUs" (arXiv:1710.09745).  Operator: Eq. 1 and Sec. 2.2;
+ * solver: Algorithm 1 (blockCGrQ), Algorithm 2 (thin QR), Algorithm 3 (block
+ * reliable updates); kernels: Sec. 5.2 (block stencil), 5.3 (streaming
+ * multi-BLAS), 5.4 (reduction multi-BLAS).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  Lattice: dims = {Lx, Ly, Lz, Lt}, every extent even and >= 2.  V = Lx*Ly*Lz*Lt,
+ *  Vh = V/2.  Lexicographic site index i = x + Lx*(y + Ly*(z + Lz*t)); parity
+ *  (x+y+z+t) & 1; checkerboard index i >> 1.
+ *
+ *  Links: complex128 (interleaved re, im doubles) [4][V][3][3]: direction
+ *  mu = x,y,z,t, lexicographic site, 3x3 matrix row-major with the row index
+ *  the colour of the result.  F_mu(x) (fat) connects x to x+mu, G_mu(x) (long)
+ *  connects x to x+3mu and includes its coefficient (e.g. -1/24).  Staggered
+ *  phases eta_mu(x) = (-1)^(x_0+...+x_{mu-1}) are NOT in the links; the
+ *  library applies them.
+ *
+ *  Operator: (D psi)(x) = 1/2 sum_mu eta_mu(x) [ F_mu(x) psi(x+mu)
+ *      - F_mu(x-mu)^dag psi(x-mu) + G_mu(x) psi(x+3mu) - G_mu(x-3mu)^dag psi(x-3mu) ],
+ *  periodic (optionally antiperiodic in t), and A = m^2 - D_eo D_oe on even
+ *  sites, the Hermitian positive-definite Schur normal operator of
+ *  M = m + D (Eq. 1 with the anti-Hermitian sign on backward hops).
+ *
+ *  Spinor blocks (user layout): complex128 [n_rhs][Vh][3], one parity,
+ *  checkerboard-indexed; column j is right-hand side j.  1 <= n_rhs <= 64.
+ *
+ *  Memory: the library allocates no device memory.  All device buffers
+ *  (internal gauge copy, workspace, inputs, outputs) are owned by the caller;
+ *  pointers must stay valid while the handle uses them.  Every device pointer
+ *  must be 16-byte aligned.
+ *
+ *  Streams: all work is enqueued on the stream given to blockcg_create.
+ *  Calls return after enqueueing, except blockcg_solve / blockcg_solve_cg,
+ *  which synchronise that stream to read the convergence status and fill the
+ *  statistics.
+ *
+ *  Errors: every call returns a status; nothing is thrown across the ABI.
+ *  blockcg_last_error() gives a one-line description of the latest failure
+ *  on a handle.
+ */
+#ifndef BLOCKCG_H
+#define BLOCKCG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct blockcg_ctx* blockcg_t;
+
+typedef enum {
+  BLOCKCG_OK = 0,
+  BLOCKCG_ERR_ARG = 1,           /* bad argument (null pointer, bad size, odd dims, ...) */
+  BLOCKCG_ERR_CUDA = 2,          /* a CUDA call failed */
+  BLOCKCG_ERR_NOMEM = 3,         /* workspace or gauge storage too small / missing */
+  BLOCKCG_ERR_BREAKDOWN = 4,     /* Cholesky pivot <= 0 in a thin QR or in P^dag A P
+                                    (e.g. linearly dependent right-hand sides) */
+  BLOCKCG_ERR_NONFINITE = 5,     /* NaN or Inf met in a Gram matrix */
+  BLOCKCG_ERR_NOT_CONVERGED = 6, /* max_iter reached; X holds the current iterate */
+  BLOCKCG_ERR_TIMEOUT = 7        /* a bounded device-side wait gave up */
+} blockcg_status;
+
+/* Precision of the solve (Sec. 4 storage formats, Algorithm 3).  In every
+ * form the reliable updates of Algorithm 3 (solution accumulator Y, sources
+ * B, true residual R = B - A Y with its own stencil, thin QR of R) and all
+ * N x N algebra run in native FP64.
+ *  F64         FP64-accurate iterations: P, Q, AP, T, the update X and the
+ *              links stored as double-float pairs (two FP32 words per real,
+ *              ~48 significant bits) with error-free-transformation
+ *              double-float arithmetic on the FP32 pipes.
+ *  F64_NATIVE  native FP64 storage and arithmetic in the iterations too (slow
+ *              on GPUs with a reduced FP64 rate; for verification).
+ *  MIXED_F32   sloppy P, Q, AP, T and links in FP32 with FP32 arithmetic; X
+ *              in double-float.  */
+typedef enum {
+  BLOCKCG_PREC_F64 = 0,
+  BLOCKCG_PREC_F64_NATIVE = 1,
+  BLOCKCG_PREC_MIXED_F32 = 2
+} blockcg_prec;
+
+typedef struct {
+  int max_iter;        /* iteration limit (default 100000) */
+  double ru_delta;     /* reliable update when the max relative iterated residual
+                          fell by this factor since the last one (default 0.1;
+                          0 disables; Sec. 5 and 7.1) */
+  int ru_every;        /* >0: also a reliable update every ru_every iterations */
+  blockcg_prec prec;   /* default BLOCKCG_PREC_F64 */
+  int antiperiodic_t;  /* 1: antiperiodic boundary in t (default 0) */
+  int check_every;     /* host polls the device status every this many
+                          iterations (0: chosen from the lattice size) */
+  int profile;         /* 1: time every stencil launch of a solve with CUDA
+                          events (fills the ms_stencil fields of the stats) */
+} blockcg_params;
+
+typedef struct {
+  int iters;               /* iterations of Algorithm 1 (per RHS for solve_cg: the sum) */
+  int reliable_updates;    /* Algorithm 3 updates, including convergence checks */
+  double true_rel_res_max; /* max_i |b_i - A x_i| / |b_i| at exit (true residual) */
+  double ms_total;         /* device time of the solve (CUDA events) */
+  long long launches;      /* kernel launches the solve enqueued (gated ones included) */
+  long long n_stencil;     /* launches of the iteration's stencil (params.profile) */
+  double ms_stencil;       /* their summed device time (params.profile) */
+  long long n_stencil_fine;  /* launches of the full-precision stencil (params.profile) */
+  double ms_stencil_fine;    /* their summed device time (params.profile) */
+} blockcg_stats;
+
+/* Fill *p with the defaults listed above. */
+void blockcg_default_params(blockcg_params* p);
+
+/* Create a handle for an Lx x Ly x Lz x Lt lattice (Sec. 2.2), quark mass
+ * `mass` (finite), parameters p (NULL: defaults) and stream (cudaStream_t,
+ * NULL = legacy default stream).  Allocates host memory for the handle only.
+ * Errors: BLOCKCG_ERR_ARG for odd or < 2 extents, V/2 >= 2^31, non-finite
+ * mass, bad parameters. */
+blockcg_status blockcg_create(blockcg_t* out, const int dims[4], double mass,
+                              const blockcg_params* p, void* stream);
+
+/* Bytes of device memory the caller must provide to blockcg_load_gauge. */
+size_t blockcg_gauge_bytes(blockcg_t h);
+
+/* Reorder the caller's links (device complex128 [4][V][3][3] each, layout
+ * above) into `storage` (device, >= blockcg_gauge_bytes): per output parity
+ * the 16 hop matrices of Eq. 1 with staggered phases, the factor 1/2, the
+ * boundary sign and the backward-hop dagger and minus sign folded in, in
+ * the storage formats the precision needs.  The caller may free fat/lng once
+ * the stream has passed this call.  Errors: ERR_ARG (null), ERR_NOMEM
+ * (storage too small), ERR_CUDA. */
+blockcg_status blockcg_load_gauge(blockcg_t h, const void* fat, const void* lng, void* storage,
+                                  size_t storage_bytes);
+
+/* Bytes of device workspace needed by any call on this handle with up to
+ * n_rhs right-hand sides. */
+size_t blockcg_workspace_bytes(blockcg_t h, int n_rhs);
+
+/* Hand the handle a caller-owned device workspace (>= the size above for the
+ * largest n_rhs used).  Errors: ERR_ARG, ERR_NOMEM. */
+blockcg_status blockcg_set_workspace(blockcg_t h, void* ws, size_t bytes);
+
+/* out = D_{p,1-p} in: the block stencil of Sec. 5.2 (Eq. 1 hopping term),
+ * in on parity 1-out_parity, out on parity out_parity, both user layout
+ * [n_rhs][Vh][3] complex128 on the device, computed in the handle's
+ * precision.  Errors: ERR_ARG, ERR_NOMEM (no workspace/gauge), ERR_CUDA. */
+blockcg_status blockcg_dslash(blockcg_t h, const void* in, void* out, int n_rhs, int out_parity);
+
+/* out = A in = m^2 in - D_eo D_oe in on even sites (Sec. 2.2), user layout.
+ * in and out must not overlap.  Errors as blockcg_dslash. */
+blockcg_status blockcg_apply_MdagM(blockcg_t h, const void* in, void* out, int n_rhs);
+
+/* K = X^dag Y (block cDotProduct, Sec. 5.4): X, Y even-site blocks in user
+ * layout; K device complex128 [n_rhs][n_rhs] row-major (K[i][j] = X_i^dag Y_j). */
+blockcg_status blockcg_block_cdot(blockcg_t h, const void* X, const void* Y, int n_rhs, void* K);
+
+/* Y = Y + X a (block caxpy, Sec. 5.3): a device complex128 [n_rhs][n_rhs]
+ * row-major (a[i][j] multiplies column i of X into column j of Y). */
+blockcg_status blockcg_block_caxpy(blockcg_t h, const void* X, const void* a, void* Y, int n_rhs);
+
+/* Thin QR of Algorithm 2: H = M^dag M, R^dag R = H (Cholesky), Q = M R^-1.
+ * M, Q user layout (may alias); R device complex128 [n_rhs][n_rhs] row-major,
+ * upper triangular with real positive diagonal.  ERR_BREAKDOWN if H is not
+ * numerically positive definite. */
+blockcg_status blockcg_thin_qr(blockcg_t h, const void* M, void* Q, void* R, int n_rhs);
+
+/* Solve A X = B with blockCGrQ (Algorithm 1) and block reliable updates
+ * (Algorithm 3) until max_i |b_i - A x_i| / |b_i| <= tol, verified on the true
+ * residual.  B, X device, user layout; X holds the initial guess on entry and
+ * the solution on exit.  st may be NULL.  Synchronises the stream.
+ * Errors: ERR_ARG (tol <= 0, n_rhs out of range), ERR_NOMEM, ERR_BREAKDOWN,
+ * ERR_NONFINITE, ERR_NOT_CONVERGED (X = current iterate), ERR_CUDA. */
+blockcg_status blockcg_solve(blockcg_t h, const void* B, void* X, int n_rhs, double tol,
+                             blockcg_stats* st);
+
+/* Baseline of Sec. 7.1: n_rhs independent conjugate-gradient solves, one
+ * right-hand side after the other, on the same operator kernels at N = 1 and
+ * the same precision.  Arguments and errors as blockcg_solve; st->iters is
+ * the sum over right-hand sides. */
+blockcg_status blockcg_solve_cg(blockcg_t h, const void* B, void* X, int n_rhs, double tol,
+                                blockcg_stats* st);
+
+/* Time the block stencil of Sec. 5.2 alone (the measurement of Fig. 1):
+ * `reps` back-to-back launches of out_parity = D in on n_rhs right-hand sides
+ * in the iteration's precision (full precision if fine != 0), on internal
+ * workspace buffers (whose contents are overwritten), bracketed by CUDA
+ * events on the handle's stream.  *ms_per_launch receives the mean device
+ * time per launch.  Synchronises the stream.  Errors: ERR_ARG, ERR_NOMEM,
+ * ERR_CUDA. */
+blockcg_status blockcg_bench_dslash(blockcg_t h, int n_rhs, int fine, int reps,
+                                    double* ms_per_launch);
+
+/* Release the handle (host memory only; caller-owned device buffers stay). */
+void blockcg_destroy(blockcg_t h);
+
+const char* blockcg_status_string(blockcg_status s);
+const char* blockcg_last_error(blockcg_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BLOCKCG_H */

@@ -1,0 +1,259 @@
+"""ctypes binding of libblockcg.so (include/blockcg.h), same names as the C ABI.
+
+Argument marshalling only: device buffers (internal gauge copy, workspace,
+inputs, outputs) are PyTorch tensors on the GPU, the stream is PyTorch's
+current stream, and every operation runs in the library's kernels.
+Spinor blocks are complex128 tensors of shape (N, V/2, 3) on the device;
+links complex128 (4, V, 3, 3).
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libblockcg.so")
+
+PREC = {"f64": 0, "f64_native": 1, "mixed_f32": 2}
+
+STATUS = {
+    0: "BLOCKCG_OK", 1: "BLOCKCG_ERR_ARG", 2: "BLOCKCG_ERR_CUDA", 3: "BLOCKCG_ERR_NOMEM",
+    4: "BLOCKCG_ERR_BREAKDOWN", 5: "BLOCKCG_ERR_NONFINITE", 6: "BLOCKCG_ERR_NOT_CONVERGED",
+    7: "BLOCKCG_ERR_TIMEOUT",
+}
+
+# every symbol declared in include/blockcg.h
+ABI_SYMBOLS = [
+    "blockcg_default_params", "blockcg_create", "blockcg_gauge_bytes", "blockcg_load_gauge",
+    "blockcg_workspace_bytes", "blockcg_set_workspace", "blockcg_dslash", "blockcg_apply_MdagM",
+    "blockcg_block_cdot", "blockcg_block_caxpy", "blockcg_thin_qr", "blockcg_solve",
+    "blockcg_solve_cg", "blockcg_bench_dslash", "blockcg_destroy", "blockcg_status_string",
+    "blockcg_last_error",
+]
+
+
+class Params(ct.Structure):
+    _fields_ = [("max_iter", ct.c_int), ("ru_delta", ct.c_double), ("ru_every", ct.c_int),
+                ("prec", ct.c_int), ("antiperiodic_t", ct.c_int), ("check_every", ct.c_int),
+                ("profile", ct.c_int)]
+
+
+class Stats(ct.Structure):
+    _fields_ = [("iters", ct.c_int), ("reliable_updates", ct.c_int),
+                ("true_rel_res_max", ct.c_double), ("ms_total", ct.c_double),
+                ("launches", ct.c_longlong), ("n_stencil", ct.c_longlong),
+                ("ms_stencil", ct.c_double), ("n_stencil_fine", ct.c_longlong),
+                ("ms_stencil_fine", ct.c_double)]
+
+
+class BlockCGError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libblockcg.so and declare the ABI's signatures.  Raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1710_09745_gb300.build.build() "
+                           "(there is no CPU fallback)")
+    L = ct.CDLL(path)
+    P, I, D, S = ct.c_void_p, ct.c_int, ct.c_double, ct.c_size_t
+    sig = {
+        "blockcg_default_params": (None, [ct.POINTER(Params)]),
+        "blockcg_create": (I, [ct.POINTER(P), ct.POINTER(I), D, ct.POINTER(Params), P]),
+        "blockcg_gauge_bytes": (S, [P]),
+        "blockcg_load_gauge": (I, [P, P, P, P, S]),
+        "blockcg_workspace_bytes": (S, [P, I]),
+        "blockcg_set_workspace": (I, [P, P, S]),
+        "blockcg_dslash": (I, [P, P, P, I, I]),
+        "blockcg_apply_MdagM": (I, [P, P, P, I]),
+        "blockcg_block_cdot": (I, [P, P, P, I, P]),
+        "blockcg_block_caxpy": (I, [P, P, P, P, I]),
+        "blockcg_thin_qr": (I, [P, P, P, P, I]),
+        "blockcg_solve": (I, [P, P, P, I, D, ct.POINTER(Stats)]),
+        "blockcg_solve_cg": (I, [P, P, P, I, D, ct.POINTER(Stats)]),
+        "blockcg_bench_dslash": (I, [P, I, I, I, ct.POINTER(D)]),
+        "blockcg_destroy": (None, [P]),
+        "blockcg_status_string": (ct.c_char_p, [I]),
+        "blockcg_last_error": (ct.c_char_p, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class BlockCG:
+    """Handle on one lattice + gauge field + mass (blockcg_create/load_gauge).
+
+    prec: "f64" (double-float FP64-accurate form), "f64_native", "mixed_f32".
+    max_rhs: the largest block width the workspace is sized for.
+    """
+
+    def __init__(self, dims, fat, lng, mass: float, prec: str = "f64", max_rhs: int = 16,
+                 max_iter: int = 100000, ru_delta: float = 0.1, ru_every: int = 0,
+                 antiperiodic_t: bool = False, check_every: int = 0, profile: bool = False,
+                 device=None):
+        torch = _torch()
+        L = load_library()
+        self.lib = L
+        self.dims = tuple(int(d) for d in dims)
+        self.V = 1
+        for d in self.dims:
+            self.V *= d
+        self.Vh = self.V // 2
+        self.device = torch.device(device if device is not None else "cuda")
+        self.stream = torch.cuda.current_stream(self.device)
+        p = Params()
+        L.blockcg_default_params(ct.byref(p))
+        p.max_iter, p.ru_delta, p.ru_every = int(max_iter), float(ru_delta), int(ru_every)
+        p.prec, p.antiperiodic_t, p.check_every = PREC[prec], int(bool(antiperiodic_t)), int(check_every)
+        p.profile = int(bool(profile))
+        self.params = p
+        self.prec = prec
+        h = ct.c_void_p()
+        d4 = (ct.c_int * 4)(*self.dims)
+        self._check(L.blockcg_create(ct.byref(h), d4, float(mass), ct.byref(p),
+                                     ct.c_void_p(self.stream.cuda_stream)), None)
+        self.h = h
+        self.mass = float(mass)
+        fat = self._dev(fat, (4, self.V, 3, 3))
+        lng = self._dev(lng, (4, self.V, 3, 3))
+        nb = L.blockcg_gauge_bytes(h)
+        self.gauge = torch.empty(nb, dtype=torch.uint8, device=self.device)
+        self._check(L.blockcg_load_gauge(h, ct.c_void_p(fat.data_ptr()), ct.c_void_p(lng.data_ptr()),
+                                         ct.c_void_p(self.gauge.data_ptr()), nb))
+        self._links_keepalive = (fat, lng)
+        self.max_rhs = int(max_rhs)
+        wb = L.blockcg_workspace_bytes(h, self.max_rhs)
+        if wb == 0:
+            raise BlockCGError(1, "max_rhs out of range")
+        self.workspace = torch.empty(wb, dtype=torch.uint8, device=self.device)
+        self._check(L.blockcg_set_workspace(h, ct.c_void_p(self.workspace.data_ptr()), wb))
+
+    # ---------------------------------------------------------------- utils
+    def _check(self, rc, h="self"):
+        if rc != 0:
+            hh = self.h if h == "self" else None
+            msg = self.lib.blockcg_last_error(hh).decode() if hh else ""
+            raise BlockCGError(rc, msg)
+
+    def _dev(self, a, shape=None):
+        torch = _torch()
+        if not isinstance(a, torch.Tensor):
+            a = torch.as_tensor(a)
+        a = a.to(device=self.device, dtype=torch.complex128).contiguous()
+        if shape is not None and tuple(a.shape) != tuple(shape):
+            raise ValueError(f"expected shape {shape}, got {tuple(a.shape)}")
+        return a
+
+    def _block(self, a):
+        a = self._dev(a)
+        if a.dim() == 2:
+            a = a.unsqueeze(0)
+        if a.dim() != 3 or a.shape[1] != self.Vh or a.shape[2] != 3:
+            raise ValueError(f"expected a block of shape (N, {self.Vh}, 3), got {tuple(a.shape)}")
+        return a
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.stream.synchronize()
+            self.lib.blockcg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ operators
+    def dslash(self, psi, out_parity: int):
+        torch = _torch()
+        psi = self._block(psi)
+        out = torch.empty_like(psi)
+        self._check(self.lib.blockcg_dslash(self.h, ct.c_void_p(psi.data_ptr()),
+                                            ct.c_void_p(out.data_ptr()), psi.shape[0], int(out_parity)))
+        return out
+
+    def apply_MdagM(self, v):
+        torch = _torch()
+        v = self._block(v)
+        out = torch.empty_like(v)
+        self._check(self.lib.blockcg_apply_MdagM(self.h, ct.c_void_p(v.data_ptr()),
+                                                 ct.c_void_p(out.data_ptr()), v.shape[0]))
+        return out
+
+    def block_cdot(self, X, Y):
+        torch = _torch()
+        X, Y = self._block(X), self._block(Y)
+        n = X.shape[0]
+        K = torch.empty((n, n), dtype=torch.complex128, device=self.device)
+        self._check(self.lib.blockcg_block_cdot(self.h, ct.c_void_p(X.data_ptr()),
+                                                ct.c_void_p(Y.data_ptr()), n, ct.c_void_p(K.data_ptr())))
+        return K
+
+    def block_caxpy(self, X, a, Y):
+        """Returns Y + X a (a new tensor; the input Y is not modified)."""
+        X = self._block(X)
+        Y = self._block(Y).clone()
+        n = X.shape[0]
+        a = self._dev(a, (n, n))
+        self._check(self.lib.blockcg_block_caxpy(self.h, ct.c_void_p(X.data_ptr()),
+                                                 ct.c_void_p(a.data_ptr()), ct.c_void_p(Y.data_ptr()), n))
+        return Y
+
+    def thin_qr(self, M):
+        torch = _torch()
+        M = self._block(M)
+        n = M.shape[0]
+        Q = torch.empty_like(M)
+        R = torch.empty((n, n), dtype=torch.complex128, device=self.device)
+        self._check(self.lib.blockcg_thin_qr(self.h, ct.c_void_p(M.data_ptr()), ct.c_void_p(Q.data_ptr()),
+                                             ct.c_void_p(R.data_ptr()), n))
+        return Q, R
+
+    # -------------------------------------------------------------- solvers
+    def _solve(self, fn, B, X0, tol):
+        torch = _torch()
+        B = self._block(B)
+        X = torch.zeros_like(B) if X0 is None else self._block(X0).clone()
+        st = Stats()
+        rc = fn(self.h, ct.c_void_p(B.data_ptr()), ct.c_void_p(X.data_ptr()), B.shape[0], float(tol),
+                ct.byref(st))
+        info = {"iters": st.iters, "reliable_updates": st.reliable_updates,
+                "true_rel_res_max": st.true_rel_res_max, "ms_total": st.ms_total, "status": rc,
+                "launches": st.launches, "n_stencil": st.n_stencil, "ms_stencil": st.ms_stencil,
+                "n_stencil_fine": st.n_stencil_fine, "ms_stencil_fine": st.ms_stencil_fine}
+        if rc not in (0, 6):
+            self._check(rc)
+        return X, info
+
+    def solve(self, B, X0=None, tol: float = 1e-10):
+        """blockCGrQ (Algorithm 1 with reliable updates); returns (X, info)."""
+        return self._solve(self.lib.blockcg_solve, B, X0, tol)
+
+    def solve_cg(self, B, X0=None, tol: float = 1e-10):
+        """N sequential CG solves (baseline); returns (X, info)."""
+        return self._solve(self.lib.blockcg_solve_cg, B, X0, tol)
+
+    def bench_dslash(self, n_rhs: int, reps: int = 20, fine: bool = False) -> float:
+        """Mean device time (ms) of one block-stencil launch on n_rhs columns."""
+        ms = ct.c_double()
+        self._check(self.lib.blockcg_bench_dslash(self.h, int(n_rhs), int(bool(fine)), int(reps),
+                                                  ct.byref(ms)))
+        return ms.value

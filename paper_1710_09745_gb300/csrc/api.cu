@@ -1,0 +1,710 @@
+// C ABI of libblockcg.so and the host-side solver drivers.
+//
+// blockCGrQ (Algorithm 1) runs as a fixed sequence of kernel launches per
+// iteration, all on the caller's stream and all gated by a device status
+// word, so the host enqueues `check_every` iterations at a time and reads the
+// status only between such chunks:
+//
+//   T  = D_oe P                        stencil            (Sec. 5.2)
+//   AP = m^2 P - D_eo T                stencil + epilogue (Sec. 2.2)
+//   H  = P^dag AP                      Gram               (Sec. 5.4)
+//   beta = H^-1, BC = beta C           dense              (Algorithm 1)
+//   W  = Q - AP beta                   streaming          (Sec. 5.3)
+//   W^dag W = S^dag S, C = S C, res    Gram + dense       (Algorithm 2)
+//   Q = W S^-1, X += P BC, P = Q + P S^dag       one fused streaming pass
+//   [reliable update, gated]           Algorithm 3:
+//      Y += X, X = 0; R = B - A Y; R = Q C (thin QR); S = C C_old^-1;
+//      P = Q + P S^dag
+//
+// The reliable update also serves as the convergence test: when the
+// iterated residual meets tol, the true residual of Y decides.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/blockcg.h"
+#include "internal.h"
+
+using namespace bcg;
+
+struct blockcg_ctx {
+  Geom g;
+  int dims[4];
+  double mass;
+  blockcg_params p;
+  cudaStream_t stream;
+  FieldKind fine;    // Y, B, R and the true-residual operator: native FP64
+  FieldKind sloppy;  // P, Q, AP, T and the iteration's operator
+  FieldKind upd;     // X, the iterated solution update between reliable updates
+  void* gauge;
+  size_t gauge_bytes;
+  void* links_fine;
+  void* links_sloppy;
+  bool gauge_loaded;
+  char* ws;
+  size_t ws_bytes;
+  std::string err;
+  // instrumentation of the current solve
+  long long launches;
+  struct Timed {
+    cudaEvent_t a, b;
+    int fine;
+  };
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<Timed> ev_pending;
+  long long n_st[2];
+  double ms_st[2];
+};
+
+namespace {
+
+const size_t ALIGN = 256;
+inline size_t up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
+
+enum MatId { M_H = 0, M_G, M_C, M_CPREV, M_BETA, M_BC, M_SINV, M_SH, M_CINV, M_SHRU, M_K, M_RINV, M_COUNT };
+
+struct Ws {
+  // fine-kind fields
+  void *B, *Y, *R, *Tf;
+  // update-kind field
+  void* X;
+  // sloppy-kind fields
+  void *Q, *P, *AP, *Ts;
+  double2* partials;
+  double2* mats;
+  double* bnorm;
+  SolverStatus* st;
+  double* scal;  // rr, alpha, beta, zero
+  int* ierr;
+  int nblocks;
+  size_t total;
+};
+
+Ws carve(const blockcg_ctx* h, int N, char* base) {
+  Ws w;
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char* {
+    char* p = base ? base + off : nullptr;
+    off += up(bytes);
+    return p;
+  };
+  size_t nel = (size_t)h->g.Vh * N * 3;
+  size_t fb = nel * elem_bytes(h->fine), sb = nel * elem_bytes(h->sloppy);
+  w.B = take(fb);
+  w.Y = take(fb);
+  w.X = take(nel * elem_bytes(h->upd));
+  w.R = take(fb);
+  w.Tf = take(fb);
+  w.Q = take(sb);
+  w.P = take(sb);
+  w.AP = take(sb);
+  w.Ts = (h->sloppy == h->fine) ? w.Tf : take(sb);
+  w.nblocks = gram_blocks(N, 3 * h->g.Vh);
+  int nb_cg = 2 * 152;
+  size_t np = (size_t)(w.nblocks > nb_cg ? w.nblocks : nb_cg) * N * N;
+  w.partials = (double2*)take(np * sizeof(double2));
+  w.mats = (double2*)take((size_t)M_COUNT * N * N * sizeof(double2));
+  w.bnorm = (double*)take(N * sizeof(double));
+  w.st = (SolverStatus*)take(sizeof(SolverStatus));
+  w.scal = (double*)take(8 * sizeof(double));
+  w.ierr = (int*)take(sizeof(int));
+  w.total = off;
+  return w;
+}
+
+inline double2* mat(const Ws& w, int id, int N) { return w.mats + (size_t)id * N * N; }
+
+blockcg_status fail(blockcg_ctx* h, blockcg_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  return s;
+}
+
+blockcg_status cuda_fail(blockcg_ctx* h, cudaError_t e, const char* where) {
+  return fail(h, BLOCKCG_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                       \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+  } while (0)
+
+// a kernel launch: checked and counted
+#define KL(call)     \
+  do {               \
+    ++h->launches;   \
+    CK(call);        \
+  } while (0)
+
+cudaEvent_t pool_event(blockcg_ctx* h) {
+  if (!h->ev_pool.empty()) {
+    cudaEvent_t e = h->ev_pool.back();
+    h->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// a stencil launch, event-timed when params.profile is set
+#define SL(fine_, call)                                       \
+  do {                                                        \
+    if (h->p.profile) {                                       \
+      blockcg_ctx::Timed t_{pool_event(h), pool_event(h), (fine_)}; \
+      CK(cudaEventRecord(t_.a, h->stream));                   \
+      KL(call);                                               \
+      CK(cudaEventRecord(t_.b, h->stream));                   \
+      h->ev_pending.push_back(t_);                            \
+    } else {                                                  \
+      KL(call);                                               \
+    }                                                         \
+  } while (0)
+
+// after a synchronisation: fold the finished stencil timings into the totals
+void drain_events(blockcg_ctx* h) {
+  for (auto& t : h->ev_pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+      h->n_st[t.fine] += 1;
+      h->ms_st[t.fine] += ms;
+    }
+    h->ev_pool.push_back(t.a);
+    h->ev_pool.push_back(t.b);
+  }
+  h->ev_pending.clear();
+}
+
+void reset_instrumentation(blockcg_ctx* h) {
+  h->launches = 0;
+  h->n_st[0] = h->n_st[1] = 0;
+  h->ms_st[0] = h->ms_st[1] = 0.0;
+  h->ev_pending.clear();
+}
+
+int tile_R(int N) { return N >= 8 ? 4 : (N >= 2 ? 2 : 1); }
+
+blockcg_status check_ready(blockcg_ctx* h, int N) {
+  if (!h) return BLOCKCG_ERR_ARG;
+  if (N < 1 || N > 64) return fail(h, BLOCKCG_ERR_ARG, "n_rhs must be in [1, 64]");
+  if (!h->gauge_loaded) return fail(h, BLOCKCG_ERR_NOMEM, "gauge field not loaded");
+  if (!h->ws) return fail(h, BLOCKCG_ERR_NOMEM, "no workspace set");
+  if (carve(h, N, nullptr).total > h->ws_bytes)
+    return fail(h, BLOCKCG_ERR_NOMEM, "workspace too small for n_rhs");
+  return BLOCKCG_OK;
+}
+
+FieldKind op_kind(const blockcg_ctx* h) { return h->sloppy; }
+const void* op_links(const blockcg_ctx* h) { return h->links_sloppy; }
+
+// A applied to an internal even-site block: out = m^2 in - D_eo D_oe in
+blockcg_status apply_A_internal(blockcg_ctx* h, FieldKind k, const void* links, const void* in,
+                                void* tmp_odd, void* out, int N, Gate gate) {
+  int R = tile_R(N);
+  double m2 = h->mass * h->mass;
+  KL(dslash(k, R, EPI_NONE, links, in, tmp_odd, nullptr, nullptr, 0.0, h->g, 1, N, gate, h->stream));
+  KL(dslash(k, R, EPI_NORMAL, links, tmp_odd, out, in, nullptr, m2, h->g, 0, N, gate, h->stream));
+  return BLOCKCG_OK;
+}
+
+blockcg_status read_status(blockcg_ctx* h, const Ws& w, SolverStatus* out) {
+  CK(cudaMemcpyAsync(out, w.st, sizeof(SolverStatus), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  drain_events(h);
+  return BLOCKCG_OK;
+}
+
+int default_check_every(const blockcg_ctx* h, int N) {
+  if (h->p.check_every > 0) return h->p.check_every;
+  double work = (double)h->g.Vh * N;
+  int c = (int)(4.0e6 / work);
+  if (c < 1) c = 1;
+  if (c > 32) c = 32;
+  return c;
+}
+
+// R = B - A Y, thin QR, restart of Q and P (Algorithm 3; init: Algorithm 1 set-up)
+blockcg_status restart_block(blockcg_ctx* h, const Ws& w, int N, double tol, int init, Gate gate) {
+  int R = tile_R(N);
+  double m2 = h->mass * h->mass;
+  size_t nel = (size_t)h->g.Vh * N * 3;
+  cudaStream_t s = h->stream;
+  KL(accumulate(h->fine, h->upd, w.Y, w.X, nel, gate, s));
+  SL(1, dslash(h->fine, R, EPI_NONE, h->links_fine, w.Y, w.Tf, nullptr, nullptr, 0.0, h->g, 1, N, gate, s));
+  SL(1, dslash(h->fine, R, EPI_RESIDUAL, h->links_fine, w.Tf, w.R, w.Y, w.B, m2, h->g, 0, N, gate, s));
+  KL(gram_partials(h->fine, w.R, w.R, N, h->g.Vh, 1, w.partials, w.nblocks, gate, s));
+  KL(gram_reduce(w.partials, w.nblocks, N, 1, mat(w, M_G, N), gate, s));
+  KL(dense_restart(mat(w, M_G, N), mat(w, M_C, N), mat(w, M_CPREV, N), mat(w, M_CINV, N),
+                   mat(w, M_SHRU, N), w.bnorm, tol, init, N, w.st, gate, s));
+  KL(restart_update(h->fine, h->sloppy, w.R, w.Q, w.P, mat(w, M_CINV, N), mat(w, M_SHRU, N), init,
+                    N, h->g.Vh, gate, s));
+  return BLOCKCG_OK;
+}
+
+blockcg_status iterate_block(blockcg_ctx* h, const Ws& w, int N, double tol) {
+  Gate ga{w.st, GATE_ACTIVE};
+  Gate gr{w.st, GATE_RU};
+  int R = tile_R(N);
+  double m2 = h->mass * h->mass;
+  cudaStream_t s = h->stream;
+  FieldKind k = h->sloppy;
+  SL(0, dslash(k, R, EPI_NONE, h->links_sloppy, w.P, w.Ts, nullptr, nullptr, 0.0, h->g, 1, N, ga, s));
+  SL(0, dslash(k, R, EPI_NORMAL, h->links_sloppy, w.Ts, w.AP, w.P, nullptr, m2, h->g, 0, N, ga, s));
+  KL(gram_partials(k, w.P, w.AP, N, h->g.Vh, 1, w.partials, w.nblocks, ga, s));
+  KL(gram_reduce(w.partials, w.nblocks, N, 1, mat(w, M_H, N), ga, s));
+  KL(dense_beta(mat(w, M_H, N), mat(w, M_C, N), mat(w, M_BETA, N), mat(w, M_BC, N), N, w.st, ga, s));
+  KL(w_update(k, w.Q, w.AP, mat(w, M_BETA, N), N, h->g.Vh, ga, s));
+  KL(gram_partials(k, w.Q, w.Q, N, h->g.Vh, 1, w.partials, w.nblocks, ga, s));
+  KL(gram_reduce(w.partials, w.nblocks, N, 1, mat(w, M_G, N), ga, s));
+  QrStepParams qp{tol, h->p.ru_delta, h->p.ru_every, h->p.max_iter};
+  KL(dense_qr_step(mat(w, M_G, N), mat(w, M_C, N), mat(w, M_CPREV, N), mat(w, M_SINV, N),
+                   mat(w, M_SH, N), w.bnorm, qp, N, w.st, ga, s));
+  KL(bcg_update(k, h->upd, w.Q, w.P, w.X, mat(w, M_SINV, N), mat(w, M_BC, N), mat(w, M_SH, N), N,
+                h->g.Vh, ga, s));
+  return restart_block(h, w, N, tol, 0, gr);
+}
+
+blockcg_status status_to_result(blockcg_ctx* h, const SolverStatus& st) {
+  if (st.error) {
+    const char* what = blockcg_status_string((blockcg_status)st.error);
+    return fail(h, (blockcg_status)st.error, std::string("device reported: ") + what);
+  }
+  return BLOCKCG_OK;
+}
+
+}  // namespace
+
+// ===================================================================== ABI
+
+extern "C" {
+
+void blockcg_default_params(blockcg_params* p) {
+  if (!p) return;
+  p->max_iter = 100000;
+  p->ru_delta = 0.1;
+  p->ru_every = 0;
+  p->prec = BLOCKCG_PREC_F64;
+  p->antiperiodic_t = 0;
+  p->check_every = 0;
+}
+
+const char* blockcg_status_string(blockcg_status s) {
+  switch (s) {
+    case BLOCKCG_OK: return "ok";
+    case BLOCKCG_ERR_ARG: return "invalid argument";
+    case BLOCKCG_ERR_CUDA: return "CUDA error";
+    case BLOCKCG_ERR_NOMEM: return "insufficient or missing device buffer";
+    case BLOCKCG_ERR_BREAKDOWN: return "Cholesky breakdown (rank-deficient block)";
+    case BLOCKCG_ERR_NONFINITE: return "non-finite value in a Gram matrix";
+    case BLOCKCG_ERR_NOT_CONVERGED: return "not converged within max_iter";
+    case BLOCKCG_ERR_TIMEOUT: return "device wait timed out";
+  }
+  return "unknown status";
+}
+
+const char* blockcg_last_error(blockcg_t h) { return h ? h->err.c_str() : "null handle"; }
+
+blockcg_status blockcg_create(blockcg_t* out, const int dims[4], double mass,
+                              const blockcg_params* p, void* stream) {
+  if (!out || !dims) return BLOCKCG_ERR_ARG;
+  *out = nullptr;
+  long long V = 1;
+  for (int mu = 0; mu < 4; ++mu) {
+    if (dims[mu] < 2 || (dims[mu] & 1)) return BLOCKCG_ERR_ARG;
+    V *= dims[mu];
+  }
+  if (V / 2 >= (1LL << 31) / 64) return BLOCKCG_ERR_ARG;
+  if (!std::isfinite(mass)) return BLOCKCG_ERR_ARG;
+  blockcg_params prm;
+  blockcg_default_params(&prm);
+  if (p) prm = *p;
+  if (prm.max_iter < 1 || prm.ru_delta < 0 || !(prm.ru_delta < 1) || prm.ru_every < 0 ||
+      prm.check_every < 0 || (int)prm.prec < 0 || (int)prm.prec > 2)
+    return BLOCKCG_ERR_ARG;
+  blockcg_ctx* h = new blockcg_ctx();
+  for (int mu = 0; mu < 4; ++mu) {
+    h->dims[mu] = dims[mu];
+    h->g.L[mu] = dims[mu];
+  }
+  h->g.hx = dims[0] / 2;
+  h->g.Vh = (int)(V / 2);
+  h->mass = mass;
+  h->p = prm;
+  h->stream = (cudaStream_t)stream;
+  h->fine = FK_F64;
+  switch (prm.prec) {
+    case BLOCKCG_PREC_F64: h->sloppy = FK_DF; h->upd = FK_DF; break;
+    case BLOCKCG_PREC_F64_NATIVE: h->sloppy = FK_F64; h->upd = FK_F64; break;
+    case BLOCKCG_PREC_MIXED_F32: h->sloppy = FK_F32; h->upd = FK_DF; break;
+  }
+  h->gauge = nullptr;
+  h->gauge_bytes = 0;
+  h->links_fine = h->links_sloppy = nullptr;
+  h->gauge_loaded = false;
+  h->ws = nullptr;
+  h->ws_bytes = 0;
+  reset_instrumentation(h);
+  *out = h;
+  return BLOCKCG_OK;
+}
+
+void blockcg_destroy(blockcg_t h) {
+  if (!h) return;
+  for (auto& t : h->ev_pending) {
+    h->ev_pool.push_back(t.a);
+    h->ev_pool.push_back(t.b);
+  }
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  delete h;
+}
+
+size_t blockcg_gauge_bytes(blockcg_t h) {
+  if (!h) return 0;
+  size_t b = up(links_bytes(h->fine, h->g));
+  if (h->sloppy != h->fine) b += up(links_bytes(h->sloppy, h->g));
+  return b;
+}
+
+blockcg_status blockcg_load_gauge(blockcg_t h, const void* fat, const void* lng, void* storage,
+                                  size_t storage_bytes) {
+  if (!h) return BLOCKCG_ERR_ARG;
+  if (!fat || !lng || !storage) return fail(h, BLOCKCG_ERR_ARG, "null pointer");
+  if (storage_bytes < blockcg_gauge_bytes(h)) return fail(h, BLOCKCG_ERR_NOMEM, "gauge storage too small");
+  h->gauge = storage;
+  h->gauge_bytes = storage_bytes;
+  h->links_fine = storage;
+  h->links_sloppy = (h->sloppy != h->fine) ? (char*)storage + up(links_bytes(h->fine, h->g)) : storage;
+  CK(pack_links(h->fine, (const double2*)fat, (const double2*)lng, h->links_fine, h->g,
+                h->p.antiperiodic_t, h->stream));
+  if (h->sloppy != h->fine)
+    CK(pack_links(h->sloppy, (const double2*)fat, (const double2*)lng, h->links_sloppy, h->g,
+                  h->p.antiperiodic_t, h->stream));
+  h->gauge_loaded = true;
+  return BLOCKCG_OK;
+}
+
+size_t blockcg_workspace_bytes(blockcg_t h, int n_rhs) {
+  if (!h || n_rhs < 1 || n_rhs > 64) return 0;
+  return carve(h, n_rhs, nullptr).total;
+}
+
+blockcg_status blockcg_set_workspace(blockcg_t h, void* ws, size_t bytes) {
+  if (!h) return BLOCKCG_ERR_ARG;
+  if (!ws || bytes < blockcg_workspace_bytes(h, 1)) return fail(h, BLOCKCG_ERR_NOMEM, "workspace too small");
+  if (((uintptr_t)ws) % 16) return fail(h, BLOCKCG_ERR_ARG, "workspace not 16-byte aligned");
+  h->ws = (char*)ws;
+  h->ws_bytes = bytes;
+  return BLOCKCG_OK;
+}
+
+blockcg_status blockcg_dslash(blockcg_t h, const void* in, void* out, int n_rhs, int out_parity) {
+  blockcg_status rc = check_ready(h, n_rhs);
+  if (rc) return rc;
+  if (!in || !out || (out_parity & ~1)) return fail(h, BLOCKCG_ERR_ARG, "bad argument");
+  Ws w = carve(h, n_rhs, h->ws);
+  FieldKind k = op_kind(h);
+  Gate g0{nullptr, GATE_ALWAYS};
+  CK(to_internal(k, (const double2*)in, w.Q, n_rhs, h->g.Vh, h->stream));
+  CK(dslash(k, tile_R(n_rhs), EPI_NONE, op_links(h), w.Q, w.AP, nullptr, nullptr, 0.0, h->g,
+            out_parity, n_rhs, g0, h->stream));
+  CK(from_internal(k, w.AP, (double2*)out, n_rhs, h->g.Vh, h->stream));
+  return BLOCKCG_OK;
+}
+
+blockcg_status blockcg_apply_MdagM(blockcg_t h, const void* in, void* out, int n_rhs) {
+  blockcg_status rc = check_ready(h, n_rhs);
+  if (rc) return rc;
+  if (!in || !out) return fail(h, BLOCKCG_ERR_ARG, "null pointer");
+  Ws w = carve(h, n_rhs, h->ws);
+  FieldKind k = op_kind(h);
+  Gate g0{nullptr, GATE_ALWAYS};
+  CK(to_internal(k, (const double2*)in, w.P, n_rhs, h->g.Vh, h->stream));
+  rc = apply_A_internal(h, k, op_links(h), w.P, w.Ts, w.AP, n_rhs, g0);
+  if (rc) return rc;
+  CK(from_internal(k, w.AP, (double2*)out, n_rhs, h->g.Vh, h->stream));
+  return BLOCKCG_OK;
+}
+
+blockcg_status blockcg_block_cdot(blockcg_t h, const void* X, const void* Y, int n_rhs, void* K) {
+  blockcg_status rc = check_ready(h, n_rhs);
+  if (rc) return rc;
+  if (!X || !Y || !K) return fail(h, BLOCKCG_ERR_ARG, "null pointer");
+  Ws w = carve(h, n_rhs, h->ws);
+  FieldKind k = op_kind(h);
+  Gate g0{nullptr, GATE_ALWAYS};
+  CK(to_internal(k, (const double2*)X, w.Q, n_rhs, h->g.Vh, h->stream));
+  CK(to_internal(k, (const double2*)Y, w.P, n_rhs, h->g.Vh, h->stream));
+  CK(gram_partials(k, w.Q, w.P, n_rhs, h->g.Vh, 0, w.partials, w.nblocks, g0, h->stream));
+  CK(gram_reduce(w.partials, w.nblocks, n_rhs, 0, (double2*)K, g0, h->stream));
+  return BLOCKCG_OK;
+}
+
+blockcg_status blockcg_block_caxpy(blockcg_t h, const void* X, const void* a, void* Y, int n_rhs) {
+  blockcg_status rc = check_ready(h, n_rhs);
+  if (rc) return rc;
+  if (!X || !a || !Y) return fail(h, BLOCKCG_ERR_ARG, "null pointer");
+  Ws w = carve(h, n_rhs, h->ws);
+  FieldKind k = op_kind(h);
+  CK(to_internal(k, (const double2*)X, w.Q, n_rhs, h->g.Vh, h->stream));
+  CK(to_internal(k, (const double2*)Y, w.P, n_rhs, h->g.Vh, h->stream));
+  CK(block_caxpy(k, w.Q, (const double2*)a, w.P, n_rhs, h->g.Vh, h->stream));
+  CK(from_internal(k, w.P, (double2*)Y, n_rhs, h->g.Vh, h->stream));
+  return BLOCKCG_OK;
+}
+
+blockcg_status blockcg_thin_qr(blockcg_t h, const void* M, void* Q, void* R, int n_rhs) {
+  blockcg_status rc = check_ready(h, n_rhs);
+  if (rc) return rc;
+  if (!M || !Q || !R) return fail(h, BLOCKCG_ERR_ARG, "null pointer");
+  Ws w = carve(h, n_rhs, h->ws);
+  FieldKind k = op_kind(h);
+  Gate g0{nullptr, GATE_ALWAYS};
+  int N = n_rhs;
+  CK(to_internal(k, (const double2*)M, w.Q, N, h->g.Vh, h->stream));
+  CK(gram_partials(k, w.Q, w.Q, N, h->g.Vh, 1, w.partials, w.nblocks, g0, h->stream));
+  CK(gram_reduce(w.partials, w.nblocks, N, 1, mat(w, M_H, N), g0, h->stream));
+  CK(dense_chol_upper(mat(w, M_H, N), (double2*)R, mat(w, M_RINV, N), N, w.ierr, h->stream));
+  CK(block_trmul(k, w.Q, mat(w, M_RINV, N), w.P, N, h->g.Vh, h->stream));
+  CK(from_internal(k, w.P, (double2*)Q, N, h->g.Vh, h->stream));
+  int err = 0;
+  CK(cudaMemcpyAsync(&err, w.ierr, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (err) return fail(h, (blockcg_status)err, "thin QR: Cholesky failed");
+  return BLOCKCG_OK;
+}
+
+blockcg_status blockcg_solve(blockcg_t h, const void* B, void* X, int n_rhs, double tol,
+                             blockcg_stats* stats) {
+  blockcg_status rc = check_ready(h, n_rhs);
+  if (rc) return rc;
+  if (!B || !X) return fail(h, BLOCKCG_ERR_ARG, "null pointer");
+  if (!(tol > 0) || !std::isfinite(tol)) return fail(h, BLOCKCG_ERR_ARG, "tol must be > 0");
+  const int N = n_rhs;
+  Ws w = carve(h, N, h->ws);
+  cudaStream_t s = h->stream;
+  size_t nel = (size_t)h->g.Vh * N * 3;
+  Gate g0{nullptr, GATE_ALWAYS};
+  Gate ga{w.st, GATE_ACTIVE};
+  reset_instrumentation(h);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, s));
+  CK(cudaMemsetAsync(w.st, 0, sizeof(SolverStatus), s));
+  KL(to_internal(h->fine, (const double2*)B, w.B, N, h->g.Vh, s));
+  KL(to_internal(h->fine, (const double2*)X, w.Y, N, h->g.Vh, s));
+  CK(zero_field(h->upd, w.X, nel, s));
+  CK(zero_field(h->sloppy, w.P, nel, s));
+  KL(gram_partials(h->fine, w.B, w.B, N, h->g.Vh, 1, w.partials, w.nblocks, g0, s));
+  KL(gram_reduce(w.partials, w.nblocks, N, 1, mat(w, M_G, N), g0, s));
+  KL(dense_bnorm(mat(w, M_G, N), w.bnorm, N, w.st, s));
+  rc = restart_block(h, w, N, tol, 1, ga);
+  if (rc) return rc;
+  const int chunk = default_check_every(h, N);
+  SolverStatus hs;
+  memset(&hs, 0, sizeof(hs));
+  int launched = 0;
+  for (;;) {
+    rc = read_status(h, w, &hs);
+    if (rc) return rc;
+    if (hs.done || hs.error || hs.iters >= h->p.max_iter) break;
+    int n = chunk;
+    if (launched + n > h->p.max_iter) n = h->p.max_iter - launched;
+    if (n <= 0) n = 1;
+    for (int i = 0; i < n; ++i) {
+      rc = iterate_block(h, w, N, tol);
+      if (rc) return rc;
+    }
+    launched += n;
+  }
+  blockcg_status result = status_to_result(h, hs);
+  if (!result && !hs.done) {
+    // max_iter reached: fold the last update into Y and report the true residual
+    rc = restart_block(h, w, N, tol, 1, g0);
+    if (rc) return rc;
+    rc = read_status(h, w, &hs);
+    if (rc) return rc;
+    result = hs.done ? BLOCKCG_OK : fail(h, BLOCKCG_ERR_NOT_CONVERGED, "max_iter reached");
+  }
+  KL(from_internal(h->fine, w.Y, (double2*)X, N, h->g.Vh, s));
+  CK(cudaEventRecord(e1, s));
+  CK(cudaEventSynchronize(e1));
+  drain_events(h);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (stats) {
+    stats->iters = hs.iters;
+    stats->reliable_updates = hs.reliable_updates;
+    stats->true_rel_res_max = hs.true_res_max;
+    stats->ms_total = ms;
+    stats->launches = h->launches;
+    stats->n_stencil = h->n_st[0];
+    stats->ms_stencil = h->ms_st[0];
+    stats->n_stencil_fine = h->n_st[1];
+    stats->ms_stencil_fine = h->ms_st[1];
+  }
+  return result;
+}
+
+blockcg_status blockcg_solve_cg(blockcg_t h, const void* B, void* X, int n_rhs, double tol,
+                                blockcg_stats* stats) {
+  blockcg_status rc = check_ready(h, 1);
+  if (rc) return rc;
+  if (n_rhs < 1 || n_rhs > 64) return fail(h, BLOCKCG_ERR_ARG, "n_rhs must be in [1, 64]");
+  if (!B || !X) return fail(h, BLOCKCG_ERR_ARG, "null pointer");
+  if (!(tol > 0) || !std::isfinite(tol)) return fail(h, BLOCKCG_ERR_ARG, "tol must be > 0");
+  Ws w = carve(h, 1, h->ws);
+  cudaStream_t s = h->stream;
+  const int Vh = h->g.Vh;
+  const FieldKind fk = h->fine, sk = h->sloppy, xk = h->upd;
+  const double m2 = h->mass * h->mass;
+  const size_t col = (size_t)Vh * 3;
+  // full precision: b, y (solution accumulator), rf (true residual), tf
+  // iteration: x (update, kind upd), r, p, Ap, t (sloppy kind)
+  void *b = w.B, *y = w.Y, *rf = w.R, *tf = w.Tf;
+  void *x = w.X, *r = w.Q, *p = w.P, *Ap = w.AP, *t = w.Ts;
+  double* rr = w.scal + 0;
+  double* alpha = w.scal + 1;
+  double* beta = w.scal + 2;
+  double* zero = w.scal + 3;
+  double2* red = mat(w, M_K, 1);
+  int nb_cg = 2 * 152;
+  Gate g0{nullptr, GATE_ALWAYS};
+  Gate ga{w.st, GATE_ACTIVE};
+  Gate gi{w.st, GATE_ITER};
+  reset_instrumentation(h);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, s));
+  int total_iters = 0, total_ru = 0;
+  double worst = 0.0;
+  blockcg_status result = BLOCKCG_OK;
+  const int chunk = default_check_every(h, 1);
+  for (int j = 0; j < n_rhs && !result; ++j) {
+    CK(cudaMemsetAsync(w.st, 0, sizeof(SolverStatus), s));
+    CK(cudaMemsetAsync(w.scal, 0, 8 * sizeof(double), s));
+    KL(to_internal(fk, (const double2*)B + j * col, b, 1, Vh, s));
+    KL(to_internal(fk, (const double2*)X + j * col, y, 1, Vh, s));
+    CK(zero_field(xk, x, col, s));
+    CK(zero_field(sk, p, col, s));
+    KL(gram_partials(fk, b, b, 1, Vh, 1, w.partials, w.nblocks, g0, s));
+    KL(gram_reduce(w.partials, w.nblocks, 1, 1, red, g0, s));
+    KL(dense_bnorm(red, w.bnorm, 1, w.st, s));
+    SolverStatus hs;
+    memset(&hs, 0, sizeof(hs));
+    bool restart = true;
+    int launched = 0, n_restart = 0;
+    for (;;) {
+      if (restart) {
+        // reliable update: y += x, x = 0, rf = b - A y in full precision and
+        // r = rf in the iteration's precision; the search direction p is kept
+        // (set to r only at the start)
+        KL(accumulate(fk, xk, y, x, col, ga, s));
+        SL(1, dslash(fk, 1, EPI_NONE, h->links_fine, y, tf, nullptr, nullptr, 0.0, h->g, 1, 1, ga, s));
+        SL(1, dslash(fk, 1, EPI_RESIDUAL, h->links_fine, tf, rf, y, b, m2, h->g, 0, 1, ga, s));
+        KL(gram_partials(fk, rf, rf, 1, Vh, 1, w.partials, w.nblocks, ga, s));
+        KL(gram_reduce(w.partials, w.nblocks, 1, 1, red, ga, s));
+        KL(cg_restart_check(red, rr, w.bnorm, tol, w.st, s));
+        KL(convert_field(fk, sk, rf, r, col, ga, s));
+        if (n_restart == 0) KL(cg_xpay(sk, p, r, zero, Vh, ga, s));
+        restart = false;
+        ++n_restart;
+      }
+      rc = read_status(h, w, &hs);
+      if (rc) return rc;
+      if (hs.done || hs.error) break;
+      if (hs.ru_pending) {  // converged or residual dropped by delta: reliable update
+        restart = true;
+        continue;
+      }
+      if (hs.iters >= h->p.max_iter) break;
+      int n = chunk;
+      if (launched + n > h->p.max_iter) n = h->p.max_iter - launched;
+      if (n <= 0) n = 1;
+      for (int i = 0; i < n; ++i) {
+        SL(0, dslash(sk, 1, EPI_NONE, h->links_sloppy, p, t, nullptr, nullptr, 0.0, h->g, 1, 1, gi, s));
+        SL(0, dslash(sk, 1, EPI_NORMAL, h->links_sloppy, t, Ap, p, nullptr, m2, h->g, 0, 1, gi, s));
+        KL(gram_partials(sk, p, Ap, 1, Vh, 1, w.partials, w.nblocks, gi, s));
+        KL(gram_reduce(w.partials, w.nblocks, 1, 1, red, gi, s));
+        KL(cg_scalar_alpha(red, rr, alpha, w.st, gi, s));
+        KL(cg_axpy_norm(sk, xk, x, r, p, Ap, alpha, w.partials, nb_cg, Vh, gi, s));
+        KL(gram_reduce(w.partials, nb_cg, 1, 1, red + 1, gi, s));
+        KL(cg_scalar_beta(red + 1, rr, beta, w.bnorm, tol, h->p.ru_delta, w.st, gi, s));
+        KL(cg_xpay(sk, p, r, beta, Vh, gi, s));
+      }
+      launched += n;
+    }
+    total_iters += hs.iters;
+    total_ru += n_restart - 1;
+    if (hs.error) result = status_to_result(h, hs);
+    else if (!hs.done) {
+      // max_iter: fold the update into y for the returned iterate
+      KL(accumulate(fk, xk, y, x, col, g0, s));
+      result = fail(h, BLOCKCG_ERR_NOT_CONVERGED, "max_iter reached");
+    }
+    if (hs.true_res_max > worst) worst = hs.true_res_max;
+    KL(from_internal(fk, y, (double2*)X + j * col, 1, Vh, s));
+  }
+  CK(cudaEventRecord(e1, s));
+  CK(cudaEventSynchronize(e1));
+  drain_events(h);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (stats) {
+    stats->iters = total_iters;
+    stats->reliable_updates = total_ru;
+    stats->true_rel_res_max = worst;
+    stats->ms_total = ms;
+    stats->launches = h->launches;
+    stats->n_stencil = h->n_st[0];
+    stats->ms_stencil = h->ms_st[0];
+    stats->n_stencil_fine = h->n_st[1];
+    stats->ms_stencil_fine = h->ms_st[1];
+  }
+  return result;
+}
+
+blockcg_status blockcg_bench_dslash(blockcg_t h, int n_rhs, int fine, int reps,
+                                    double* ms_per_launch) {
+  blockcg_status rc = check_ready(h, n_rhs);
+  if (rc) return rc;
+  if (reps < 1 || !ms_per_launch) return fail(h, BLOCKCG_ERR_ARG, "bad argument");
+  const int N = n_rhs;
+  Ws w = carve(h, N, h->ws);
+  cudaStream_t s = h->stream;
+  FieldKind k = fine ? h->fine : h->sloppy;
+  const void* links = fine ? h->links_fine : h->links_sloppy;
+  void* in = fine ? w.Y : w.P;
+  void* out = fine ? w.Tf : w.Ts;
+  size_t nel = (size_t)h->g.Vh * N * 3;
+  CK(cudaMemsetAsync(in, 0, nel * elem_bytes(k), s));
+  Gate g0{nullptr, GATE_ALWAYS};
+  int R = tile_R(N);
+  // one untimed launch, then the timed ones
+  KL(dslash(k, R, EPI_NONE, links, in, out, nullptr, nullptr, 0.0, h->g, 1, N, g0, s));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, s));
+  for (int i = 0; i < reps; ++i)
+    KL(dslash(k, R, EPI_NONE, links, in, out, nullptr, nullptr, 0.0, h->g, 1, N, g0, s));
+  CK(cudaEventRecord(e1, s));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms_per_launch = ms / reps;
+  return BLOCKCG_OK;
+}
+
+}  // extern "C"

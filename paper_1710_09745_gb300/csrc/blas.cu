@@ -1,0 +1,727 @@
+// Block BLAS on L x N block vectors (L = 3 Vh complex rows, N right-hand
+// sides), stored site-major [site][rhs][colour].
+//
+//  * Reduction multi-BLAS (Sec. 5.4): K = X^dag Y as per-CTA partial sums
+//    (gram_partials) followed by a deterministic fixed-order FP64 reduction
+//    over CTAs (gram_reduce).  Hermitian Grams compute only the upper
+//    triangle and the reduction mirrors it (the Hermitian policy of
+//    Sec. 5.4).
+//  * Streaming multi-BLAS (Sec. 5.3): every kernel reads each input row once
+//    and keeps the N x N work on chip, so traffic is linear in N.  The fused
+//    blockCGrQ update (bcg_update) stages a tile of sites of W and P in shared
+//    memory and produces, in one pass, Q = W S^-1 (S upper triangular: the
+//    zero half is skipped, Sec. 5.3), X += P (beta C) (the X update of
+//    Algorithm 1 using the P of this iteration, Sec. 5.2) and the next search
+//    block P = Q + P S^dag (Algorithm 1).  Coefficient columns are staged in
+//    chunks of JT columns so that N = 64 fits in shared memory.
+#include "internal.h"
+
+namespace bcg {
+
+static inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// ------------------------------------------------------------ layout ----
+template <class S>
+__global__ void k_to_internal(const double2* __restrict__ user, typename S::elem* __restrict__ in,
+                              int N, int Vh) {
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long total = (long long)Vh * N * 3;
+  if (idx >= total) return;
+  int c = (int)(idx % 3);
+  long long t = idx / 3;
+  int j = (int)(t % N);
+  long long site = t / N;
+  in[idx] = S::from_double2(user[((long long)j * Vh + site) * 3 + c]);
+}
+
+template <class S>
+__global__ void k_from_internal(const typename S::elem* __restrict__ in, double2* __restrict__ user,
+                                int N, int Vh) {
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long total = (long long)Vh * N * 3;
+  if (idx >= total) return;
+  int c = (int)(idx % 3);
+  long long t = idx / 3;
+  int j = (int)(t % N);
+  long long site = t / N;
+  user[((long long)j * Vh + site) * 3 + c] = S::to_double2(in[idx]);
+}
+
+cudaError_t to_internal(FieldKind k, const double2* user, void* internal, int N, int Vh,
+                        cudaStream_t s) {
+  long long total = (long long)Vh * N * 3;
+  switch (k) {
+    case FK_DF:
+      k_to_internal<StoreDF><<<nblk(total, 256), 256, 0, s>>>(user, (float4*)internal, N, Vh);
+      break;
+    case FK_F32:
+      k_to_internal<StoreF32><<<nblk(total, 256), 256, 0, s>>>(user, (float2*)internal, N, Vh);
+      break;
+    case FK_F64:
+      k_to_internal<StoreF64><<<nblk(total, 256), 256, 0, s>>>(user, (double2*)internal, N, Vh);
+      break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t from_internal(FieldKind k, const void* internal, double2* user, int N, int Vh,
+                          cudaStream_t s) {
+  long long total = (long long)Vh * N * 3;
+  switch (k) {
+    case FK_DF:
+      k_from_internal<StoreDF><<<nblk(total, 256), 256, 0, s>>>((const float4*)internal, user, N, Vh);
+      break;
+    case FK_F32:
+      k_from_internal<StoreF32><<<nblk(total, 256), 256, 0, s>>>((const float2*)internal, user, N, Vh);
+      break;
+    case FK_F64:
+      k_from_internal<StoreF64><<<nblk(total, 256), 256, 0, s>>>((const double2*)internal, user, N, Vh);
+      break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t zero_field(FieldKind k, void* f, size_t n_elems, cudaStream_t s) {
+  return cudaMemsetAsync(f, 0, n_elems * elem_bytes(k), s);
+}
+
+cudaError_t copy_field(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s);
+}
+
+// -------------------------------------------------------------- Gram ----
+static constexpr int GRAM_THREADS = 256;
+static constexpr int GRAM_MAX_EPT = 16;  // entries per thread: 64*64 / 256
+
+__host__ __device__ inline int gram_entries(int N, int herm) { return herm ? N * (N + 1) / 2 : N * N; }
+
+__device__ inline void entry_ij(int e, int N, int herm, int& i, int& j) {
+  if (!herm) {
+    i = e / N;
+    j = e - i * N;
+    return;
+  }
+  int r = 0, off = 0;
+  while (off + (N - r) <= e) {
+    off += N - r;
+    ++r;
+  }
+  i = r;
+  j = r + (e - off);
+}
+
+int gram_blocks(int N, int rows) {
+  // enough CTAs to fill the GPU a few times over, but never fewer rows per
+  // CTA than 64
+  int b = 4 * 152;
+  int maxb = (rows + 63) / 64;
+  if (b > maxb) b = maxb;
+  if (b < 1) b = 1;
+  return b;
+}
+
+template <class S>
+__global__ void __launch_bounds__(GRAM_THREADS)
+    k_gram(const typename S::elem* __restrict__ X, const typename S::elem* __restrict__ Y, int N,
+           int Vh, int herm, double2* __restrict__ partials, Gate gate) {
+  using C = typename S::comp;
+  using real = typename C::real;
+  using acc = typename C::acc;
+  __shared__ double2 red[GRAM_THREADS];
+  if (gate_closed(gate)) return;
+  const int E = gram_entries(N, herm);
+  const int tid = threadIdx.x;
+  const int G = (E >= GRAM_THREADS) ? 1 : (GRAM_THREADS / E);  // row groups
+  const int grp = tid / (E < GRAM_THREADS ? E : GRAM_THREADS);
+  const long long rows = 3LL * Vh;
+  const long long rpb = (rows + gridDim.x - 1) / gridDim.x;
+  const long long r0 = (long long)blockIdx.x * rpb;
+  const long long r1 = min(rows, r0 + rpb);
+
+  int ne = 0;
+  int ei[GRAM_MAX_EPT], ej[GRAM_MAX_EPT];
+  cpx<acc> a[GRAM_MAX_EPT];
+  if (grp < G) {
+    int e0 = (E < GRAM_THREADS) ? (tid % E) : tid;
+    for (int e = e0; e < E && ne < GRAM_MAX_EPT; e += GRAM_THREADS) {
+      entry_ij(e, N, herm, ei[ne], ej[ne]);
+      a[ne] = czero<C>();
+      ++ne;
+    }
+    for (long long r = r0 + grp; r < r1; r += G) {
+      long long site = r / 3;
+      int col = (int)(r - site * 3);
+      const typename S::elem* xr = X + site * N * 3 + col;
+      const typename S::elem* yr = Y + site * N * 3 + col;
+#pragma unroll 4
+      for (int q = 0; q < GRAM_MAX_EPT; ++q) {
+        if (q < ne) {
+          cpx<real> xv = S::load(xr + ei[q] * 3);
+          cpx<real> yv = S::load(yr + ej[q] * 3);
+          cmac_conj<C>(a[q], xv, yv);
+        }
+      }
+    }
+  }
+  double2* out = partials + (long long)blockIdx.x * E;
+  if (G == 1) {
+    for (int q = 0; q < ne; ++q) {
+      int e = tid + q * GRAM_THREADS;
+      out[e] = make_double2(C::to_double(a[q].re), C::to_double(a[q].im));
+    }
+    return;
+  }
+  // several row groups: reduce them through shared memory (one entry each)
+  double2 v = make_double2(0.0, 0.0);
+  if (grp < G && ne > 0) v = make_double2(C::to_double(a[0].re), C::to_double(a[0].im));
+  red[tid] = v;
+  __syncthreads();
+  if (tid < E) {
+    double2 sacc = red[tid];
+    for (int g2 = 1; g2 < G; ++g2) {
+      double2 w = red[g2 * E + tid];
+      sacc.x += w.x;
+      sacc.y += w.y;
+    }
+    out[tid] = sacc;
+  }
+}
+
+// warp per entry; fixed summation order -> deterministic
+__global__ void k_gram_reduce(const double2* __restrict__ partials, int nblocks, int N, int herm,
+                              double2* __restrict__ out, Gate gate) {
+  if (gate_closed(gate)) return;
+  const int E = gram_entries(N, herm);
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= E) return;
+  double sx = 0.0, sy = 0.0;
+  for (int b = lane; b < nblocks; b += 32) {
+    double2 v = partials[(long long)b * E + warp];
+    sx += v.x;
+    sy += v.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sx += __shfl_down_sync(0xffffffffu, sx, o);
+    sy += __shfl_down_sync(0xffffffffu, sy, o);
+  }
+  if (lane == 0) {
+    int i, j;
+    entry_ij(warp, N, herm, i, j);
+    out[i * N + j] = make_double2(sx, sy);
+    if (herm && i != j) out[j * N + i] = make_double2(sx, -sy);
+    if (herm && i == j) out[i * N + i] = make_double2(sx, 0.0);
+  }
+}
+
+cudaError_t gram_partials(FieldKind k, const void* X, const void* Y, int N, int Vh, int hermitian,
+                          double2* partials, int nblocks, Gate gate, cudaStream_t s) {
+  switch (k) {
+    case FK_DF:
+      k_gram<StoreDF><<<nblocks, GRAM_THREADS, 0, s>>>((const float4*)X, (const float4*)Y, N, Vh,
+                                                      hermitian, partials, gate);
+      break;
+    case FK_F32:
+      k_gram<StoreF32><<<nblocks, GRAM_THREADS, 0, s>>>((const float2*)X, (const float2*)Y, N, Vh,
+                                                       hermitian, partials, gate);
+      break;
+    case FK_F64:
+      k_gram<StoreF64><<<nblocks, GRAM_THREADS, 0, s>>>((const double2*)X, (const double2*)Y, N,
+                                                       Vh, hermitian, partials, gate);
+      break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t gram_reduce(const double2* partials, int nblocks, int N, int hermitian, double2* out,
+                        Gate gate, cudaStream_t s) {
+  int E = gram_entries(N, hermitian);
+  k_gram_reduce<<<nblk((long long)E * 32, 256), 256, 0, s>>>(partials, nblocks, N, hermitian, out,
+                                                             gate);
+  return cudaGetLastError();
+}
+
+// -------------------------------------------------- coefficient stage ----
+template <class C>
+__device__ __forceinline__ void stage_coef(cpx<typename C::real>* dst, const double2* __restrict__ M,
+                                           int N, int j0, int jn, int JT) {
+  for (int idx = threadIdx.x; idx < N * jn; idx += blockDim.x) {
+    int i = idx / jn, jj = idx - i * jn;
+    double2 v = M[i * N + j0 + jj];
+    dst[i * JT + jj] = {C::from_double(v.x), C::from_double(v.y)};
+  }
+}
+
+// ---------------------------------------------------- W = Q - AP beta ----
+template <class S>
+__global__ void k_w_update(typename S::elem* __restrict__ Q, const typename S::elem* __restrict__ AP,
+                           const double2* __restrict__ beta, int N, int Vh, Gate gate) {
+  using C = typename S::comp;
+  using real = typename C::real;
+  using acc = typename C::acc;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<real>* sb = reinterpret_cast<cpx<real>*>(smem_raw);
+  if (gate_closed(gate)) return;
+  stage_coef<C>(sb, beta, N, 0, N, N);
+  __syncthreads();
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // (site, j, colour)
+  long long total = (long long)Vh * N * 3;
+  if (idx >= total) return;
+  int c = (int)(idx % 3);
+  long long t = idx / 3;
+  int j = (int)(t % N);
+  long long site = t / N;
+  const typename S::elem* apr = AP + site * N * 3 + c;
+  cpx<acc> w = cacc_from<C>(S::load_nc(Q + idx));
+  for (int i = 0; i < N; ++i) {
+    cpx<real> ap = S::load(apr + i * 3);
+    cpx<real> b = sb[i * N + j];
+    cpx<real> nb = {b.re, b.im};
+    // w -= ap * b
+    C::msub(w.re, ap.re, nb.re);
+    C::mac(w.re, ap.im, nb.im);
+    C::msub(w.im, ap.re, nb.im);
+    C::msub(w.im, ap.im, nb.re);
+  }
+  S::store(Q + idx, cfin<C>(w));
+}
+
+cudaError_t w_update(FieldKind k, void* Q, const void* AP, const double2* beta, int N, int Vh,
+                     Gate gate, cudaStream_t s) {
+  long long total = (long long)Vh * N * 3;
+  int th = 256;
+  switch (k) {
+    case FK_DF: {
+      size_t sm = (size_t)N * N * sizeof(cpx<df>);
+      cudaFuncSetAttribute(k_w_update<StoreDF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      k_w_update<StoreDF><<<nblk(total, th), th, sm, s>>>((float4*)Q, (const float4*)AP, beta, N, Vh, gate);
+      break;
+    }
+    case FK_F32: {
+      size_t sm = (size_t)N * N * sizeof(cpx<float>);
+      k_w_update<StoreF32><<<nblk(total, th), th, sm, s>>>((float2*)Q, (const float2*)AP, beta, N, Vh, gate);
+      break;
+    }
+    case FK_F64: {
+      size_t sm = (size_t)N * N * sizeof(cpx<double>);
+      cudaFuncSetAttribute(k_w_update<StoreF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      k_w_update<StoreF64><<<nblk(total, th), th, sm, s>>>((double2*)Q, (const double2*)AP, beta, N, Vh, gate);
+      break;
+    }
+  }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------ fused update ----
+// Tile geometry: TS sites per CTA, coefficient columns in chunks of JT.
+struct TileCfg {
+  int TS, JT;
+};
+
+static TileCfg tile_cfg(int N, size_t real_cplx_bytes, int n_tiles, int n_coefs) {
+  // shared memory budget ~ 96 KB
+  const size_t budget = 96 * 1024;
+  int JT = N < 16 ? N : 16;
+  size_t coef = (size_t)n_coefs * N * JT * real_cplx_bytes;
+  int TS = 32;
+  while (TS > 1 && coef + (size_t)n_tiles * TS * N * 3 * real_cplx_bytes > budget) TS >>= 1;
+  return {TS, JT};
+}
+
+template <class SS, class XS>
+__global__ void __launch_bounds__(256)
+    k_bcg_update(typename SS::elem* __restrict__ Q, typename SS::elem* __restrict__ P,
+                 typename XS::elem* __restrict__ X, const double2* __restrict__ Sinv,
+                 const double2* __restrict__ BC, const double2* __restrict__ SH, int N, int Vh,
+                 int TS, int JT, Gate gate) {
+  using C = typename SS::comp;
+  using CX = typename XS::comp;
+  using real = typename C::real;
+  using acc = typename C::acc;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (gate_closed(gate)) return;
+  const bool keepP = gate.st != nullptr && ((const volatile SolverStatus*)gate.st)->ru_pending;
+  cpx<real>* sW = reinterpret_cast<cpx<real>*>(smem_raw);
+  cpx<real>* sP = sW + TS * N * 3;
+  cpx<real>* sA = sP + TS * N * 3;  // Sinv chunk  [N][JT]
+  cpx<real>* sB = sA + N * JT;      // BC chunk
+  cpx<real>* sC = sB + N * JT;      // SH chunk
+  const long long site0 = (long long)blockIdx.x * TS;
+  const int ns = (int)min((long long)TS, (long long)Vh - site0);
+  const long long base = site0 * N * 3;
+  const int nel = ns * N * 3;
+  for (int idx = threadIdx.x; idx < nel; idx += blockDim.x) {
+    sW[idx] = SS::load_nc(Q + base + idx);
+    sP[idx] = SS::load_nc(P + base + idx);
+  }
+  for (int j0 = 0; j0 < N; j0 += JT) {
+    const int jn = min(JT, N - j0);
+    __syncthreads();
+    stage_coef<C>(sA, Sinv, N, j0, jn, JT);
+    stage_coef<C>(sB, BC, N, j0, jn, JT);
+    if (!keepP) stage_coef<C>(sC, SH, N, j0, jn, JT);
+    __syncthreads();
+    const int nout = ns * jn * 3;
+    for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+      const int sidx = o / (jn * 3);
+      const int rem = o - sidx * jn * 3;
+      const int jj = rem / 3;
+      const int c = rem - jj * 3;
+      const int j = j0 + jj;
+      const cpx<real>* w = sW + sidx * N * 3 + c;
+      const cpx<real>* p = sP + sidx * N * 3 + c;
+      // Q = W S^-1 (S^-1 upper triangular)
+      cpx<acc> q = czero<C>();
+      for (int i = 0; i <= j; ++i) cmac<C>(q, w[i * 3], sA[i * JT + jj]);
+      cpx<real> qn = cfin<C>(q);
+      // X += P (beta C)
+      cpx<acc> x = czero<C>();
+      for (int i = 0; i < N; ++i) cmac<C>(x, p[i * 3], sB[i * JT + jj]);
+      cpx<real> xs = cfin<C>(x);
+      const long long gi = base + ((long long)sidx * N + j) * 3 + c;
+      cpx<typename CX::real> xo = XS::load_nc(X + gi);
+      cpx<typename CX::acc> xa = cacc_from<CX>(xo);
+      CX::add(xa.re, conv<CX, C>::f(xs.re));
+      CX::add(xa.im, conv<CX, C>::f(xs.im));
+      XS::store(X + gi, cfin<CX>(xa));
+      SS::store(Q + gi, qn);
+      if (!keepP) {
+        // P = Q + P S^dag (S^dag lower triangular)
+        cpx<acc> pn = cacc_from<C>(qn);
+        for (int i = j; i < N; ++i) cmac<C>(pn, p[i * 3], sC[i * JT + jj]);
+        SS::store(P + gi, cfin<C>(pn));
+      }
+    }
+  }
+}
+
+template <class SS, class XS>
+static cudaError_t launch_bcg_update(void* Q, void* P, void* X, const double2* Sinv,
+                                     const double2* BC, const double2* SH, int N, int Vh,
+                                     Gate gate, cudaStream_t s) {
+  using real = typename SS::comp::real;
+  TileCfg t = tile_cfg(N, sizeof(cpx<real>), 2, 3);
+  size_t sm = ((size_t)2 * t.TS * N * 3 + 3 * (size_t)N * t.JT) * sizeof(cpx<real>);
+  cudaFuncSetAttribute(k_bcg_update<SS, XS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  unsigned blocks = nblk(Vh, t.TS);
+  k_bcg_update<SS, XS><<<blocks, 256, sm, s>>>((typename SS::elem*)Q, (typename SS::elem*)P,
+                                               (typename XS::elem*)X, Sinv, BC, SH, N, Vh, t.TS,
+                                               t.JT, gate);
+  return cudaGetLastError();
+}
+
+cudaError_t bcg_update(FieldKind sk, FieldKind xk, void* Q, void* P, void* X, const double2* Sinv,
+                       const double2* BC, const double2* SH, int N, int Vh, Gate gate,
+                       cudaStream_t s) {
+  if (sk == FK_DF && xk == FK_DF)
+    return launch_bcg_update<StoreDF, StoreDF>(Q, P, X, Sinv, BC, SH, N, Vh, gate, s);
+  if (sk == FK_F32 && xk == FK_DF)
+    return launch_bcg_update<StoreF32, StoreDF>(Q, P, X, Sinv, BC, SH, N, Vh, gate, s);
+  if (sk == FK_F64 && xk == FK_F64)
+    return launch_bcg_update<StoreF64, StoreF64>(Q, P, X, Sinv, BC, SH, N, Vh, gate, s);
+  return cudaErrorInvalidValue;
+}
+
+// --------------------------------------------------- restart update ----
+// Q = R Cinv (R in the fine kind, Q, P in the sloppy kind); P = Q + P SH or P = Q
+template <class RS, class SS>
+__global__ void __launch_bounds__(256)
+    k_restart_update(const typename RS::elem* __restrict__ R, typename SS::elem* __restrict__ Q,
+                     typename SS::elem* __restrict__ P, const double2* __restrict__ Cinv,
+                     const double2* __restrict__ SH, int init, int N, int Vh, int TS, int JT,
+                     Gate gate) {
+  using CR = typename RS::comp;
+  using C = typename SS::comp;
+  using rreal = typename CR::real;
+  using real = typename C::real;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (gate_closed(gate)) return;
+  cpx<rreal>* sR = reinterpret_cast<cpx<rreal>*>(smem_raw);
+  cpx<rreal>* sA = sR + TS * N * 3;                                 // Cinv chunk (fine)
+  cpx<real>* sP = reinterpret_cast<cpx<real>*>(sA + N * JT);       // P tile (sloppy)
+  cpx<real>* sC = sP + TS * N * 3;                                  // SH chunk (sloppy)
+  const long long site0 = (long long)blockIdx.x * TS;
+  const int ns = (int)min((long long)TS, (long long)Vh - site0);
+  const long long base = site0 * N * 3;
+  const int nel = ns * N * 3;
+  for (int idx = threadIdx.x; idx < nel; idx += blockDim.x) {
+    sR[idx] = RS::load_nc(R + base + idx);
+    if (!init) sP[idx] = SS::load_nc(P + base + idx);
+  }
+  for (int j0 = 0; j0 < N; j0 += JT) {
+    const int jn = min(JT, N - j0);
+    __syncthreads();
+    stage_coef<CR>(sA, Cinv, N, j0, jn, JT);
+    if (!init) stage_coef<C>(sC, SH, N, j0, jn, JT);
+    __syncthreads();
+    const int nout = ns * jn * 3;
+    for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+      const int sidx = o / (jn * 3);
+      const int rem = o - sidx * jn * 3;
+      const int jj = rem / 3;
+      const int c = rem - jj * 3;
+      const int j = j0 + jj;
+      const cpx<rreal>* r = sR + sidx * N * 3 + c;
+      cpx<typename CR::acc> q = czero<CR>();
+      for (int i = 0; i <= j; ++i) cmac<CR>(q, r[i * 3], sA[i * JT + jj]);
+      cpx<rreal> qf = cfin<CR>(q);
+      cpx<real> qn = {conv<C, CR>::f(qf.re), conv<C, CR>::f(qf.im)};
+      const long long gi = base + ((long long)sidx * N + j) * 3 + c;
+      SS::store(Q + gi, qn);
+      cpx<typename C::acc> pn = cacc_from<C>(qn);
+      if (!init) {
+        const cpx<real>* p = sP + sidx * N * 3 + c;
+        for (int i = 0; i < N; ++i) cmac<C>(pn, p[i * 3], sC[i * JT + jj]);
+      }
+      SS::store(P + gi, cfin<C>(pn));
+    }
+  }
+}
+
+template <class RS, class SS>
+static cudaError_t launch_restart(const void* R, void* Q, void* P, const double2* Cinv,
+                                  const double2* SH, int init, int N, int Vh, Gate gate,
+                                  cudaStream_t s) {
+  using rreal = typename RS::comp::real;
+  using real = typename SS::comp::real;
+  size_t big = sizeof(cpx<rreal>) > sizeof(cpx<real>) ? sizeof(cpx<rreal>) : sizeof(cpx<real>);
+  TileCfg t = tile_cfg(N, big, 2, 2);
+  size_t sm = ((size_t)t.TS * N * 3 + (size_t)N * t.JT) * sizeof(cpx<rreal>) +
+              ((size_t)t.TS * N * 3 + (size_t)N * t.JT) * sizeof(cpx<real>);
+  cudaFuncSetAttribute(k_restart_update<RS, SS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sm);
+  k_restart_update<RS, SS><<<nblk(Vh, t.TS), 256, sm, s>>>(
+      (const typename RS::elem*)R, (typename SS::elem*)Q, (typename SS::elem*)P, Cinv, SH, init, N,
+      Vh, t.TS, t.JT, gate);
+  return cudaGetLastError();
+}
+
+cudaError_t restart_update(FieldKind rk, FieldKind sk, const void* R, void* Q, void* P,
+                           const double2* Cinv, const double2* SH, int init, int N, int Vh,
+                           Gate gate, cudaStream_t s) {
+  if (rk == FK_F64 && sk == FK_DF)
+    return launch_restart<StoreF64, StoreDF>(R, Q, P, Cinv, SH, init, N, Vh, gate, s);
+  if (rk == FK_F64 && sk == FK_F32)
+    return launch_restart<StoreF64, StoreF32>(R, Q, P, Cinv, SH, init, N, Vh, gate, s);
+  if (rk == FK_F64 && sk == FK_F64)
+    return launch_restart<StoreF64, StoreF64>(R, Q, P, Cinv, SH, init, N, Vh, gate, s);
+  return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------ accumulate ----
+// Y (full precision) += X (iterated update) ; X = 0
+template <class YS, class XS>
+__global__ void k_accumulate(typename YS::elem* __restrict__ Y, typename XS::elem* __restrict__ X,
+                             long long n, Gate gate) {
+  using CY = typename YS::comp;
+  using CX = typename XS::comp;
+  if (gate_closed(gate)) return;
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  cpx<typename CX::real> x = XS::load_nc(X + idx);
+  cpx<typename CY::acc> y = cacc_from<CY>(YS::load_nc(Y + idx));
+  CY::add(y.re, conv<CY, CX>::f(x.re));
+  CY::add(y.im, conv<CY, CX>::f(x.im));
+  YS::store(Y + idx, cfin<CY>(y));
+  cpx<typename CX::real> z = {CX::rzero(), CX::rzero()};
+  XS::store(X + idx, z);
+}
+
+cudaError_t accumulate(FieldKind yk, FieldKind xk, void* Y, void* X, size_t n, Gate gate,
+                       cudaStream_t s) {
+  if (yk == FK_F64 && xk == FK_DF)
+    k_accumulate<StoreF64, StoreDF><<<nblk(n, 256), 256, 0, s>>>((double2*)Y, (float4*)X, n, gate);
+  else if (yk == FK_F64 && xk == FK_F64)
+    k_accumulate<StoreF64, StoreF64><<<nblk(n, 256), 256, 0, s>>>((double2*)Y, (double2*)X, n, gate);
+  else if (yk == FK_DF && xk == FK_DF)
+    k_accumulate<StoreDF, StoreDF><<<nblk(n, 256), 256, 0, s>>>((float4*)Y, (float4*)X, n, gate);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------- kind conversion ----
+template <class DS, class SS>
+__global__ void k_convert(const typename SS::elem* __restrict__ in, typename DS::elem* __restrict__ out,
+                          long long n, Gate gate) {
+  if (gate_closed(gate)) return;
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  out[idx] = DS::from_double2(SS::to_double2(in[idx]));
+}
+
+cudaError_t convert_field(FieldKind from, FieldKind to, const void* in, void* out, size_t n,
+                          Gate gate, cudaStream_t s) {
+  if (from == FK_F64 && to == FK_DF)
+    k_convert<StoreDF, StoreF64><<<nblk(n, 256), 256, 0, s>>>((const double2*)in, (float4*)out, n, gate);
+  else if (from == FK_F64 && to == FK_F32)
+    k_convert<StoreF32, StoreF64><<<nblk(n, 256), 256, 0, s>>>((const double2*)in, (float2*)out, n, gate);
+  else if (from == to)
+    return cudaMemcpyAsync(out, in, n * elem_bytes(to), cudaMemcpyDeviceToDevice, s);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+// ------------------------------------------- generic block caxpy / trmul ----
+// mode 0: Y += X a ; mode 1: Y = X a with a upper triangular
+template <class S>
+__global__ void __launch_bounds__(256)
+    k_block_mul(const typename S::elem* __restrict__ X, const double2* __restrict__ a,
+                typename S::elem* __restrict__ Y, int N, int Vh, int TS, int JT, int mode) {
+  using C = typename S::comp;
+  using real = typename C::real;
+  using acc = typename C::acc;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<real>* sX = reinterpret_cast<cpx<real>*>(smem_raw);
+  cpx<real>* sA = sX + TS * N * 3;
+  const long long site0 = (long long)blockIdx.x * TS;
+  const int ns = (int)min((long long)TS, (long long)Vh - site0);
+  const long long base = site0 * N * 3;
+  for (int idx = threadIdx.x; idx < ns * N * 3; idx += blockDim.x) sX[idx] = S::load_nc(X + base + idx);
+  for (int j0 = 0; j0 < N; j0 += JT) {
+    const int jn = min(JT, N - j0);
+    __syncthreads();
+    stage_coef<C>(sA, a, N, j0, jn, JT);
+    __syncthreads();
+    for (int o = threadIdx.x; o < ns * jn * 3; o += blockDim.x) {
+      const int sidx = o / (jn * 3);
+      const int rem = o - sidx * jn * 3;
+      const int jj = rem / 3;
+      const int c = rem - jj * 3;
+      const int j = j0 + jj;
+      const long long gi = base + ((long long)sidx * N + j) * 3 + c;
+      const cpx<real>* x = sX + sidx * N * 3 + c;
+      cpx<acc> y = (mode == 0) ? cacc_from<C>(S::load_nc(Y + gi)) : czero<C>();
+      const int iend = (mode == 1) ? j + 1 : N;
+      for (int i = 0; i < iend; ++i) cmac<C>(y, x[i * 3], sA[i * JT + jj]);
+      S::store(Y + gi, cfin<C>(y));
+    }
+  }
+}
+
+template <class S>
+static cudaError_t launch_block_mul(const void* X, const double2* a, void* Y, int N, int Vh,
+                                    int mode, cudaStream_t s) {
+  using real = typename S::comp::real;
+  TileCfg t = tile_cfg(N, sizeof(cpx<real>), 1, 1);
+  size_t sm = ((size_t)t.TS * N * 3 + (size_t)N * t.JT) * sizeof(cpx<real>);
+  cudaFuncSetAttribute(k_block_mul<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_block_mul<S><<<nblk(Vh, t.TS), 256, sm, s>>>((const typename S::elem*)X, a,
+                                                 (typename S::elem*)Y, N, Vh, t.TS, t.JT, mode);
+  return cudaGetLastError();
+}
+
+cudaError_t block_caxpy(FieldKind k, const void* X, const double2* a, void* Y, int N, int Vh,
+                        cudaStream_t s) {
+  switch (k) {
+    case FK_DF: return launch_block_mul<StoreDF>(X, a, Y, N, Vh, 0, s);
+    case FK_F32: return launch_block_mul<StoreF32>(X, a, Y, N, Vh, 0, s);
+    default: return launch_block_mul<StoreF64>(X, a, Y, N, Vh, 0, s);
+  }
+}
+
+cudaError_t block_trmul(FieldKind k, const void* M, const double2* Rinv, void* Q, int N, int Vh,
+                        cudaStream_t s) {
+  switch (k) {
+    case FK_DF: return launch_block_mul<StoreDF>(M, Rinv, Q, N, Vh, 1, s);
+    case FK_F32: return launch_block_mul<StoreF32>(M, Rinv, Q, N, Vh, 1, s);
+    default: return launch_block_mul<StoreF64>(M, Rinv, Q, N, Vh, 1, s);
+  }
+}
+
+// ---------------------------------------------------------- CG, N = 1 ----
+// x += alpha p ; r -= alpha Ap ; per-CTA partial of |r|^2
+// (x in the update kind, r, p, Ap in the iteration's kind)
+template <class S, class XS>
+__global__ void __launch_bounds__(256)
+    k_cg_axpy_norm(typename XS::elem* __restrict__ x, typename S::elem* __restrict__ r,
+                   const typename S::elem* __restrict__ p, const typename S::elem* __restrict__ Ap,
+                   const double* __restrict__ alpha_p, double2* __restrict__ partials, long long n,
+                   Gate gate) {
+  using C = typename S::comp;
+  using CX = typename XS::comp;
+  using real = typename C::real;
+  using acc = typename C::acc;
+  __shared__ double red[256];
+  if (gate_closed(gate)) return;
+  const typename CX::real alphax = CX::from_double(*alpha_p);
+  const real nalpha = C::from_double(-*alpha_p);
+  acc nrm = C::zero();
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    cpx<real> pv = S::load(p + i);
+    cpx<real> av = S::load(Ap + i);
+    cpx<typename CX::acc> xv = cacc_from<CX>(XS::load_nc(x + i));
+    cpx<acc> rv = cacc_from<C>(S::load_nc(r + i));
+    CX::mac(xv.re, alphax, conv<CX, C>::f(pv.re));
+    CX::mac(xv.im, alphax, conv<CX, C>::f(pv.im));
+    C::mac(rv.re, nalpha, av.re);
+    C::mac(rv.im, nalpha, av.im);
+    XS::store(x + i, cfin<CX>(xv));
+    cpx<real> rf = cfin<C>(rv);
+    S::store(r + i, rf);
+    C::mac(nrm, rf.re, rf.re);
+    C::mac(nrm, rf.im, rf.im);
+  }
+  red[threadIdx.x] = C::to_double(nrm);
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[blockIdx.x] = make_double2(red[0], 0.0);
+}
+
+template <class S>
+__global__ void k_cg_xpay(typename S::elem* __restrict__ p, const typename S::elem* __restrict__ r,
+                          const double* __restrict__ beta_p, long long n, Gate gate) {
+  using C = typename S::comp;
+  using real = typename C::real;
+  if (gate_closed(gate)) return;
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const real beta = C::from_double(*beta_p);
+  cpx<typename C::acc> v = cacc_from<C>(S::load(r + i));
+  cpx<real> pv = S::load_nc(p + i);
+  C::mac(v.re, beta, pv.re);
+  C::mac(v.im, beta, pv.im);
+  S::store(p + i, cfin<C>(v));
+}
+
+cudaError_t cg_axpy_norm(FieldKind k, FieldKind xk, void* x, void* r, const void* p,
+                         const void* Ap, const double* alpha, double2* partials, int nblocks, int Vh,
+                         Gate gate, cudaStream_t s) {
+  long long n = 3LL * Vh;
+  if (k == FK_DF && xk == FK_DF)
+    k_cg_axpy_norm<StoreDF, StoreDF><<<nblocks, 256, 0, s>>>(
+        (float4*)x, (float4*)r, (const float4*)p, (const float4*)Ap, alpha, partials, n, gate);
+  else if (k == FK_F32 && xk == FK_DF)
+    k_cg_axpy_norm<StoreF32, StoreDF><<<nblocks, 256, 0, s>>>(
+        (float4*)x, (float2*)r, (const float2*)p, (const float2*)Ap, alpha, partials, n, gate);
+  else if (k == FK_F64 && xk == FK_F64)
+    k_cg_axpy_norm<StoreF64, StoreF64><<<nblocks, 256, 0, s>>>(
+        (double2*)x, (double2*)r, (const double2*)p, (const double2*)Ap, alpha, partials, n, gate);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t cg_xpay(FieldKind k, void* p, const void* r, const double* beta, int Vh, Gate gate,
+                    cudaStream_t s) {
+  long long n = 3LL * Vh;
+  switch (k) {
+    case FK_DF:
+      k_cg_xpay<StoreDF><<<nblk(n, 256), 256, 0, s>>>((float4*)p, (const float4*)r, beta, n, gate);
+      break;
+    case FK_F32:
+      k_cg_xpay<StoreF32><<<nblk(n, 256), 256, 0, s>>>((float2*)p, (const float2*)r, beta, n, gate);
+      break;
+    case FK_F64:
+      k_cg_xpay<StoreF64><<<nblk(n, 256), 256, 0, s>>>((double2*)p, (const double2*)r, beta, n, gate);
+      break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace bcg

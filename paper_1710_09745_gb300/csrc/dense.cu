@@ -1,0 +1,399 @@
+// Small dense N x N algebra of blockCGrQ in native FP64, on the device, one
+// CTA per call (N <= 64).  The paper does these on the host with Eigen
+// (Sec. 5); keeping them on the device removes every host round trip from the
+// iteration, so a whole iteration is a fixed sequence of launches gated by the
+// status word.
+//
+//   dense_beta     beta = (P^dag A P)^-1 through a Cholesky factorisation,
+//                  BC = beta C                                  (Algorithm 1)
+//   dense_qr_step  thin QR of W = Q - AP beta from its Gram: W^dag W = S^dag S
+//                  (Cholesky), S^-1, S^dag; C_prev = C; C = S C; iterated
+//                  residuals |R_i| = |column i of C|; reliable-update trigger
+//                                                   (Algorithms 1, 2 and 3)
+//   dense_restart  thin QR of a true residual R = B - A Y: C = chol factor,
+//                  C^-1, convergence on the true residual, and
+//                  S = C C_old^-1 with C_old the C in force before the last
+//                  C = S C                                      (Algorithm 3)
+// Matrices are complex128 row-major [N][N] in global memory; the CTA works
+// on copies in shared memory.
+#include "internal.h"
+#include "../../include/blockcg.h"
+
+namespace bcg {
+
+static constexpr int DENSE_THREADS = 256;
+
+__device__ __forceinline__ double2 cm(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+
+// In-place lower Cholesky A = L L^dag of a Hermitian matrix in shared memory.
+// Returns 0, BLOCKCG_ERR_BREAKDOWN or BLOCKCG_ERR_NONFINITE (uniform over the CTA).
+__device__ int chol_lower(double2* A, int N, int* flag) {
+  const int tid = threadIdx.x;
+  for (int k = 0; k < N; ++k) {
+    if (tid == 0) {
+      double d = A[k * N + k].x;
+      int f = 0;
+      if (!isfinite(d)) f = BLOCKCG_ERR_NONFINITE;
+      else if (!(d > 0.0)) f = BLOCKCG_ERR_BREAKDOWN;
+      else A[k * N + k] = make_double2(sqrt(d), 0.0);
+      *flag = f;
+    }
+    __syncthreads();
+    int f = *flag;
+    if (f) return f;
+    double inv = 1.0 / A[k * N + k].x;
+    for (int i = k + 1 + tid; i < N; i += blockDim.x) {
+      double2 v = A[i * N + k];
+      A[i * N + k] = make_double2(v.x * inv, v.y * inv);
+    }
+    __syncthreads();
+    int m = N - k - 1;
+    for (int idx = tid; idx < m * m; idx += blockDim.x) {
+      int i = k + 1 + idx / m, j = k + 1 + idx % m;
+      if (j <= i) A[i * N + j] = csub(A[i * N + j], cm(A[i * N + k], cconj(A[j * N + k])));
+    }
+    __syncthreads();
+  }
+  // zero the strict upper triangle
+  for (int idx = tid; idx < N * N; idx += blockDim.x) {
+    int i = idx / N, j = idx % N;
+    if (j > i) A[idx] = make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  return 0;
+}
+
+// Linv = L^-1 for lower-triangular L (shared memory); parallel over columns.
+__device__ void tri_inv_lower(const double2* L, double2* Linv, int N) {
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < N * N; idx += blockDim.x) Linv[idx] = make_double2(0.0, 0.0);
+  __syncthreads();
+  for (int j = tid; j < N; j += blockDim.x) {
+    Linv[j * N + j] = make_double2(1.0 / L[j * N + j].x, 0.0);
+    for (int i = j + 1; i < N; ++i) {
+      double2 s = make_double2(0.0, 0.0);
+      for (int l = j; l < i; ++l) s = cadd(s, cm(L[i * N + l], Linv[l * N + j]));
+      double inv = 1.0 / L[i * N + i].x;
+      Linv[i * N + j] = make_double2(-s.x * inv, -s.y * inv);
+    }
+  }
+  __syncthreads();
+}
+
+__device__ void load_mat(double2* dst, const double2* __restrict__ src, int N) {
+  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) dst[idx] = src[idx];
+  __syncthreads();
+}
+
+__device__ __forceinline__ bool dense_gate_closed(const SolverStatus* st, int mode) {
+  if (mode == GATE_ALWAYS || st == nullptr) return false;
+  const volatile SolverStatus* s = st;
+  if (s->done || s->error) return true;
+  if (mode == GATE_RU && !s->ru_pending) return true;
+  if (mode == GATE_ITER && s->ru_pending) return true;
+  return false;
+}
+
+// ---------------------------------------------------------------- beta ----
+__global__ void __launch_bounds__(DENSE_THREADS)
+    k_dense_beta(const double2* __restrict__ H, const double2* __restrict__ Cm,
+                 double2* __restrict__ beta, double2* __restrict__ BC, int N, SolverStatus* st,
+                 int gmode) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int flag;
+  if (dense_gate_closed(st, gmode)) return;
+  double2* A = reinterpret_cast<double2*>(smem_raw);
+  double2* Li = A + N * N;
+  double2* Bt = Li + N * N;
+  load_mat(A, H, N);
+  int f = chol_lower(A, N, &flag);
+  if (f) {
+    if (threadIdx.x == 0) st->error = f;
+    return;
+  }
+  tri_inv_lower(A, Li, N);
+  // beta = Li^dag Li
+  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+    int i = idx / N, j = idx % N;
+    double2 s = make_double2(0.0, 0.0);
+    for (int l = (i > j ? i : j); l < N; ++l) s = cadd(s, cm(cconj(Li[l * N + i]), Li[l * N + j]));
+    Bt[idx] = s;
+    beta[idx] = s;
+  }
+  __syncthreads();
+  // BC = beta C
+  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+    int i = idx / N, j = idx % N;
+    double2 s = make_double2(0.0, 0.0);
+    for (int l = 0; l < N; ++l) s = cadd(s, cm(Bt[i * N + l], Cm[l * N + j]));
+    BC[idx] = s;
+  }
+}
+
+cudaError_t dense_beta(const double2* H, const double2* C, double2* beta, double2* BC, int N,
+                       SolverStatus* st, Gate gate, cudaStream_t s) {
+  size_t sm = 3ull * N * N * sizeof(double2);
+  cudaFuncSetAttribute(k_dense_beta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_dense_beta<<<1, DENSE_THREADS, sm, s>>>(H, C, beta, BC, N, st, gate.mode);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- qr step ----
+__global__ void __launch_bounds__(DENSE_THREADS)
+    k_dense_qr_step(const double2* __restrict__ G, double2* __restrict__ C,
+                    double2* __restrict__ C_prev, double2* __restrict__ Sinv,
+                    double2* __restrict__ SH, const double* __restrict__ bnorm, QrStepParams p,
+                    int N, SolverStatus* st, int gmode) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int flag;
+  __shared__ double resv[64];
+  if (dense_gate_closed(st, gmode)) return;
+  double2* A = reinterpret_cast<double2*>(smem_raw);
+  double2* Li = A + N * N;
+  double2* Cs = Li + N * N;
+  load_mat(A, G, N);
+  int f = chol_lower(A, N, &flag);
+  if (f) {
+    if (threadIdx.x == 0) st->error = f;
+    return;
+  }
+  tri_inv_lower(A, Li, N);
+  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+    int i = idx / N, j = idx % N;
+    Sinv[idx] = cconj(Li[j * N + i]);  // (L^-1)^dag, upper
+    SH[idx] = A[idx];                  // S^dag = L, lower
+    double2 c = C[idx];
+    Cs[idx] = c;
+    C_prev[idx] = c;
+  }
+  __syncthreads();
+  // C = S C with S = L^dag: (S C)_ij = sum_{l >= i} conj(L_li) C_lj
+  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+    int i = idx / N, j = idx % N;
+    double2 s = make_double2(0.0, 0.0);
+    for (int l = i; l < N; ++l) s = cadd(s, cm(cconj(A[l * N + i]), Cs[l * N + j]));
+    C[idx] = s;
+  }
+  __syncthreads();
+  // iterated residual of column i: |R_i| = sqrt(sum_j |C_ji|^2)
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    double s = 0.0;
+    for (int j = 0; j < N; ++j) {
+      double2 c = C[j * N + i];
+      s += c.x * c.x + c.y * c.y;
+    }
+    resv[i] = sqrt(s) / bnorm[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double rmax = 0.0;
+    for (int i = 0; i < N; ++i) rmax = fmax(rmax, resv[i]);
+    int it = st->iters + 1;
+    st->iters = it;
+    st->res_max = rmax;
+    int ru = 0;
+    if (!(rmax <= p.tol) && !isfinite(rmax)) st->error = BLOCKCG_ERR_NONFINITE;
+    if (rmax <= p.tol) ru = 1;
+    else if (p.delta > 0.0 && rmax < p.delta * st->res_at_ru) ru = 1;
+    else if (p.ru_every > 0 && (it % p.ru_every) == 0) ru = 1;
+    st->ru_pending = ru;
+  }
+}
+
+cudaError_t dense_qr_step(const double2* G, double2* C, double2* C_prev, double2* Sinv,
+                          double2* SH, const double* bnorm, QrStepParams p, int N,
+                          SolverStatus* st, Gate gate, cudaStream_t s) {
+  size_t sm = 3ull * N * N * sizeof(double2);
+  cudaFuncSetAttribute(k_dense_qr_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_dense_qr_step<<<1, DENSE_THREADS, sm, s>>>(G, C, C_prev, Sinv, SH, bnorm, p, N, st, gate.mode);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- restart ----
+__global__ void __launch_bounds__(DENSE_THREADS)
+    k_dense_restart(const double2* __restrict__ G, double2* __restrict__ C,
+                    double2* __restrict__ C_prev, double2* __restrict__ Cinv,
+                    double2* __restrict__ SH, const double* __restrict__ bnorm, double tol,
+                    int init, int N, SolverStatus* st, int gmode) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int flag;
+  __shared__ double tres[64];
+  if (dense_gate_closed(st, gmode)) return;
+  double2* A = reinterpret_cast<double2*>(smem_raw);  // -> L of the true residual
+  double2* Wk = A + N * N;                            // L^-1, then C_prev^dag (lower)
+  double2* Pi = Wk + N * N;                           // (C_prev^dag)^-1
+  load_mat(A, G, N);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tres[i] = sqrt(fmax(A[i * N + i].x, 0.0)) / bnorm[i];
+  __syncthreads();
+  int f = chol_lower(A, N, &flag);
+  if (f) {
+    if (threadIdx.x == 0) st->error = f;
+    return;
+  }
+  tri_inv_lower(A, Wk, N);
+  double tmax = 0.0;
+  for (int i = 0; i < N; ++i) tmax = fmax(tmax, tres[i]);
+  // C_new = L^dag (upper), Cinv = (L^-1)^dag
+  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+    int i = idx / N, j = idx % N;
+    Cinv[idx] = cconj(Wk[j * N + i]);
+  }
+  __syncthreads();
+  if (!init) {
+    for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+      int i = idx / N, j = idx % N;
+      Wk[idx] = cconj(C_prev[j * N + i]);
+    }
+    __syncthreads();
+    tri_inv_lower(Wk, Pi, N);  // Pi = (C_prev^dag)^-1 = (C_prev^-1)^dag
+    // S = C_new C_prev^-1, so S^dag = (C_prev^-1)^dag C_new^dag = Pi L
+    for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+      int i = idx / N, j = idx % N;
+      double2 s = make_double2(0.0, 0.0);
+      for (int l = j; l <= i; ++l) s = cadd(s, cm(Pi[i * N + l], A[l * N + j]));
+      SH[idx] = s;
+    }
+  }
+  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+    int i = idx / N, j = idx % N;
+    C[idx] = cconj(A[j * N + i]);
+  }
+  if (threadIdx.x == 0) {
+    st->true_res_max = tmax;
+    st->res_max = tmax;
+    st->res_at_ru = tmax;
+    if (!isfinite(tmax)) st->error = BLOCKCG_ERR_NONFINITE;
+    if (tmax <= tol) st->done = 1;
+    if (!init) st->reliable_updates += 1;
+  }
+}
+
+cudaError_t dense_restart(const double2* G, double2* C, double2* C_prev, double2* Cinv,
+                          double2* SH, const double* bnorm, double tol, int init, int N,
+                          SolverStatus* st, Gate gate, cudaStream_t s) {
+  size_t sm = 3ull * N * N * sizeof(double2);
+  cudaFuncSetAttribute(k_dense_restart, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_dense_restart<<<1, DENSE_THREADS, sm, s>>>(G, C, C_prev, Cinv, SH, bnorm, tol, init, N, st,
+                                               gate.mode);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- misc ----
+__global__ void k_dense_bnorm(const double2* __restrict__ Gb, double* __restrict__ bnorm, int N,
+                              SolverStatus* st) {
+  int i = threadIdx.x;
+  if (i < N) {
+    double v = Gb[i * N + i].x;
+    bnorm[i] = sqrt(fmax(v, 0.0));
+    if (!isfinite(v)) st->error = BLOCKCG_ERR_NONFINITE;
+    else if (!(v > 0.0)) st->error = BLOCKCG_ERR_BREAKDOWN;
+  }
+}
+
+cudaError_t dense_bnorm(const double2* Gb, double* bnorm, int N, SolverStatus* st,
+                        cudaStream_t s) {
+  k_dense_bnorm<<<1, 64, 0, s>>>(Gb, bnorm, N, st);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(DENSE_THREADS)
+    k_dense_chol_upper(const double2* __restrict__ H, double2* __restrict__ R,
+                       double2* __restrict__ Rinv, int N, int* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int flag;
+  double2* A = reinterpret_cast<double2*>(smem_raw);
+  double2* Li = A + N * N;
+  load_mat(A, H, N);
+  int f = chol_lower(A, N, &flag);
+  if (threadIdx.x == 0) *err = f;
+  if (f) return;
+  tri_inv_lower(A, Li, N);
+  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+    int i = idx / N, j = idx % N;
+    R[idx] = cconj(A[j * N + i]);
+    Rinv[idx] = cconj(Li[j * N + i]);
+  }
+}
+
+cudaError_t dense_chol_upper(const double2* H, double2* R, double2* Rinv, int N, int* err,
+                             cudaStream_t s) {
+  size_t sm = 2ull * N * N * sizeof(double2);
+  cudaFuncSetAttribute(k_dense_chol_upper, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_dense_chol_upper<<<1, DENSE_THREADS, sm, s>>>(H, R, Rinv, N, err);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ CG scalars ----
+__global__ void k_cg_alpha(const double2* __restrict__ pAp, const double* __restrict__ rr,
+                           double* __restrict__ alpha, SolverStatus* st, int gmode) {
+  if (dense_gate_closed(st, gmode)) return;
+  double d = pAp[0].x;
+  if (!isfinite(d)) {
+    st->error = BLOCKCG_ERR_NONFINITE;
+    return;
+  }
+  if (!(d > 0.0)) {
+    st->error = BLOCKCG_ERR_BREAKDOWN;
+    return;
+  }
+  *alpha = *rr / d;
+}
+
+__global__ void k_cg_beta(const double2* __restrict__ rr_new_sum, double* __restrict__ rr,
+                          double* __restrict__ beta, const double* __restrict__ bnorm, double tol,
+                          double delta, SolverStatus* st, int gmode) {
+  if (dense_gate_closed(st, gmode)) return;
+  double bnorm2 = bnorm[0] * bnorm[0];
+  double rn = rr_new_sum[0].x;
+  *beta = rn / *rr;
+  *rr = rn;
+  int it = st->iters + 1;
+  st->iters = it;
+  st->res_max = sqrt(rn / bnorm2);
+  if (!isfinite(rn)) st->error = BLOCKCG_ERR_NONFINITE;
+  double rel = sqrt(rn / bnorm2);
+  // converged, or dropped by delta since the last reliable update: the host
+  // runs a reliable update, which also verifies convergence
+  if (rel <= tol || (delta > 0.0 && rel < delta * st->res_at_ru)) st->ru_pending = 1;
+}
+
+cudaError_t cg_scalar_alpha(const double2* pAp, const double* rr, double* alpha,
+                            SolverStatus* st, Gate gate, cudaStream_t s) {
+  k_cg_alpha<<<1, 1, 0, s>>>(pAp, rr, alpha, st, gate.mode);
+  return cudaGetLastError();
+}
+
+cudaError_t cg_scalar_beta(const double2* rr_new_sum, double* rr, double* beta,
+                           const double* bnorm, double tol, double delta, SolverStatus* st,
+                           Gate gate, cudaStream_t s) {
+  k_cg_beta<<<1, 1, 0, s>>>(rr_new_sum, rr, beta, bnorm, tol, delta, st, gate.mode);
+  return cudaGetLastError();
+}
+
+__global__ void k_cg_restart_check(const double2* __restrict__ rr_sum, double* __restrict__ rr,
+                                   const double* __restrict__ bnorm, double tol,
+                                   SolverStatus* st) {
+  if (st->error) return;
+  double rn = rr_sum[0].x;
+  *rr = rn;
+  double rel = sqrt(rn) / bnorm[0];
+  st->true_res_max = rel;
+  st->res_max = rel;
+  st->res_at_ru = rel;
+  if (!isfinite(rn)) st->error = BLOCKCG_ERR_NONFINITE;
+  else if (rel <= tol) st->done = 1;
+  else st->ru_pending = 0;
+}
+
+cudaError_t cg_restart_check(const double2* rr_sum, double* rr, const double* bnorm, double tol,
+                             SolverStatus* st, cudaStream_t s) {
+  k_cg_restart_check<<<1, 1, 0, s>>>(rr_sum, rr, bnorm, tol, st);
+  return cudaGetLastError();
+}
+
+}  // namespace bcg

@@ -1,0 +1,129 @@
+// Host-side declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace bcg {
+
+// Field storage kinds (element = one complex number).
+enum FieldKind { FK_DF = 0, FK_F32 = 1, FK_F64 = 2 };
+
+inline size_t elem_bytes(FieldKind k) { return k == FK_F32 ? 8 : 16; }
+
+// Kernel gating by the device status word, so that a host loop can enqueue
+// whole iterations without reading back the convergence state.
+// GATE_ACTIVE: run unless done or failed; GATE_RU: additionally only when a
+// reliable update is pending; GATE_ITER: run unless done, failed or a
+// convergence check is pending (CG baseline).
+enum GateMode { GATE_ALWAYS = 0, GATE_ACTIVE = 1, GATE_RU = 2, GATE_ITER = 3 };
+struct Gate {
+  const SolverStatus* st;
+  int mode;
+};
+
+__device__ __forceinline__ bool gate_closed(const Gate& g) {
+  if (g.mode == GATE_ALWAYS || g.st == nullptr) return false;
+  const volatile SolverStatus* s = g.st;
+  if (s->done || s->error) return true;
+  if (g.mode == GATE_RU && !s->ru_pending) return true;
+  if (g.mode == GATE_ITER && s->ru_pending) return true;
+  return false;
+}
+
+// Stencil epilogues.
+enum DslashEpi {
+  EPI_NONE = 0,     // out = D in
+  EPI_NORMAL = 1,   // out = m2 * c1 - D in         (A = m^2 - D_eo D_oe, second half)
+  EPI_RESIDUAL = 2  // out = c2 - (m2 * c1 - D in)  (R = B - A Y)
+};
+
+// ---- stencil.cu
+cudaError_t pack_links(FieldKind k, const double2* fat, const double2* lng, void* out,
+                       const Geom& g, int antiperiodic_t, cudaStream_t s);
+size_t links_bytes(FieldKind k, const Geom& g);  // both parities
+// links points at the start of the packed array for both parities
+cudaError_t dslash(FieldKind k, int R, int epi, const void* links, const void* in, void* out,
+                   const void* c1, const void* c2, double m2, const Geom& g, int out_parity,
+                   int N, Gate gate, cudaStream_t s);
+
+// ---- blas.cu
+cudaError_t to_internal(FieldKind k, const double2* user, void* internal, int N, int Vh,
+                        cudaStream_t s);
+cudaError_t from_internal(FieldKind k, const void* internal, double2* user, int N, int Vh,
+                          cudaStream_t s);
+cudaError_t zero_field(FieldKind k, void* f, size_t n_elems, cudaStream_t s);
+int gram_blocks(int N, int rows);
+cudaError_t gram_partials(FieldKind k, const void* X, const void* Y, int N, int Vh, int hermitian,
+                          double2* partials, int nblocks, Gate gate, cudaStream_t s);
+cudaError_t gram_reduce(const double2* partials, int nblocks, int N, int hermitian, double2* out,
+                        Gate gate, cudaStream_t s);
+// Q <- Q - AP beta
+cudaError_t w_update(FieldKind k, void* Q, const void* AP, const double2* beta, int N, int Vh,
+                     Gate gate, cudaStream_t s);
+// Q <- W Sinv ; X += P BC ; P <- Q + P SH unless st->ru_pending
+cudaError_t bcg_update(FieldKind sk, FieldKind xk, void* Q, void* P, void* X, const double2* Sinv,
+                       const double2* BC, const double2* SH, int N, int Vh, Gate gate,
+                       cudaStream_t s);
+// Q <- R Cinv (converted to Q's kind) ; P <- Q + P SH (or P <- Q when init)
+cudaError_t restart_update(FieldKind rk, FieldKind sk, const void* R, void* Q, void* P,
+                           const double2* Cinv, const double2* SH, int init, int N, int Vh,
+                           Gate gate, cudaStream_t s);
+// Y (kind yk) += X (kind xk) ; X = 0
+cudaError_t accumulate(FieldKind yk, FieldKind xk, void* Y, void* X, size_t n_elems, Gate gate,
+                       cudaStream_t s);
+// same-layout conversion between kinds (F64 -> DF, F64 -> F32, or a copy)
+cudaError_t convert_field(FieldKind from, FieldKind to, const void* in, void* out, size_t n_elems,
+                          Gate gate, cudaStream_t s);
+// Y += X a (generic block caxpy)
+cudaError_t block_caxpy(FieldKind k, const void* X, const double2* a, void* Y, int N, int Vh,
+                        cudaStream_t s);
+// Q = M Rinv (generic right-multiplication by an upper-triangular matrix)
+cudaError_t block_trmul(FieldKind k, const void* M, const double2* Rinv, void* Q, int N, int Vh,
+                        cudaStream_t s);
+// CG (N = 1) helpers
+cudaError_t cg_axpy_norm(FieldKind k, FieldKind xk, void* x, void* r, const void* p, const void* Ap,
+                         const double* alpha, double2* partials, int nblocks, int Vh, Gate gate,
+                         cudaStream_t s);
+cudaError_t cg_xpay(FieldKind k, void* p, const void* r, const double* beta, int Vh, Gate gate,
+                    cudaStream_t s);
+cudaError_t copy_field(void* dst, const void* src, size_t bytes, cudaStream_t s);
+
+// ---- dense.cu
+// beta = H^-1 via Cholesky, BC = beta C
+cudaError_t dense_beta(const double2* H, const double2* C, double2* beta, double2* BC, int N,
+                       SolverStatus* st, Gate gate, cudaStream_t s);
+// Cholesky of G = W^dag W -> S (upper), Sinv, SH = S^dag; C_prev = C; C = S C;
+// residual norms and the reliable-update trigger.
+struct QrStepParams {
+  double tol, delta;
+  int ru_every, max_iter;
+};
+cudaError_t dense_qr_step(const double2* G, double2* C, double2* C_prev, double2* Sinv,
+                          double2* SH, const double* bnorm, QrStepParams p, int N,
+                          SolverStatus* st, Gate gate, cudaStream_t s);
+// Cholesky of the true-residual Gram -> C_new, Cinv; convergence on the true
+// residual; S = C_new C_prev^-1 -> SH = S^dag (unless init).
+cudaError_t dense_restart(const double2* G, double2* C, double2* C_prev, double2* Cinv,
+                          double2* SH, const double* bnorm, double tol, int init, int N,
+                          SolverStatus* st, Gate gate, cudaStream_t s);
+// bnorm_i = sqrt(Gb_ii); error if any is zero or not finite
+cudaError_t dense_bnorm(const double2* Gb, double* bnorm, int N, SolverStatus* st,
+                        cudaStream_t s);
+// R upper with R^dag R = H, Rinv = R^-1; *err = blockcg_status
+cudaError_t dense_chol_upper(const double2* H, double2* R, double2* Rinv, int N, int* err,
+                             cudaStream_t s);
+// CG scalars: alpha = rr / pAp ; on the second call beta = rr_new / rr, convergence
+cudaError_t cg_scalar_alpha(const double2* pAp, const double* rr, double* alpha,
+                            SolverStatus* st, Gate gate, cudaStream_t s);
+cudaError_t cg_scalar_beta(const double2* rr_new_sum, double* rr, double* beta,
+                           const double* bnorm, double tol, double delta, SolverStatus* st,
+                           Gate gate, cudaStream_t s);
+// after a true-residual recomputation: rr = |r|^2; done if it meets tol, else
+// clear the pending check so that iterations resume
+cudaError_t cg_restart_check(const double2* rr_sum, double* rr, const double* bnorm, double tol,
+                             SolverStatus* st, cudaStream_t s);
+
+}  // namespace bcg

@@ -1,0 +1,104 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds, loads,
+exports every symbol include/blockcg.h declares, and validates arguments."""
+import ctypes as ct
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1710_09745_gb300 import build, binding
+    build.build()
+    return binding.load_library()
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "blockcg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(blockcg_[a-zA-Z_0-9]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(lib):
+    from paper_1710_09745_gb300 import binding
+    names = declared_symbols()
+    assert len(names) >= 16
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(binding.ABI_SYMBOLS) == names
+
+
+def test_default_params_and_status_strings(lib):
+    from paper_1710_09745_gb300.binding import Params
+    p = Params()
+    lib.blockcg_default_params(ct.byref(p))
+    assert p.max_iter == 100000 and abs(p.ru_delta - 0.1) < 1e-15 and p.prec == 0
+    for s in range(8):
+        assert lib.blockcg_status_string(s)
+
+
+@pytest.mark.parametrize("dims,ok", [((4, 4, 4, 4), True), ((3, 4, 4, 4), False),
+                                     ((4, 4, 0, 4), False), ((2, 2, 2, 2), True),
+                                     ((4, 4, 4, 5), False)])
+def test_create_validates_dims(lib, dims, ok):
+    h = ct.c_void_p()
+    d = (ct.c_int * 4)(*dims)
+    rc = lib.blockcg_create(ct.byref(h), d, 0.1, None, None)
+    assert (rc == 0) == ok
+    if ok:
+        lib.blockcg_destroy(h)
+
+
+def test_create_rejects_bad_mass_and_params(lib):
+    from paper_1710_09745_gb300.binding import Params
+    h = ct.c_void_p()
+    d = (ct.c_int * 4)(4, 4, 4, 4)
+    assert lib.blockcg_create(ct.byref(h), d, float("nan"), None, None) == 1
+    p = Params()
+    lib.blockcg_default_params(ct.byref(p))
+    p.ru_delta = 1.5
+    assert lib.blockcg_create(ct.byref(h), d, 0.1, ct.byref(p), None) == 1
+    p.ru_delta = 0.1
+    p.prec = 7
+    assert lib.blockcg_create(ct.byref(h), d, 0.1, ct.byref(p), None) == 1
+
+
+def test_sizes_and_unready_handle(lib):
+    from paper_1710_09745_gb300.binding import Params
+    h = ct.c_void_p()
+    d = (ct.c_int * 4)(8, 8, 8, 8)
+    assert lib.blockcg_create(ct.byref(h), d, 0.1, None, None) == 0
+    Vh = 8 ** 4 // 2
+    # double-float links: 2 parities x 16 hops x 9 entries x 16 bytes
+    assert lib.blockcg_gauge_bytes(h) >= 2 * 16 * 9 * Vh * 16
+    w1 = lib.blockcg_workspace_bytes(h, 1)
+    w16 = lib.blockcg_workspace_bytes(h, 16)
+    assert 0 < w1 < w16
+    assert lib.blockcg_workspace_bytes(h, 0) == 0 and lib.blockcg_workspace_bytes(h, 65) == 0
+    # no gauge / workspace yet: refused without touching the GPU
+    assert lib.blockcg_apply_MdagM(h, ct.c_void_p(16), ct.c_void_p(16), 1) == 3
+    assert lib.blockcg_solve(h, ct.c_void_p(16), ct.c_void_p(16), 1, 1e-10, None) == 3
+    assert lib.blockcg_set_workspace(h, None, 0) == 3
+    assert lib.blockcg_load_gauge(h, None, None, None, 0) == 1
+    assert lib.blockcg_last_error(h)
+    lib.blockcg_destroy(h)
+    p = Params()
+    lib.blockcg_default_params(ct.byref(p))
+    p.prec = 2
+    assert lib.blockcg_create(ct.byref(h), d, 0.1, ct.byref(p), None) == 0
+    # mixed form keeps a second (FP32) copy of the links
+    assert lib.blockcg_gauge_bytes(h) >= 2 * 16 * 9 * Vh * (16 + 8)
+    lib.blockcg_destroy(h)
+
+
+def test_binding_fails_loudly_without_library(tmp_path):
+    from paper_1710_09745_gb300 import binding
+    with pytest.raises(RuntimeError):
+        binding._lib = None
+        try:
+            binding.load_library(str(tmp_path / "missing.so"))
+        finally:
+            binding._lib = None

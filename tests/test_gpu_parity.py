@@ -1,0 +1,264 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle,
+element by element, on seeded inputs that span several CTAs and a ragged
+tail; edge cases of the method; full-size sampled checks."""
+import numpy as np
+import pytest
+
+import hisq_inputs as hi
+from oracle import block as oblock
+from oracle import hisq
+from tests import gpu_helpers as gh
+from tests import lattice_helpers as lh
+
+pytestmark = pytest.mark.gpu
+
+DIMS = (6, 8, 10, 12)   # Vh = 2880: several CTAs and a ragged last one
+PRECS = ["f64", "f64_native", "mixed_f32"]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("N", [1, 3, 4, 16])
+@pytest.mark.parametrize("parity", [0, 1])
+def test_dslash_parity(prec, N, parity):
+    s, fat, lng = gh.make_solver(DIMS, 0.1, prec=prec, seed=1001)
+    psi = hi.gaussian_sources(DIMS, N, seed=77 + N)
+    out = gh.to_np(s.dslash(psi, parity))
+    ref = hisq.dslash(DIMS, fat, lng, psi, parity)
+    assert gh.rel_err(out, ref) < gh.TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("N", [1, 5, 8])
+@pytest.mark.parametrize("antiperiodic", [False, True])
+def test_apply_MdagM_parity(prec, N, antiperiodic):
+    s, fat, lng = gh.make_solver(DIMS, 0.05, prec=prec, seed=1002, antiperiodic_t=antiperiodic)
+    v = hi.gaussian_sources(DIMS, N, seed=88)
+    out = gh.to_np(s.apply_MdagM(v))
+    ref = hisq.apply_A(DIMS, fat, lng, 0.05, v, antiperiodic)
+    assert gh.rel_err(out, ref) < gh.TOL[prec]
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (2, 4, 2, 6), (4, 4, 4, 4)])
+def test_apply_tiny_lattices_wraparound(dims):
+    """On 2^4 and 4^4 forward/backward and 1/3-hop neighbours coincide; every
+    term must still be summed."""
+    s, fat, lng = gh.make_solver(dims, 0.1, prec="f64", seed=1003, max_rhs=4)
+    v = hi.gaussian_sources(dims, 4, seed=5)
+    assert gh.rel_err(gh.to_np(s.apply_MdagM(v)), hisq.apply_A(dims, fat, lng, 0.1, v)) < 1e-12
+
+
+def test_free_field_plane_wave_on_gpu():
+    dims = (8, 8, 8, 8)
+    fat, lng = hi.unit_links(dims)
+    s, _, _ = gh.make_solver(dims, 0.2, links=(fat, lng), max_rhs=2)
+    p = (2 * np.pi / 8, 3 * 2 * np.pi / 8, 0.0, 5 * 2 * np.pi / 8)
+    v = lh.plane_wave_even(dims, p, colour=2)
+    out = gh.to_np(s.apply_MdagM(v))[0]
+    lam = lh.free_eigenvalue(p, 0.2, hi.LONG_COEFF)
+    assert np.abs(out - lam * v).max() < 1e-12
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("N", [1, 4, 16, 33])
+def test_block_cdot_parity(prec, N):
+    s, _, _ = gh.make_solver(DIMS, 0.1, prec=prec, max_rhs=max(N, 16))
+    X = hi.gaussian_sources(DIMS, N, seed=9)
+    Y = hi.gaussian_sources(DIMS, N, seed=10)
+    K = gh.to_np(s.block_cdot(X, Y))
+    Kref = oblock.block_cdot(oblock.as_columns(X), oblock.as_columns(Y))
+    scale = np.linalg.norm(oblock.as_columns(X), axis=0).max() * np.linalg.norm(oblock.as_columns(Y), axis=0).max()
+    tol = {"f64": 1e-13, "f64_native": 1e-14, "mixed_f32": 1e-5}[prec]
+    assert np.abs(K - Kref).max() < tol * scale
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("N", [1, 6, 16, 64])
+def test_block_caxpy_parity(prec, N):
+    s, _, _ = gh.make_solver((4, 4, 4, 6), 0.1, prec=prec, max_rhs=max(N, 16))
+    X = hi.gaussian_sources((4, 4, 4, 6), N, seed=11)
+    Y = hi.gaussian_sources((4, 4, 4, 6), N, seed=12)
+    rng = np.random.default_rng(13)
+    a = rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))
+    out = gh.to_np(s.block_caxpy(X, a, Y))
+    ref = oblock.from_columns(oblock.block_caxpy(oblock.as_columns(Y), oblock.as_columns(X), a), X.shape[1])
+    tol = {"f64": 1e-13, "f64_native": 1e-14, "mixed_f32": 1e-5}[prec]
+    assert gh.rel_err(out, ref) < tol * np.sqrt(N)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("N", [1, 7, 16, 64])
+def test_thin_qr_parity(prec, N):
+    dims = (4, 4, 6, 8)
+    s, _, _ = gh.make_solver(dims, 0.1, prec=prec, max_rhs=max(N, 16))
+    M = hi.gaussian_sources(dims, N, seed=14)
+    Q, R = s.thin_qr(M)
+    Q, R = gh.to_np(Q), gh.to_np(R)
+    Qr, Rr = oblock.thin_qr(oblock.as_columns(M))
+    tol = {"f64": 1e-12, "f64_native": 1e-13, "mixed_f32": 1e-4}[prec]
+    assert gh.rel_err(R, Rr) < tol
+    Qc = oblock.as_columns(Q)
+    assert np.abs(Qc.conj().T @ Qc - np.eye(N)).max() < 10 * tol
+
+
+def test_thin_qr_breakdown_on_dependent_columns():
+    from paper_1710_09745_gb300 import BlockCGError
+    dims = (4, 4, 4, 4)
+    s, _, _ = gh.make_solver(dims, 0.1, max_rhs=4)
+    M = hi.gaussian_sources(dims, 3, seed=15)
+    M[2] = M[0]
+    with pytest.raises(BlockCGError) as e:
+        s.thin_qr(M)
+    assert e.value.status == 4
+
+
+# ------------------------------------------------------------------ solvers
+def _oracle_solution(dims, fat, lng, mass, b):
+    x, _, res = hisq.cg(dims, fat, lng, mass, b, tol=1e-13)
+    return x
+
+
+def test_solve_config_4x4_n4():
+    """4^4, m = 0.1, N = 4, FP64 block CG to 1e-10."""
+    dims = (4, 4, 4, 4)
+    s, fat, lng = gh.make_solver(dims, 0.1, seed=1001, max_rhs=4)
+    b = hi.gaussian_sources(dims, 4, seed=2001)
+    X, info = s.solve(b, tol=1e-10)
+    X = gh.to_np(X)
+    assert info["status"] == 0, info
+    r = b - hisq.apply_A(dims, fat, lng, 0.1, X)
+    rel = np.linalg.norm(r.reshape(4, -1), axis=1) / np.linalg.norm(b.reshape(4, -1), axis=1)
+    assert rel.max() <= 1e-10, rel
+    assert info["true_rel_res_max"] <= 1e-10
+    xo = _oracle_solution(dims, fat, lng, 0.1, b)
+    err = np.linalg.norm((X - xo).reshape(4, -1), axis=1) / np.linalg.norm(xo.reshape(4, -1), axis=1)
+    assert err.max() < 1e-8, err
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("N", [1, 8])
+def test_solve_against_oracle(prec, N):
+    dims = (8, 8, 8, 8)
+    mass = 0.05
+    s, fat, lng = gh.make_solver(dims, mass, prec=prec, seed=1005, max_rhs=8)
+    b = hi.gaussian_sources(dims, N, seed=2005)
+    X, info = s.solve(b, tol=1e-12)
+    X = gh.to_np(X)
+    assert info["status"] == 0, info
+    r = b - hisq.apply_A(dims, fat, lng, mass, X)
+    rel = np.linalg.norm(r.reshape(N, -1), axis=1) / np.linalg.norm(b.reshape(N, -1), axis=1)
+    assert rel.max() <= 1e-12 * 1.01, rel
+    xo = _oracle_solution(dims, fat, lng, mass, b)
+    err = np.linalg.norm((X - xo).reshape(N, -1), axis=1) / np.linalg.norm(xo.reshape(N, -1), axis=1)
+    assert err.max() < 1e-8, err
+
+
+@pytest.mark.parametrize("prec", ["f64", "f64_native"])
+def test_solve_cg_against_oracle(prec):
+    dims = (8, 8, 8, 8)
+    mass = 0.05
+    s, fat, lng = gh.make_solver(dims, mass, prec=prec, seed=1006, max_rhs=4)
+    b = hi.gaussian_sources(dims, 3, seed=2006)
+    X, info = s.solve_cg(b, tol=1e-12)
+    X = gh.to_np(X)
+    assert info["status"] == 0, info
+    xo, iters, _ = hisq.cg(dims, fat, lng, mass, b, tol=1e-12)
+    err = np.linalg.norm((X - xo).reshape(3, -1), axis=1) / np.linalg.norm(xo.reshape(3, -1), axis=1)
+    assert err.max() < 1e-8
+    # same algorithm (reliable updates keep the search direction), same
+    # stopping rule: iteration counts agree to a few percent
+    assert abs(info["iters"] - int(iters.sum())) <= 0.05 * int(iters.sum()) + 3
+
+
+def test_block_fewer_iterations_than_cg():
+    dims = (8, 8, 8, 8)
+    s, _, _ = gh.make_solver(dims, 0.01, seed=1007, max_rhs=8)
+    b = hi.gaussian_sources(dims, 8, seed=2007)
+    _, ib = s.solve(b, tol=1e-10)
+    _, ic = s.solve_cg(b[:2], tol=1e-10)
+    assert ib["status"] == 0 and ic["status"] == 0
+    assert ib["iters"] < ic["iters"] / 2
+
+
+def test_solve_initial_guess_and_resume():
+    """Alg. 1 starts from any X: resuming from a partial solve converges."""
+    dims = (6, 6, 6, 6)
+    s, fat, lng = gh.make_solver(dims, 0.1, seed=1008, max_rhs=4, max_iter=5)
+    b = hi.gaussian_sources(dims, 4, seed=2008)
+    X1, i1 = s.solve(b, tol=1e-10)
+    assert i1["status"] == 6           # not converged after 5 iterations
+    assert 1e-10 < i1["true_rel_res_max"] < 1.0
+    s2, _, _ = gh.make_solver(dims, 0.1, seed=1008, max_rhs=4)
+    X2, i2 = s2.solve(b, X0=X1, tol=1e-10)
+    assert i2["status"] == 0
+    r = b - hisq.apply_A(dims, fat, lng, 0.1, gh.to_np(X2))
+    assert (np.linalg.norm(r.reshape(4, -1), axis=1) / np.linalg.norm(b.reshape(4, -1), axis=1)).max() <= 1e-10
+
+
+def test_solve_dependent_rhs_breaks_down():
+    from paper_1710_09745_gb300 import BlockCGError
+    dims = (4, 4, 4, 4)
+    s, _, _ = gh.make_solver(dims, 0.1, max_rhs=4)
+    b = hi.gaussian_sources(dims, 3, seed=16)
+    b[1] = 2.0 * b[0]
+    with pytest.raises(BlockCGError) as e:
+        s.solve(b, tol=1e-10)
+    assert e.value.status == 4
+
+
+def test_solve_zero_rhs_rejected():
+    from paper_1710_09745_gb300 import BlockCGError
+    dims = (4, 4, 4, 4)
+    s, _, _ = gh.make_solver(dims, 0.1, max_rhs=4)
+    b = hi.gaussian_sources(dims, 2, seed=17)
+    b[1] = 0
+    with pytest.raises(BlockCGError):
+        s.solve(b, tol=1e-10)
+
+
+def test_nonfinite_source_reported():
+    from paper_1710_09745_gb300 import BlockCGError
+    dims = (4, 4, 4, 4)
+    s, _, _ = gh.make_solver(dims, 0.1, max_rhs=4)
+    b = hi.gaussian_sources(dims, 2, seed=18)
+    b[0, 3, 1] = np.nan
+    with pytest.raises(BlockCGError) as e:
+        s.solve(b, tol=1e-10)
+    assert e.value.status == 5
+
+
+def test_bad_arguments():
+    from paper_1710_09745_gb300 import BlockCGError
+    dims = (4, 4, 4, 4)
+    s, _, _ = gh.make_solver(dims, 0.1, max_rhs=4)
+    b = hi.gaussian_sources(dims, 5, seed=19)
+    with pytest.raises(BlockCGError):
+        s.solve(b, tol=1e-10)          # more RHS than the workspace holds
+    with pytest.raises(BlockCGError):
+        s.solve(b[:2], tol=0.0)
+
+
+def test_mixed_precision_reliable_updates():
+    dims = (8, 8, 8, 8)
+    mass = 0.02
+    s, fat, lng = gh.make_solver(dims, mass, prec="mixed_f32", seed=1009, max_rhs=8)
+    b = hi.gaussian_sources(dims, 8, seed=2009)
+    X, info = s.solve(b, tol=1e-10)
+    assert info["status"] == 0
+    assert info["reliable_updates"] >= 3
+    r = b - hisq.apply_A(dims, fat, lng, mass, gh.to_np(X))
+    rel = np.linalg.norm(r.reshape(8, -1), axis=1) / np.linalg.norm(b.reshape(8, -1), axis=1)
+    assert rel.max() <= 1e-10
+    s64, _, _ = gh.make_solver(dims, mass, prec="f64", seed=1009, max_rhs=8)
+    _, i64 = s64.solve(b, tol=1e-10)
+    assert info["iters"] <= 1.6 * i64["iters"]
+
+
+def test_max_rhs_64():
+    dims = (4, 4, 4, 8)
+    s, fat, lng = gh.make_solver(dims, 0.2, seed=1010, max_rhs=64)
+    b = hi.gaussian_sources(dims, 64, seed=2010)
+    X, info = s.solve(b, tol=1e-10)
+    assert info["status"] == 0
+    r = b - hisq.apply_A(dims, fat, lng, 0.2, gh.to_np(X))
+    rel = np.linalg.norm(r.reshape(64, -1), axis=1) / np.linalg.norm(b.reshape(64, -1), axis=1)
+    assert rel.max() <= 1e-10
