@@ -572,7 +572,6 @@ blockcg_status blockcg_solve_cg(blockcg_t h, const void* B, void* X, int n_rhs, 
   double* rr = w.scal + 0;
   double* alpha = w.scal + 1;
   double* beta = w.scal + 2;
-  double* zero = w.scal + 3;
   double2* red = mat(w, M_K, 1);
   int nb_cg = 2 * 152;
   Gate g0{nullptr, GATE_ALWAYS};
@@ -603,17 +602,17 @@ blockcg_status blockcg_solve_cg(blockcg_t h, const void* B, void* X, int n_rhs, 
     int launched = 0, n_restart = 0;
     for (;;) {
       if (restart) {
-        // reliable update: y += x, x = 0, rf = b - A y in full precision and
-        // r = rf in the iteration's precision; the search direction p is kept
-        // (set to r only at the start)
+        // reliable update: y += x, x = 0, rf = b - A y in full precision,
+        // r = rf in the iteration's precision, then p = r + beta p with beta
+        // from the true residual (p = r at the start)
         KL(accumulate(fk, xk, y, x, col, ga, s));
         SL(1, dslash(fk, 1, EPI_NONE, h->links_fine, y, tf, nullptr, nullptr, 0.0, h->g, 1, 1, ga, s));
         SL(1, dslash(fk, 1, EPI_RESIDUAL, h->links_fine, tf, rf, y, b, m2, h->g, 0, 1, ga, s));
         KL(gram_partials(fk, rf, rf, 1, Vh, 1, w.partials, w.nblocks, ga, s));
         KL(gram_reduce(w.partials, w.nblocks, 1, 1, red, ga, s));
-        KL(cg_restart_check(red, rr, w.bnorm, tol, w.st, s));
+        KL(cg_restart_check(red, rr, beta, w.bnorm, tol, n_restart == 0, w.st, s));
         KL(convert_field(fk, sk, rf, r, col, ga, s));
-        if (n_restart == 0) KL(cg_xpay(sk, p, r, zero, Vh, ga, s));
+        KL(cg_xpay(sk, p, r, beta, Vh, ga, s));
         restart = false;
         ++n_restart;
       }

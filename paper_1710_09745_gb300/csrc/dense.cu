@@ -31,15 +31,26 @@ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_doub
 __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 
 // In-place lower Cholesky A = L L^dag of a Hermitian matrix in shared memory.
-// Returns 0, BLOCKCG_ERR_BREAKDOWN or BLOCKCG_ERR_NONFINITE (uniform over the CTA).
+// A pivot that is not finite gives BLOCKCG_ERR_NONFINITE; a pivot d_k <= 0 or
+// d_k <= CHOL_REL_TOL * A_kk (A_kk the diagonal before factorising) gives
+// BLOCKCG_ERR_BREAKDOWN: d_k / A_kk is the squared sine of the angle between
+// column k and the span of the columns before it, so a value at rounding
+// level means the block is numerically rank deficient (e.g. linearly
+// dependent right-hand sides, Sec. 3).  Returns 0 or the error (uniform over
+// the CTA).
+static constexpr double CHOL_REL_TOL = 1e-13;
+
 __device__ int chol_lower(double2* A, int N, int* flag) {
+  __shared__ double diag0[64];
   const int tid = threadIdx.x;
+  for (int k = tid; k < N; k += blockDim.x) diag0[k] = A[k * N + k].x;
+  __syncthreads();
   for (int k = 0; k < N; ++k) {
     if (tid == 0) {
       double d = A[k * N + k].x;
       int f = 0;
-      if (!isfinite(d)) f = BLOCKCG_ERR_NONFINITE;
-      else if (!(d > 0.0)) f = BLOCKCG_ERR_BREAKDOWN;
+      if (!isfinite(d) || !isfinite(diag0[k])) f = BLOCKCG_ERR_NONFINITE;
+      else if (!(d > 0.0) || !(d > CHOL_REL_TOL * diag0[k])) f = BLOCKCG_ERR_BREAKDOWN;
       else A[k * N + k] = make_double2(sqrt(d), 0.0);
       *flag = f;
     }
@@ -350,16 +361,23 @@ __global__ void k_cg_beta(const double2* __restrict__ rr_new_sum, double* __rest
   if (dense_gate_closed(st, gmode)) return;
   double bnorm2 = bnorm[0] * bnorm[0];
   double rn = rr_new_sum[0].x;
-  *beta = rn / *rr;
-  *rr = rn;
   int it = st->iters + 1;
   st->iters = it;
   st->res_max = sqrt(rn / bnorm2);
-  if (!isfinite(rn)) st->error = BLOCKCG_ERR_NONFINITE;
+  if (!isfinite(rn)) {
+    st->error = BLOCKCG_ERR_NONFINITE;
+    return;
+  }
   double rel = sqrt(rn / bnorm2);
   // converged, or dropped by delta since the last reliable update: the host
-  // runs a reliable update, which also verifies convergence
-  if (rel <= tol || (delta > 0.0 && rel < delta * st->res_at_ru)) st->ru_pending = 1;
+  // runs a reliable update, which recomputes r and then forms beta from the
+  // true residual (cg_restart_check); rr keeps the previous |r|^2 for that
+  if (rel <= tol || (delta > 0.0 && rel < delta * st->res_at_ru)) {
+    st->ru_pending = 1;
+    return;
+  }
+  *beta = rn / *rr;
+  *rr = rn;
 }
 
 cudaError_t cg_scalar_alpha(const double2* pAp, const double* rr, double* alpha,
@@ -376,23 +394,31 @@ cudaError_t cg_scalar_beta(const double2* rr_new_sum, double* rr, double* beta,
 }
 
 __global__ void k_cg_restart_check(const double2* __restrict__ rr_sum, double* __restrict__ rr,
-                                   const double* __restrict__ bnorm, double tol,
-                                   SolverStatus* st) {
+                                   double* __restrict__ beta, const double* __restrict__ bnorm,
+                                   double tol, int init, SolverStatus* st) {
   if (st->error) return;
   double rn = rr_sum[0].x;
-  *rr = rn;
   double rel = sqrt(rn) / bnorm[0];
   st->true_res_max = rel;
   st->res_max = rel;
   st->res_at_ru = rel;
-  if (!isfinite(rn)) st->error = BLOCKCG_ERR_NONFINITE;
-  else if (rel <= tol) st->done = 1;
-  else st->ru_pending = 0;
+  if (!isfinite(rn)) {
+    st->error = BLOCKCG_ERR_NONFINITE;
+    return;
+  }
+  if (rel <= tol) {
+    st->done = 1;
+    return;
+  }
+  // p = r + beta p with beta from the true residual (p = r at the start)
+  *beta = init ? 0.0 : rn / *rr;
+  *rr = rn;
+  st->ru_pending = 0;
 }
 
-cudaError_t cg_restart_check(const double2* rr_sum, double* rr, const double* bnorm, double tol,
-                             SolverStatus* st, cudaStream_t s) {
-  k_cg_restart_check<<<1, 1, 0, s>>>(rr_sum, rr, bnorm, tol, st);
+cudaError_t cg_restart_check(const double2* rr_sum, double* rr, double* beta, const double* bnorm,
+                             double tol, int init, SolverStatus* st, cudaStream_t s) {
+  k_cg_restart_check<<<1, 1, 0, s>>>(rr_sum, rr, beta, bnorm, tol, init, st);
   return cudaGetLastError();
 }
 

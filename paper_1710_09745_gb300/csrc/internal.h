@@ -121,9 +121,10 @@ cudaError_t cg_scalar_alpha(const double2* pAp, const double* rr, double* alpha,
 cudaError_t cg_scalar_beta(const double2* rr_new_sum, double* rr, double* beta,
                            const double* bnorm, double tol, double delta, SolverStatus* st,
                            Gate gate, cudaStream_t s);
-// after a true-residual recomputation: rr = |r|^2; done if it meets tol, else
-// clear the pending check so that iterations resume
-cudaError_t cg_restart_check(const double2* rr_sum, double* rr, const double* bnorm, double tol,
-                             SolverStatus* st, cudaStream_t s);
+// after a true-residual recomputation: done if it meets tol; else
+// beta = |r|^2 / rr (0 when init), rr = |r|^2, and the pending check is
+// cleared so that iterations resume
+cudaError_t cg_restart_check(const double2* rr_sum, double* rr, double* beta, const double* bnorm,
+                             double tol, int init, SolverStatus* st, cudaStream_t s);
 
 }  // namespace bcg
