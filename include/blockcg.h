@@ -194,6 +194,33 @@ blockcg_status blockcg_solve_cg(blockcg_t h, const void* B, void* X, int n_rhs, 
 blockcg_status blockcg_bench_dslash(blockcg_t h, int n_rhs, int fine, int reps,
                                     double* ms_per_launch);
 
+/* K = X^dag Y, the same block inner product as blockcg_block_cdot, for
+ * callers that cannot allocate device memory: code running inside a memory
+ * pool it does not own, plug-ins that receive only the host application's
+ * buffers, or programs that must avoid cudaMalloc because it may synchronise
+ * the device.  The paper has no counterpart to this entry point.
+ *
+ * Needs no handle and no workspace.  X, Y: device complex128 [n_rhs][vh][3]
+ * (user layout, vh = sites per parity); K: device complex128
+ * [n_rhs][n_rhs] row-major; stream: cudaStream_t (NULL = legacy default).
+ * Computed in native FP64.  Enqueues two kernels and returns.
+ *
+ * Scratch: the partial sums live in a fixed 4 MiB array inside the library's
+ * device image, which every GPU that loads the library holds until the
+ * process exits.  The entry point calls no cudaMalloc, cudaFree or any other
+ * allocating routine.  On its first call on a device (with that device
+ * current) it looks up the array's device address once, so make that first
+ * call before any stream capture.  Every call overwrites the whole region it
+ * uses, so no state carries over from one call to the next, but all calls
+ * share the one array: calls whose kernels overlap on the GPU (e.g. on two
+ * streams at once) race and must be serialised by the caller.
+ *
+ * Errors: BLOCKCG_ERR_ARG for null pointers, vh < 1, or n_rhs outside
+ * [1, 64] (the scratch holds 64 x 64 partial matrices per CTA at most);
+ * BLOCKCG_ERR_CUDA if the symbol lookup or a launch fails. */
+blockcg_status blockcg_block_cdot_noalloc(const void* X, const void* Y, int n_rhs, long long vh,
+                                          void* K, void* stream);
+
 /* Release the handle (host memory only; caller-owned device buffers stay). */
 void blockcg_destroy(blockcg_t h);
 

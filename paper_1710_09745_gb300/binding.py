@@ -28,7 +28,7 @@ ABI_SYMBOLS = [
     "blockcg_workspace_bytes", "blockcg_set_workspace", "blockcg_dslash", "blockcg_apply_MdagM",
     "blockcg_block_cdot", "blockcg_block_caxpy", "blockcg_thin_qr", "blockcg_solve",
     "blockcg_solve_cg", "blockcg_bench_dslash", "blockcg_destroy", "blockcg_status_string",
-    "blockcg_last_error",
+    "blockcg_last_error", "blockcg_block_cdot_noalloc",
 ]
 
 
@@ -80,6 +80,7 @@ def load_library(path: str = LIB_PATH):
         "blockcg_solve": (I, [P, P, P, I, D, ct.POINTER(Stats)]),
         "blockcg_solve_cg": (I, [P, P, P, I, D, ct.POINTER(Stats)]),
         "blockcg_bench_dslash": (I, [P, I, I, I, ct.POINTER(D)]),
+        "blockcg_block_cdot_noalloc": (I, [P, P, I, ct.c_longlong, P, P]),
         "blockcg_destroy": (None, [P]),
         "blockcg_status_string": (ct.c_char_p, [I]),
         "blockcg_last_error": (ct.c_char_p, [P]),
