@@ -58,6 +58,9 @@ def parse_args():
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--prec", default="f64")
     ap.add_argument("--no-extras", action="store_true", help="skip CG/mixed/sweep/CPU legs")
+    ap.add_argument("--dslash-only", action="store_true",
+                    help="only the stencil sweep (Fig. 1 analogue) for --prec over --sweep")
+    ap.add_argument("--sweep", type=int, nargs="+", default=[1, 4, 8, 16, 32])
     return ap.parse_args()
 
 
@@ -211,10 +214,36 @@ def run_reference(a):
 
 
 # -------------------------------------------------------------------- ours
+def dslash_only(a):
+    """Stencil GB/s per N for one precision (no solve); one JSON line."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1710_09745_gb300 import BlockCG
+    dims = tuple(a.dims)
+    Vh = int(np.prod(dims)) // 2
+    fat, lng, _ = cpu_inputs(a)
+    dev = torch.device("cuda", 0)
+    h = BlockCG(dims, fat.to(dev), lng.to(dev), a.mass, prec=a.prec, max_rhs=max(a.sweep), device=dev)
+    hbm_peak, _ = load_peaks()
+    bpr = {"f64": 8, "f64_native": 8, "mixed_f32": 4}[a.prec]
+    rows = {}
+    for n in a.sweep:
+        ms = h.bench_dslash(n, reps=max(a.steps, 1) * 10)
+        gbs = (288 + 12 * n) * bpr * Vh / (ms * 1e-3) / 1e9
+        rows[str(n)] = {"ms": ms, "gbs": gbs, "hbm_frac": gbs / hbm_peak,
+                        "gflops": STENCIL_FLOPS * n * Vh / (ms * 1e-3) / 1e9}
+    print(json.dumps({"dslash": rows, "prec": a.prec, "dims": list(dims)}))
+
+
 def main():
     a = parse_args()
     if a.impl == "reference":
         run_reference(a)
+        return
+    if a.dslash_only:
+        dslash_only(a)
         return
     world, rank, local = dist_env()
     import numpy as np
@@ -339,7 +368,10 @@ def main():
         "gpu_launches": int(sum(i["launches"] for i in infos)),
         "roofline": roof,
         "solve": {"iters": infos[-1]["iters"], "reliable_updates": infos[-1]["reliable_updates"],
-                  "true_rel_res_max": infos[-1]["true_rel_res_max"], "converged": ok},
+                  "true_rel_res_max": infos[-1]["true_rel_res_max"], "converged": ok,
+                  "ms_breakdown": {k: sum(i[k] for i in infos) / a.steps for k in
+                                   ("ms_stencil", "ms_stencil_fine", "ms_gram", "ms_stream",
+                                    "ms_dense", "ms_total")}},
     }
 
     if rank == 0 and not a.no_extras:

@@ -98,6 +98,9 @@ typedef struct {
                           iterations (0: chosen from the lattice size) */
   int profile;         /* 1: time every stencil launch of a solve with CUDA
                           events (fills the ms_stencil fields of the stats) */
+  int dslash_variant;  /* stencil kernel: 0 = autotuned on first use (default);
+                          else R in {1, 2, 4, 8} right-hand sides per thread,
+                          plus 256 for the bulk-copy pipelined kernel */
 } blockcg_params;
 
 typedef struct {
@@ -110,6 +113,9 @@ typedef struct {
   double ms_stencil;       /* their summed device time (params.profile) */
   long long n_stencil_fine;  /* launches of the full-precision stencil (params.profile) */
   double ms_stencil_fine;    /* their summed device time (params.profile) */
+  double ms_gram;          /* params.profile: Gram partials + reductions (Sec. 5.4) */
+  double ms_stream;        /* params.profile: streaming block BLAS (Sec. 5.3) */
+  double ms_dense;         /* params.profile: N x N algebra on the device */
 } blockcg_stats;
 
 /* Fill *p with the defaults listed above. */

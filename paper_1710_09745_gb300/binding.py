@@ -35,7 +35,7 @@ ABI_SYMBOLS = [
 class Params(ct.Structure):
     _fields_ = [("max_iter", ct.c_int), ("ru_delta", ct.c_double), ("ru_every", ct.c_int),
                 ("prec", ct.c_int), ("antiperiodic_t", ct.c_int), ("check_every", ct.c_int),
-                ("profile", ct.c_int)]
+                ("profile", ct.c_int), ("dslash_variant", ct.c_int)]
 
 
 class Stats(ct.Structure):
@@ -43,7 +43,8 @@ class Stats(ct.Structure):
                 ("true_rel_res_max", ct.c_double), ("ms_total", ct.c_double),
                 ("launches", ct.c_longlong), ("n_stencil", ct.c_longlong),
                 ("ms_stencil", ct.c_double), ("n_stencil_fine", ct.c_longlong),
-                ("ms_stencil_fine", ct.c_double)]
+                ("ms_stencil_fine", ct.c_double), ("ms_gram", ct.c_double),
+                ("ms_stream", ct.c_double), ("ms_dense", ct.c_double)]
 
 
 class BlockCGError(RuntimeError):
@@ -108,7 +109,7 @@ class BlockCG:
     def __init__(self, dims, fat, lng, mass: float, prec: str = "f64", max_rhs: int = 16,
                  max_iter: int = 100000, ru_delta: float = 0.1, ru_every: int = 0,
                  antiperiodic_t: bool = False, check_every: int = 0, profile: bool = False,
-                 device=None):
+                 dslash_variant: int = 0, device=None):
         torch = _torch()
         L = load_library()
         self.lib = L
@@ -124,6 +125,7 @@ class BlockCG:
         p.max_iter, p.ru_delta, p.ru_every = int(max_iter), float(ru_delta), int(ru_every)
         p.prec, p.antiperiodic_t, p.check_every = PREC[prec], int(bool(antiperiodic_t)), int(check_every)
         p.profile = int(bool(profile))
+        p.dslash_variant = int(dslash_variant)
         self.params = p
         self.prec = prec
         h = ct.c_void_p()
@@ -239,7 +241,8 @@ class BlockCG:
         info = {"iters": st.iters, "reliable_updates": st.reliable_updates,
                 "true_rel_res_max": st.true_rel_res_max, "ms_total": st.ms_total, "status": rc,
                 "launches": st.launches, "n_stencil": st.n_stencil, "ms_stencil": st.ms_stencil,
-                "n_stencil_fine": st.n_stencil_fine, "ms_stencil_fine": st.ms_stencil_fine}
+                "n_stencil_fine": st.n_stencil_fine, "ms_stencil_fine": st.ms_stencil_fine,
+                "ms_gram": st.ms_gram, "ms_stream": st.ms_stream, "ms_dense": st.ms_dense}
         if rc not in (0, 6):
             self._check(rc)
         return X, info

@@ -23,6 +23,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -56,8 +57,10 @@ struct blockcg_ctx {
   };
   std::vector<cudaEvent_t> ev_pool;
   std::vector<Timed> ev_pending;
-  long long n_st[2];
-  double ms_st[2];
+  long long n_st[5];   // timed launches per category (see TL)
+  double ms_st[5];
+  // autotuned register tile of the stencil, keyed by kind * 128 + N
+  std::map<int, int> tuned_R;
 };
 
 namespace {
@@ -151,11 +154,14 @@ cudaEvent_t pool_event(blockcg_ctx* h) {
   return e;
 }
 
-// a stencil launch, event-timed when params.profile is set
-#define SL(fine_, call)                                       \
+// a launch of category cat, event-timed when params.profile is set:
+// 0 iteration stencil, 1 full-precision stencil, 2 Gram, 3 streaming BLAS,
+// 4 dense N x N
+enum { TC_STENCIL = 0, TC_STENCIL_FINE = 1, TC_GRAM = 2, TC_STREAM = 3, TC_DENSE = 4 };
+#define TL(cat_, call)                                        \
   do {                                                        \
     if (h->p.profile) {                                       \
-      blockcg_ctx::Timed t_{pool_event(h), pool_event(h), (fine_)}; \
+      blockcg_ctx::Timed t_{pool_event(h), pool_event(h), (cat_)}; \
       CK(cudaEventRecord(t_.a, h->stream));                   \
       KL(call);                                               \
       CK(cudaEventRecord(t_.b, h->stream));                   \
@@ -164,6 +170,7 @@ cudaEvent_t pool_event(blockcg_ctx* h) {
       KL(call);                                               \
     }                                                         \
   } while (0)
+#define SL(fine_, call) TL((fine_) ? TC_STENCIL_FINE : TC_STENCIL, call)
 
 // after a synchronisation: fold the finished stencil timings into the totals
 void drain_events(blockcg_ctx* h) {
@@ -181,12 +188,74 @@ void drain_events(blockcg_ctx* h) {
 
 void reset_instrumentation(blockcg_ctx* h) {
   h->launches = 0;
-  h->n_st[0] = h->n_st[1] = 0;
-  h->ms_st[0] = h->ms_st[1] = 0.0;
+  for (int i = 0; i < 5; ++i) {
+    h->n_st[i] = 0;
+    h->ms_st[i] = 0.0;
+  }
   h->ev_pending.clear();
 }
 
+void fill_stats(const blockcg_ctx* h, blockcg_stats* st) {
+  st->launches = h->launches;
+  st->n_stencil = h->n_st[0];
+  st->ms_stencil = h->ms_st[0];
+  st->n_stencil_fine = h->n_st[1];
+  st->ms_stencil_fine = h->ms_st[1];
+  st->ms_gram = h->ms_st[TC_GRAM];
+  st->ms_stream = h->ms_st[TC_STREAM];
+  st->ms_dense = h->ms_st[TC_DENSE];
+}
+
 int tile_R(int N) { return N >= 8 ? 4 : (N >= 2 ? 2 : 1); }
+
+// Register tile of the stencil for (kind, N): tuned once per handle by timing
+// every candidate R on the handle's own buffers (the register-tile tuning of
+// Sec. 5.2); in is read, out is scratch.  Falls back to tile_R on any error.
+int stencil_R(blockcg_ctx* h, FieldKind k, int N, const void* links, const void* in, void* out) {
+  if (h->p.dslash_variant) return h->p.dslash_variant;
+  const int key = (int)k * 128 + N;
+  auto it = h->tuned_R.find(key);
+  if (it != h->tuned_R.end()) return it->second;
+  int best = tile_R(N);
+  float best_ms = 1e30f;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    h->tuned_R[key] = best;
+    return best;
+  }
+  Gate g0{nullptr, GATE_ALWAYS};
+  const int cands[8] = {1, 2, 4, 8, 1 | DSLASH_TMA, 2 | DSLASH_TMA, 4 | DSLASH_TMA, 8 | DSLASH_TMA};
+  for (int R : cands) {
+    if ((R & 0xff) > 1 && (R & 0xff) > N) continue;
+    if (dslash(k, R, EPI_NONE, links, in, out, nullptr, nullptr, 0.0, h->g, 1, N, g0, h->stream) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaEventRecord(e0, h->stream);
+    for (int i = 0; i < 3; ++i)
+      dslash(k, R, EPI_NONE, links, in, out, nullptr, nullptr, 0.0, h->g, 1, N, g0, h->stream);
+    cudaEventRecord(e1, h->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) continue;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = R;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGetLastError();
+  h->tuned_R[key] = best;
+  return best;
+}
+
+int cached_R(const blockcg_ctx* h, FieldKind k, int N) {
+  if (h->p.dslash_variant) return h->p.dslash_variant;
+  auto it = h->tuned_R.find((int)k * 128 + N);
+  return it != h->tuned_R.end() ? it->second : tile_R(N);
+}
 
 blockcg_status check_ready(blockcg_ctx* h, int N) {
   if (!h) return BLOCKCG_ERR_ARG;
@@ -204,7 +273,7 @@ const void* op_links(const blockcg_ctx* h) { return h->links_sloppy; }
 // A applied to an internal even-site block: out = m^2 in - D_eo D_oe in
 blockcg_status apply_A_internal(blockcg_ctx* h, FieldKind k, const void* links, const void* in,
                                 void* tmp_odd, void* out, int N, Gate gate) {
-  int R = tile_R(N);
+  int R = stencil_R(h, k, N, links, in, tmp_odd);
   double m2 = h->mass * h->mass;
   KL(dslash(k, R, EPI_NONE, links, in, tmp_odd, nullptr, nullptr, 0.0, h->g, 1, N, gate, h->stream));
   KL(dslash(k, R, EPI_NORMAL, links, tmp_odd, out, in, nullptr, m2, h->g, 0, N, gate, h->stream));
@@ -229,18 +298,18 @@ int default_check_every(const blockcg_ctx* h, int N) {
 
 // R = B - A Y, thin QR, restart of Q and P (Algorithm 3; init: Algorithm 1 set-up)
 blockcg_status restart_block(blockcg_ctx* h, const Ws& w, int N, double tol, int init, Gate gate) {
-  int R = tile_R(N);
+  int R = cached_R(h, h->fine, N);
   double m2 = h->mass * h->mass;
   size_t nel = (size_t)h->g.Vh * N * 3;
   cudaStream_t s = h->stream;
-  KL(accumulate(h->fine, h->upd, w.Y, w.X, nel, gate, s));
+  TL(TC_STREAM, accumulate(h->fine, h->upd, w.Y, w.X, nel, gate, s));
   SL(1, dslash(h->fine, R, EPI_NONE, h->links_fine, w.Y, w.Tf, nullptr, nullptr, 0.0, h->g, 1, N, gate, s));
   SL(1, dslash(h->fine, R, EPI_RESIDUAL, h->links_fine, w.Tf, w.R, w.Y, w.B, m2, h->g, 0, N, gate, s));
-  KL(gram_partials(h->fine, w.R, w.R, N, h->g.Vh, 1, w.partials, w.nblocks, gate, s));
-  KL(gram_reduce(w.partials, w.nblocks, N, 1, mat(w, M_G, N), gate, s));
-  KL(dense_restart(mat(w, M_G, N), mat(w, M_C, N), mat(w, M_CPREV, N), mat(w, M_CINV, N),
+  TL(TC_GRAM, gram_partials(h->fine, w.R, w.R, N, h->g.Vh, 1, w.partials, w.nblocks, gate, s));
+  TL(TC_GRAM, gram_reduce(w.partials, w.nblocks, N, 1, mat(w, M_G, N), gate, s));
+  TL(TC_DENSE, dense_restart(mat(w, M_G, N), mat(w, M_C, N), mat(w, M_CPREV, N), mat(w, M_CINV, N),
                    mat(w, M_SHRU, N), w.bnorm, tol, init, N, w.st, gate, s));
-  KL(restart_update(h->fine, h->sloppy, w.R, w.Q, w.P, mat(w, M_CINV, N), mat(w, M_SHRU, N), init,
+  TL(TC_STREAM, restart_update(h->fine, h->sloppy, w.R, w.Q, w.P, mat(w, M_CINV, N), mat(w, M_SHRU, N), init,
                     N, h->g.Vh, gate, s));
   return BLOCKCG_OK;
 }
@@ -248,22 +317,22 @@ blockcg_status restart_block(blockcg_ctx* h, const Ws& w, int N, double tol, int
 blockcg_status iterate_block(blockcg_ctx* h, const Ws& w, int N, double tol) {
   Gate ga{w.st, GATE_ACTIVE};
   Gate gr{w.st, GATE_RU};
-  int R = tile_R(N);
+  int R = cached_R(h, h->sloppy, N);
   double m2 = h->mass * h->mass;
   cudaStream_t s = h->stream;
   FieldKind k = h->sloppy;
   SL(0, dslash(k, R, EPI_NONE, h->links_sloppy, w.P, w.Ts, nullptr, nullptr, 0.0, h->g, 1, N, ga, s));
   SL(0, dslash(k, R, EPI_NORMAL, h->links_sloppy, w.Ts, w.AP, w.P, nullptr, m2, h->g, 0, N, ga, s));
-  KL(gram_partials(k, w.P, w.AP, N, h->g.Vh, 1, w.partials, w.nblocks, ga, s));
-  KL(gram_reduce(w.partials, w.nblocks, N, 1, mat(w, M_H, N), ga, s));
-  KL(dense_beta(mat(w, M_H, N), mat(w, M_C, N), mat(w, M_BETA, N), mat(w, M_BC, N), N, w.st, ga, s));
-  KL(w_update(k, w.Q, w.AP, mat(w, M_BETA, N), N, h->g.Vh, ga, s));
-  KL(gram_partials(k, w.Q, w.Q, N, h->g.Vh, 1, w.partials, w.nblocks, ga, s));
-  KL(gram_reduce(w.partials, w.nblocks, N, 1, mat(w, M_G, N), ga, s));
+  TL(TC_GRAM, gram_partials(k, w.P, w.AP, N, h->g.Vh, 1, w.partials, w.nblocks, ga, s));
+  TL(TC_GRAM, gram_reduce(w.partials, w.nblocks, N, 1, mat(w, M_H, N), ga, s));
+  TL(TC_DENSE, dense_beta(mat(w, M_H, N), mat(w, M_C, N), mat(w, M_BETA, N), mat(w, M_BC, N), N, w.st, ga, s));
+  TL(TC_STREAM, w_update(k, w.Q, w.AP, mat(w, M_BETA, N), N, h->g.Vh, ga, s));
+  TL(TC_GRAM, gram_partials(k, w.Q, w.Q, N, h->g.Vh, 1, w.partials, w.nblocks, ga, s));
+  TL(TC_GRAM, gram_reduce(w.partials, w.nblocks, N, 1, mat(w, M_G, N), ga, s));
   QrStepParams qp{tol, h->p.ru_delta, h->p.ru_every, h->p.max_iter};
-  KL(dense_qr_step(mat(w, M_G, N), mat(w, M_C, N), mat(w, M_CPREV, N), mat(w, M_SINV, N),
+  TL(TC_DENSE, dense_qr_step(mat(w, M_G, N), mat(w, M_C, N), mat(w, M_CPREV, N), mat(w, M_SINV, N),
                    mat(w, M_SH, N), w.bnorm, qp, N, w.st, ga, s));
-  KL(bcg_update(k, h->upd, w.Q, w.P, w.X, mat(w, M_SINV, N), mat(w, M_BC, N), mat(w, M_SH, N), N,
+  TL(TC_STREAM, bcg_update(k, h->upd, w.Q, w.P, w.X, mat(w, M_SINV, N), mat(w, M_BC, N), mat(w, M_SH, N), N,
                 h->g.Vh, ga, s));
   return restart_block(h, w, N, tol, 0, gr);
 }
@@ -290,6 +359,8 @@ void blockcg_default_params(blockcg_params* p) {
   p->prec = BLOCKCG_PREC_F64;
   p->antiperiodic_t = 0;
   p->check_every = 0;
+  p->profile = 0;
+  p->dslash_variant = 0;
 }
 
 const char* blockcg_status_string(blockcg_status s) {
@@ -325,6 +396,10 @@ blockcg_status blockcg_create(blockcg_t* out, const int dims[4], double mass,
   if (prm.max_iter < 1 || prm.ru_delta < 0 || !(prm.ru_delta < 1) || prm.ru_every < 0 ||
       prm.check_every < 0 || (int)prm.prec < 0 || (int)prm.prec > 2)
     return BLOCKCG_ERR_ARG;
+  {
+    int r = prm.dslash_variant & ~DSLASH_TMA;
+    if (prm.dslash_variant != 0 && r != 1 && r != 2 && r != 4 && r != 8) return BLOCKCG_ERR_ARG;
+  }
   blockcg_ctx* h = new blockcg_ctx();
   for (int mu = 0; mu < 4; ++mu) {
     h->dims[mu] = dims[mu];
@@ -409,7 +484,7 @@ blockcg_status blockcg_dslash(blockcg_t h, const void* in, void* out, int n_rhs,
   FieldKind k = op_kind(h);
   Gate g0{nullptr, GATE_ALWAYS};
   CK(to_internal(k, (const double2*)in, w.Q, n_rhs, h->g.Vh, h->stream));
-  CK(dslash(k, tile_R(n_rhs), EPI_NONE, op_links(h), w.Q, w.AP, nullptr, nullptr, 0.0, h->g,
+  CK(dslash(k, stencil_R(h, k, n_rhs, op_links(h), w.Q, w.AP), EPI_NONE, op_links(h), w.Q, w.AP, nullptr, nullptr, 0.0, h->g,
             out_parity, n_rhs, g0, h->stream));
   CK(from_internal(k, w.AP, (double2*)out, n_rhs, h->g.Vh, h->stream));
   return BLOCKCG_OK;
@@ -502,6 +577,8 @@ blockcg_status blockcg_solve(blockcg_t h, const void* B, void* X, int n_rhs, dou
   KL(gram_partials(h->fine, w.B, w.B, N, h->g.Vh, 1, w.partials, w.nblocks, g0, s));
   KL(gram_reduce(w.partials, w.nblocks, N, 1, mat(w, M_G, N), g0, s));
   KL(dense_bnorm(mat(w, M_G, N), w.bnorm, N, w.st, s));
+  stencil_R(h, h->sloppy, N, h->links_sloppy, w.P, w.Ts);
+  stencil_R(h, h->fine, N, h->links_fine, w.Y, w.Tf);
   rc = restart_block(h, w, N, tol, 1, ga);
   if (rc) return rc;
   const int chunk = default_check_every(h, N);
@@ -543,11 +620,7 @@ blockcg_status blockcg_solve(blockcg_t h, const void* B, void* X, int n_rhs, dou
     stats->reliable_updates = hs.reliable_updates;
     stats->true_rel_res_max = hs.true_res_max;
     stats->ms_total = ms;
-    stats->launches = h->launches;
-    stats->n_stencil = h->n_st[0];
-    stats->ms_stencil = h->ms_st[0];
-    stats->n_stencil_fine = h->n_st[1];
-    stats->ms_stencil_fine = h->ms_st[1];
+    fill_stats(h, stats);
   }
   return result;
 }
@@ -593,8 +666,8 @@ blockcg_status blockcg_solve_cg(blockcg_t h, const void* B, void* X, int n_rhs, 
     KL(to_internal(fk, (const double2*)X + j * col, y, 1, Vh, s));
     CK(zero_field(xk, x, col, s));
     CK(zero_field(sk, p, col, s));
-    KL(gram_partials(fk, b, b, 1, Vh, 1, w.partials, w.nblocks, g0, s));
-    KL(gram_reduce(w.partials, w.nblocks, 1, 1, red, g0, s));
+    TL(TC_GRAM, gram_partials(fk, b, b, 1, Vh, 1, w.partials, w.nblocks, g0, s));
+    TL(TC_GRAM, gram_reduce(w.partials, w.nblocks, 1, 1, red, g0, s));
     KL(dense_bnorm(red, w.bnorm, 1, w.st, s));
     SolverStatus hs;
     memset(&hs, 0, sizeof(hs));
@@ -605,14 +678,14 @@ blockcg_status blockcg_solve_cg(blockcg_t h, const void* B, void* X, int n_rhs, 
         // reliable update: y += x, x = 0, rf = b - A y in full precision,
         // r = rf in the iteration's precision, then p = r + beta p with beta
         // from the true residual (p = r at the start)
-        KL(accumulate(fk, xk, y, x, col, ga, s));
+        TL(TC_STREAM, accumulate(fk, xk, y, x, col, ga, s));
         SL(1, dslash(fk, 1, EPI_NONE, h->links_fine, y, tf, nullptr, nullptr, 0.0, h->g, 1, 1, ga, s));
         SL(1, dslash(fk, 1, EPI_RESIDUAL, h->links_fine, tf, rf, y, b, m2, h->g, 0, 1, ga, s));
-        KL(gram_partials(fk, rf, rf, 1, Vh, 1, w.partials, w.nblocks, ga, s));
-        KL(gram_reduce(w.partials, w.nblocks, 1, 1, red, ga, s));
-        KL(cg_restart_check(red, rr, beta, w.bnorm, tol, n_restart == 0, w.st, s));
-        KL(convert_field(fk, sk, rf, r, col, ga, s));
-        KL(cg_xpay(sk, p, r, beta, Vh, ga, s));
+        TL(TC_GRAM, gram_partials(fk, rf, rf, 1, Vh, 1, w.partials, w.nblocks, ga, s));
+        TL(TC_GRAM, gram_reduce(w.partials, w.nblocks, 1, 1, red, ga, s));
+        TL(TC_DENSE, cg_restart_check(red, rr, beta, w.bnorm, tol, n_restart == 0, w.st, s));
+        TL(TC_STREAM, convert_field(fk, sk, rf, r, col, ga, s));
+        TL(TC_STREAM, cg_xpay(sk, p, r, beta, Vh, ga, s));
         restart = false;
         ++n_restart;
       }
@@ -630,13 +703,13 @@ blockcg_status blockcg_solve_cg(blockcg_t h, const void* B, void* X, int n_rhs, 
       for (int i = 0; i < n; ++i) {
         SL(0, dslash(sk, 1, EPI_NONE, h->links_sloppy, p, t, nullptr, nullptr, 0.0, h->g, 1, 1, gi, s));
         SL(0, dslash(sk, 1, EPI_NORMAL, h->links_sloppy, t, Ap, p, nullptr, m2, h->g, 0, 1, gi, s));
-        KL(gram_partials(sk, p, Ap, 1, Vh, 1, w.partials, w.nblocks, gi, s));
-        KL(gram_reduce(w.partials, w.nblocks, 1, 1, red, gi, s));
-        KL(cg_scalar_alpha(red, rr, alpha, w.st, gi, s));
-        KL(cg_axpy_norm(sk, xk, x, r, p, Ap, alpha, w.partials, nb_cg, Vh, gi, s));
-        KL(gram_reduce(w.partials, nb_cg, 1, 1, red + 1, gi, s));
-        KL(cg_scalar_beta(red + 1, rr, beta, w.bnorm, tol, h->p.ru_delta, w.st, gi, s));
-        KL(cg_xpay(sk, p, r, beta, Vh, gi, s));
+        TL(TC_GRAM, gram_partials(sk, p, Ap, 1, Vh, 1, w.partials, w.nblocks, gi, s));
+        TL(TC_GRAM, gram_reduce(w.partials, w.nblocks, 1, 1, red, gi, s));
+        TL(TC_DENSE, cg_scalar_alpha(red, rr, alpha, w.st, gi, s));
+        TL(TC_STREAM, cg_axpy_norm(sk, xk, x, r, p, Ap, alpha, w.partials, nb_cg, Vh, gi, s));
+        TL(TC_GRAM, gram_reduce(w.partials, nb_cg, 1, 1, red + 1, gi, s));
+        TL(TC_DENSE, cg_scalar_beta(red + 1, rr, beta, w.bnorm, tol, h->p.ru_delta, w.st, gi, s));
+        TL(TC_STREAM, cg_xpay(sk, p, r, beta, Vh, gi, s));
       }
       launched += n;
     }
@@ -645,7 +718,7 @@ blockcg_status blockcg_solve_cg(blockcg_t h, const void* B, void* X, int n_rhs, 
     if (hs.error) result = status_to_result(h, hs);
     else if (!hs.done) {
       // max_iter: fold the update into y for the returned iterate
-      KL(accumulate(fk, xk, y, x, col, g0, s));
+      TL(TC_STREAM, accumulate(fk, xk, y, x, col, g0, s));
       result = fail(h, BLOCKCG_ERR_NOT_CONVERGED, "max_iter reached");
     }
     if (hs.true_res_max > worst) worst = hs.true_res_max;
@@ -663,11 +736,7 @@ blockcg_status blockcg_solve_cg(blockcg_t h, const void* B, void* X, int n_rhs, 
     stats->reliable_updates = total_ru;
     stats->true_rel_res_max = worst;
     stats->ms_total = ms;
-    stats->launches = h->launches;
-    stats->n_stencil = h->n_st[0];
-    stats->ms_stencil = h->ms_st[0];
-    stats->n_stencil_fine = h->n_st[1];
-    stats->ms_stencil_fine = h->ms_st[1];
+    fill_stats(h, stats);
   }
   return result;
 }
@@ -687,7 +756,7 @@ blockcg_status blockcg_bench_dslash(blockcg_t h, int n_rhs, int fine, int reps,
   size_t nel = (size_t)h->g.Vh * N * 3;
   CK(cudaMemsetAsync(in, 0, nel * elem_bytes(k), s));
   Gate g0{nullptr, GATE_ALWAYS};
-  int R = tile_R(N);
+  int R = stencil_R(h, k, N, links, in, out);
   // one untimed launch, then the timed ones
   KL(dslash(k, R, EPI_NONE, links, in, out, nullptr, nullptr, 0.0, h->g, 1, N, g0, s));
   cudaEvent_t e0, e1;

@@ -1,5 +1,6 @@
 // Block BLAS on L x N block vectors (L = 3 Vh complex rows, N right-hand
-// sides), stored site-major [site][rhs][colour].
+// sides), stored site-major [site][colour][rhs] (row = (site, colour), the N
+// columns of a row contiguous).
 //
 //  * Reduction multi-BLAS (Sec. 5.4): K = X^dag Y as per-CTA partial sums
 //    (gram_partials) followed by a deterministic fixed-order FP64 reduction
@@ -19,6 +20,12 @@
 namespace bcg {
 
 static inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+// grid for grid-stride kernels: enough CTAs to fill the GPU, never a huge
+// grid of trivial CTAs (a gated-off launch then costs a few microseconds)
+static inline unsigned gcap(long long n, int t, unsigned cap = 152 * 8) {
+  unsigned b = nblk(n, t);
+  return b < cap ? (b ? b : 1) : cap;
+}
 
 // ------------------------------------------------------------ layout ----
 template <class S>
@@ -27,10 +34,10 @@ __global__ void k_to_internal(const double2* __restrict__ user, typename S::elem
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   long long total = (long long)Vh * N * 3;
   if (idx >= total) return;
-  int c = (int)(idx % 3);
-  long long t = idx / 3;
-  int j = (int)(t % N);
-  long long site = t / N;
+  int j = (int)(idx % N);
+  long long t = idx / N;
+  int c = (int)(t % 3);
+  long long site = t / 3;
   in[idx] = S::from_double2(user[((long long)j * Vh + site) * 3 + c]);
 }
 
@@ -40,10 +47,10 @@ __global__ void k_from_internal(const typename S::elem* __restrict__ in, double2
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   long long total = (long long)Vh * N * 3;
   if (idx >= total) return;
-  int c = (int)(idx % 3);
-  long long t = idx / 3;
-  int j = (int)(t % N);
-  long long site = t / N;
+  int j = (int)(idx % N);
+  long long t = idx / N;
+  int c = (int)(t % 3);
+  long long site = t / 3;
   user[((long long)j * Vh + site) * 3 + c] = S::to_double2(in[idx]);
 }
 
@@ -91,7 +98,6 @@ cudaError_t copy_field(void* dst, const void* src, size_t bytes, cudaStream_t s)
 
 // -------------------------------------------------------------- Gram ----
 static constexpr int GRAM_THREADS = 256;
-static constexpr int GRAM_MAX_EPT = 16;  // entries per thread: 64*64 / 256
 
 __host__ __device__ inline int gram_entries(int N, int herm) { return herm ? N * (N + 1) / 2 : N * N; }
 
@@ -120,74 +126,108 @@ int gram_blocks(int N, int rows) {
   return b;
 }
 
-template <class S>
+// Register-blocked Gram: a CTA stages TS sites of X and Y in shared memory
+// (coalesced 128-bit loads of whole sites), then each thread accumulates a
+// B x B block of entries (i, j) over the rows of its row group, so every
+// value read from shared memory feeds B complex multiply-adds.  Hermitian
+// Grams visit only the blocks on and above the block diagonal (Sec. 5.4).
+// The CTA walks the tiles grid-stride and writes one N x N partial (row-major
+// [i][j], only the blocks it computed) for the fixed-order reduction.
+template <class S, int B>
 __global__ void __launch_bounds__(GRAM_THREADS)
     k_gram(const typename S::elem* __restrict__ X, const typename S::elem* __restrict__ Y, int N,
-           int Vh, int herm, double2* __restrict__ partials, Gate gate) {
+           int Vh, int herm, int same, int TS, double2* __restrict__ partials, Gate gate) {
   using C = typename S::comp;
   using real = typename C::real;
   using acc = typename C::acc;
-  __shared__ double2 red[GRAM_THREADS];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   if (gate_closed(gate)) return;
-  const int E = gram_entries(N, herm);
+  cpx<real>* sX = reinterpret_cast<cpx<real>*>(smem_raw);
+  cpx<real>* sY = same ? sX : sX + TS * N * 3;
   const int tid = threadIdx.x;
-  const int G = (E >= GRAM_THREADS) ? 1 : (GRAM_THREADS / E);  // row groups
-  const int grp = tid / (E < GRAM_THREADS ? E : GRAM_THREADS);
-  const long long rows = 3LL * Vh;
-  const long long rpb = (rows + gridDim.x - 1) / gridDim.x;
-  const long long r0 = (long long)blockIdx.x * rpb;
-  const long long r1 = min(rows, r0 + rpb);
-
-  int ne = 0;
-  int ei[GRAM_MAX_EPT], ej[GRAM_MAX_EPT];
-  cpx<acc> a[GRAM_MAX_EPT];
-  if (grp < G) {
-    int e0 = (E < GRAM_THREADS) ? (tid % E) : tid;
-    for (int e = e0; e < E && ne < GRAM_MAX_EPT; e += GRAM_THREADS) {
-      entry_ij(e, N, herm, ei[ne], ej[ne]);
-      a[ne] = czero<C>();
-      ++ne;
+  const int nb = (N + B - 1) / B;
+  const int NB = herm ? nb * (nb + 1) / 2 : nb * nb;
+  const int G = NB >= GRAM_THREADS ? 1 : GRAM_THREADS / NB;
+  const int grp = tid / NB;
+  const int blk = tid - grp * NB;
+  const bool active = grp < G && blk < NB;
+  int bi = 0, bj = 0;
+  if (herm) {
+    int r = 0, off = 0;
+    while (off + (nb - r) <= blk) {
+      off += nb - r;
+      ++r;
     }
-    for (long long r = r0 + grp; r < r1; r += G) {
-      long long site = r / 3;
-      int col = (int)(r - site * 3);
-      const typename S::elem* xr = X + site * N * 3 + col;
-      const typename S::elem* yr = Y + site * N * 3 + col;
-#pragma unroll 4
-      for (int q = 0; q < GRAM_MAX_EPT; ++q) {
-        if (q < ne) {
-          cpx<real> xv = S::load(xr + ei[q] * 3);
-          cpx<real> yv = S::load(yr + ej[q] * 3);
-          cmac_conj<C>(a[q], xv, yv);
+    bi = r;
+    bj = r + (blk - off);
+  } else {
+    bi = blk / nb;
+    bj = blk - bi * nb;
+  }
+  const int i0 = bi * B, j0 = bj * B;
+  cpx<acc> a[B][B];
+#pragma unroll
+  for (int u = 0; u < B; ++u)
+#pragma unroll
+    for (int v = 0; v < B; ++v) a[u][v] = czero<C>();
+
+  for (long long tile = blockIdx.x; tile * TS < Vh; tile += gridDim.x) {
+    const long long site0 = tile * TS;
+    const int ns = (int)min((long long)TS, (long long)Vh - site0);
+    const int nel = ns * N * 3;
+    const long long base = site0 * N * 3;
+    __syncthreads();
+    for (int idx = tid; idx < nel; idx += GRAM_THREADS) {
+      sX[idx] = S::load(X + base + idx);
+      if (!same) sY[idx] = S::load(Y + base + idx);
+    }
+    __syncthreads();
+    if (active) {
+      for (int r = grp; r < ns * 3; r += G) {
+        const int s = r / 3;
+        const int c = r - s * 3;
+        const cpx<real>* xr = sX + (s * 3 + c) * N;
+        const cpx<real>* yr = sY + (s * 3 + c) * N;
+        cpx<real> xv[B], yv[B];
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+          xv[u] = (i0 + u < N) ? xr[i0 + u] : cpx<real>{C::rzero(), C::rzero()};
+          yv[u] = (j0 + u < N) ? yr[j0 + u] : cpx<real>{C::rzero(), C::rzero()};
         }
+#pragma unroll
+        for (int u = 0; u < B; ++u)
+#pragma unroll
+          for (int v = 0; v < B; ++v) cmac_conj<C>(a[u][v], xv[u], yv[v]);
       }
     }
   }
-  double2* out = partials + (long long)blockIdx.x * E;
-  if (G == 1) {
-    for (int q = 0; q < ne; ++q) {
-      int e = tid + q * GRAM_THREADS;
-      out[e] = make_double2(C::to_double(a[q].re), C::to_double(a[q].im));
-    }
-    return;
-  }
-  // several row groups: reduce them through shared memory (one entry each)
-  double2 v = make_double2(0.0, 0.0);
-  if (grp < G && ne > 0) v = make_double2(C::to_double(a[0].re), C::to_double(a[0].im));
-  red[tid] = v;
+  // reduce the row groups of each block through shared memory, one entry of
+  // the B x B block at a time, and write this CTA's partial
   __syncthreads();
-  if (tid < E) {
-    double2 sacc = red[tid];
-    for (int g2 = 1; g2 < G; ++g2) {
-      double2 w = red[g2 * E + tid];
-      sacc.x += w.x;
-      sacc.y += w.y;
+  double2* red = reinterpret_cast<double2*>(smem_raw);
+  double2* out = partials + (long long)blockIdx.x * N * N;
+#pragma unroll
+  for (int u = 0; u < B; ++u)
+#pragma unroll
+    for (int v = 0; v < B; ++v) {
+      red[tid] = active ? make_double2(C::to_double(a[u][v].re), C::to_double(a[u][v].im))
+                        : make_double2(0.0, 0.0);
+      __syncthreads();
+      if (tid < NB) {
+        double2 sacc = red[tid];
+        for (int g2 = 1; g2 < G; ++g2) {
+          double2 w = red[g2 * NB + tid];
+          sacc.x += w.x;
+          sacc.y += w.y;
+        }
+        if (i0 + u < N && j0 + v < N) out[(i0 + u) * N + (j0 + v)] = sacc;
+      }
+      __syncthreads();
     }
-    out[tid] = sacc;
-  }
 }
 
-// warp per entry; fixed summation order -> deterministic
+// warp per entry of the result (upper triangle when Hermitian); fixed
+// summation order over the per-CTA partials -> deterministic
 __global__ void k_gram_reduce(const double2* __restrict__ partials, int nblocks, int N, int herm,
                               double2* __restrict__ out, Gate gate) {
   if (gate_closed(gate)) return;
@@ -195,9 +235,11 @@ __global__ void k_gram_reduce(const double2* __restrict__ partials, int nblocks,
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (warp >= E) return;
+  int i, j;
+  entry_ij(warp, N, herm, i, j);
   double sx = 0.0, sy = 0.0;
   for (int b = lane; b < nblocks; b += 32) {
-    double2 v = partials[(long long)b * E + warp];
+    double2 v = partials[(long long)b * N * N + i * N + j];
     sx += v.x;
     sy += v.y;
   }
@@ -206,29 +248,44 @@ __global__ void k_gram_reduce(const double2* __restrict__ partials, int nblocks,
     sy += __shfl_down_sync(0xffffffffu, sy, o);
   }
   if (lane == 0) {
-    int i, j;
-    entry_ij(warp, N, herm, i, j);
-    out[i * N + j] = make_double2(sx, sy);
+    out[i * N + j] = make_double2(sx, (herm && i == j) ? 0.0 : sy);
     if (herm && i != j) out[j * N + i] = make_double2(sx, -sy);
-    if (herm && i == j) out[i * N + i] = make_double2(sx, 0.0);
   }
+}
+
+template <class S, int B>
+static void launch_gram_b(const void* X, const void* Y, int N, int Vh, int herm, double2* partials,
+                          int nblocks, Gate gate, cudaStream_t s) {
+  using real = typename S::comp::real;
+  int TS = 256 / N;
+  if (TS < 1) TS = 1;
+  int same = (X == Y);
+  size_t tiles = (same ? 1 : 2) * (size_t)TS * N * 3 * sizeof(cpx<real>);
+  size_t red = GRAM_THREADS * sizeof(double2);
+  size_t sm = tiles > red ? tiles : red;
+  cudaFuncSetAttribute(k_gram<S, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_gram<S, B><<<nblocks, GRAM_THREADS, sm, s>>>((const typename S::elem*)X,
+                                                (const typename S::elem*)Y, N, Vh, herm, same, TS,
+                                                partials, gate);
+}
+
+template <class S>
+static void launch_gram(const void* X, const void* Y, int N, int Vh, int herm, double2* partials,
+                        int nblocks, Gate gate, cudaStream_t s) {
+  if (N == 1)
+    launch_gram_b<S, 1>(X, Y, N, Vh, herm, partials, nblocks, gate, s);
+  else if (N <= 16)
+    launch_gram_b<S, 2>(X, Y, N, Vh, herm, partials, nblocks, gate, s);
+  else
+    launch_gram_b<S, 4>(X, Y, N, Vh, herm, partials, nblocks, gate, s);
 }
 
 cudaError_t gram_partials(FieldKind k, const void* X, const void* Y, int N, int Vh, int hermitian,
                           double2* partials, int nblocks, Gate gate, cudaStream_t s) {
   switch (k) {
-    case FK_DF:
-      k_gram<StoreDF><<<nblocks, GRAM_THREADS, 0, s>>>((const float4*)X, (const float4*)Y, N, Vh,
-                                                      hermitian, partials, gate);
-      break;
-    case FK_F32:
-      k_gram<StoreF32><<<nblocks, GRAM_THREADS, 0, s>>>((const float2*)X, (const float2*)Y, N, Vh,
-                                                       hermitian, partials, gate);
-      break;
-    case FK_F64:
-      k_gram<StoreF64><<<nblocks, GRAM_THREADS, 0, s>>>((const double2*)X, (const double2*)Y, N,
-                                                       Vh, hermitian, partials, gate);
-      break;
+    case FK_DF: launch_gram<StoreDF>(X, Y, N, Vh, hermitian, partials, nblocks, gate, s); break;
+    case FK_F32: launch_gram<StoreF32>(X, Y, N, Vh, hermitian, partials, nblocks, gate, s); break;
+    case FK_F64: launch_gram<StoreF64>(X, Y, N, Vh, hermitian, partials, nblocks, gate, s); break;
   }
   return cudaGetLastError();
 }
@@ -253,9 +310,13 @@ __device__ __forceinline__ void stage_coef(cpx<typename C::real>* dst, const dou
 }
 
 // ---------------------------------------------------- W = Q - AP beta ----
+// thread = (row, group of WJB consecutive columns): each AP value read feeds
+// WJB outputs; beta staged once per CTA in shared memory
+static constexpr int WJB = 4;
 template <class S>
-__global__ void k_w_update(typename S::elem* __restrict__ Q, const typename S::elem* __restrict__ AP,
-                           const double2* __restrict__ beta, int N, int Vh, Gate gate) {
+__global__ void __launch_bounds__(256)
+    k_w_update(typename S::elem* __restrict__ Q, const typename S::elem* __restrict__ AP,
+               const double2* __restrict__ beta, int N, int Vh, Gate gate) {
   using C = typename S::comp;
   using real = typename C::real;
   using acc = typename C::acc;
@@ -264,48 +325,58 @@ __global__ void k_w_update(typename S::elem* __restrict__ Q, const typename S::e
   if (gate_closed(gate)) return;
   stage_coef<C>(sb, beta, N, 0, N, N);
   __syncthreads();
-  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // (site, j, colour)
-  long long total = (long long)Vh * N * 3;
-  if (idx >= total) return;
-  int c = (int)(idx % 3);
-  long long t = idx / 3;
-  int j = (int)(t % N);
-  long long site = t / N;
-  const typename S::elem* apr = AP + site * N * 3 + c;
-  cpx<acc> w = cacc_from<C>(S::load_nc(Q + idx));
-  for (int i = 0; i < N; ++i) {
-    cpx<real> ap = S::load(apr + i * 3);
-    cpx<real> b = sb[i * N + j];
-    cpx<real> nb = {b.re, b.im};
-    // w -= ap * b
-    C::msub(w.re, ap.re, nb.re);
-    C::mac(w.re, ap.im, nb.im);
-    C::msub(w.im, ap.re, nb.im);
-    C::msub(w.im, ap.im, nb.re);
+  const int ng = (N + WJB - 1) / WJB;
+  const long long total = (long long)Vh * 3 * ng;  // (row, column group)
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long row = idx / ng;
+    const int j0 = (int)(idx - row * ng) * WJB;
+    const typename S::elem* apr = AP + row * N;
+    typename S::elem* qr = Q + row * N;
+    cpx<acc> w[WJB];
+#pragma unroll
+    for (int u = 0; u < WJB; ++u)
+      w[u] = (j0 + u < N) ? cacc_from<C>(S::load_nc(qr + j0 + u)) : czero<C>();
+    for (int i = 0; i < N; ++i) {
+      const cpx<real> ap = S::load(apr + i);
+#pragma unroll
+      for (int u = 0; u < WJB; ++u) {
+        if (j0 + u < N) {
+          const cpx<real> bb = sb[i * N + j0 + u];
+          // w -= ap * bb
+          C::msub(w[u].re, ap.re, bb.re);
+          C::mac(w[u].re, ap.im, bb.im);
+          C::msub(w[u].im, ap.re, bb.im);
+          C::msub(w[u].im, ap.im, bb.re);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < WJB; ++u)
+      if (j0 + u < N) S::store(qr + j0 + u, cfin<C>(w[u]));
   }
-  S::store(Q + idx, cfin<C>(w));
 }
 
 cudaError_t w_update(FieldKind k, void* Q, const void* AP, const double2* beta, int N, int Vh,
                      Gate gate, cudaStream_t s) {
-  long long total = (long long)Vh * N * 3;
+  long long total = (long long)Vh * 3 * ((N + WJB - 1) / WJB);
   int th = 256;
   switch (k) {
     case FK_DF: {
       size_t sm = (size_t)N * N * sizeof(cpx<df>);
       cudaFuncSetAttribute(k_w_update<StoreDF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      k_w_update<StoreDF><<<nblk(total, th), th, sm, s>>>((float4*)Q, (const float4*)AP, beta, N, Vh, gate);
+      k_w_update<StoreDF><<<gcap(total, th, 152 * 8), th, sm, s>>>((float4*)Q, (const float4*)AP, beta, N, Vh, gate);
       break;
     }
     case FK_F32: {
       size_t sm = (size_t)N * N * sizeof(cpx<float>);
-      k_w_update<StoreF32><<<nblk(total, th), th, sm, s>>>((float2*)Q, (const float2*)AP, beta, N, Vh, gate);
+      k_w_update<StoreF32><<<gcap(total, th, 152 * 8), th, sm, s>>>((float2*)Q, (const float2*)AP, beta, N, Vh, gate);
       break;
     }
     case FK_F64: {
       size_t sm = (size_t)N * N * sizeof(cpx<double>);
       cudaFuncSetAttribute(k_w_update<StoreF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      k_w_update<StoreF64><<<nblk(total, th), th, sm, s>>>((double2*)Q, (const double2*)AP, beta, N, Vh, gate);
+      k_w_update<StoreF64><<<gcap(total, th, 152 * 8), th, sm, s>>>((double2*)Q, (const double2*)AP, beta, N, Vh, gate);
       break;
     }
   }
@@ -328,7 +399,9 @@ static TileCfg tile_cfg(int N, size_t real_cplx_bytes, int n_tiles, int n_coefs)
   return {TS, JT};
 }
 
-template <class SS, class XS>
+// Each thread produces JB consecutive output columns j of one row (site,
+// colour), so every W and P value read from shared memory feeds JB outputs.
+template <class SS, class XS, int JB>
 __global__ void __launch_bounds__(256)
     k_bcg_update(typename SS::elem* __restrict__ Q, typename SS::elem* __restrict__ P,
                  typename XS::elem* __restrict__ X, const double2* __restrict__ Sinv,
@@ -346,50 +419,84 @@ __global__ void __launch_bounds__(256)
   cpx<real>* sA = sP + TS * N * 3;  // Sinv chunk  [N][JT]
   cpx<real>* sB = sA + N * JT;      // BC chunk
   cpx<real>* sC = sB + N * JT;      // SH chunk
-  const long long site0 = (long long)blockIdx.x * TS;
-  const int ns = (int)min((long long)TS, (long long)Vh - site0);
-  const long long base = site0 * N * 3;
-  const int nel = ns * N * 3;
-  for (int idx = threadIdx.x; idx < nel; idx += blockDim.x) {
-    sW[idx] = SS::load_nc(Q + base + idx);
-    sP[idx] = SS::load_nc(P + base + idx);
+  const bool one_chunk = (JT >= N);
+  if (one_chunk) {  // all coefficients fit: stage them once per CTA
+    stage_coef<C>(sA, Sinv, N, 0, N, JT);
+    stage_coef<C>(sB, BC, N, 0, N, JT);
+    if (!keepP) stage_coef<C>(sC, SH, N, 0, N, JT);
   }
-  for (int j0 = 0; j0 < N; j0 += JT) {
-    const int jn = min(JT, N - j0);
+  for (long long tile = blockIdx.x; tile * TS < Vh; tile += gridDim.x) {
+    const long long site0 = tile * TS;
+    const int ns = (int)min((long long)TS, (long long)Vh - site0);
+    const long long base = site0 * N * 3;
+    const int nel = ns * N * 3;
     __syncthreads();
-    stage_coef<C>(sA, Sinv, N, j0, jn, JT);
-    stage_coef<C>(sB, BC, N, j0, jn, JT);
-    if (!keepP) stage_coef<C>(sC, SH, N, j0, jn, JT);
-    __syncthreads();
-    const int nout = ns * jn * 3;
-    for (int o = threadIdx.x; o < nout; o += blockDim.x) {
-      const int sidx = o / (jn * 3);
-      const int rem = o - sidx * jn * 3;
-      const int jj = rem / 3;
-      const int c = rem - jj * 3;
-      const int j = j0 + jj;
-      const cpx<real>* w = sW + sidx * N * 3 + c;
-      const cpx<real>* p = sP + sidx * N * 3 + c;
-      // Q = W S^-1 (S^-1 upper triangular)
-      cpx<acc> q = czero<C>();
-      for (int i = 0; i <= j; ++i) cmac<C>(q, w[i * 3], sA[i * JT + jj]);
-      cpx<real> qn = cfin<C>(q);
-      // X += P (beta C)
-      cpx<acc> x = czero<C>();
-      for (int i = 0; i < N; ++i) cmac<C>(x, p[i * 3], sB[i * JT + jj]);
-      cpx<real> xs = cfin<C>(x);
-      const long long gi = base + ((long long)sidx * N + j) * 3 + c;
-      cpx<typename CX::real> xo = XS::load_nc(X + gi);
-      cpx<typename CX::acc> xa = cacc_from<CX>(xo);
-      CX::add(xa.re, conv<CX, C>::f(xs.re));
-      CX::add(xa.im, conv<CX, C>::f(xs.im));
-      XS::store(X + gi, cfin<CX>(xa));
-      SS::store(Q + gi, qn);
-      if (!keepP) {
-        // P = Q + P S^dag (S^dag lower triangular)
-        cpx<acc> pn = cacc_from<C>(qn);
-        for (int i = j; i < N; ++i) cmac<C>(pn, p[i * 3], sC[i * JT + jj]);
-        SS::store(P + gi, cfin<C>(pn));
+    for (int idx = threadIdx.x; idx < nel; idx += blockDim.x) {
+      sW[idx] = SS::load_nc(Q + base + idx);
+      sP[idx] = SS::load_nc(P + base + idx);
+    }
+    for (int j0 = 0; j0 < N; j0 += JT) {
+      const int jn = min(JT, N - j0);
+      if (!one_chunk) {
+        __syncthreads();
+        stage_coef<C>(sA, Sinv, N, j0, jn, JT);
+        stage_coef<C>(sB, BC, N, j0, jn, JT);
+        if (!keepP) stage_coef<C>(sC, SH, N, j0, jn, JT);
+      }
+      __syncthreads();
+      const int ng = (jn + JB - 1) / JB;  // column groups
+      const int nout = ns * 3 * ng;
+      for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+        const int row = o / ng;  // (site, colour)
+        const int jg = o - row * ng;
+        const int jj0 = jg * JB;
+        const cpx<real>* w = sW + row * N;
+        const cpx<real>* p = sP + row * N;
+        cpx<acc> q[JB], x[JB], pn[JB];
+#pragma unroll
+        for (int u = 0; u < JB; ++u) {
+          q[u] = czero<C>();
+          x[u] = czero<C>();
+          pn[u] = czero<C>();
+        }
+        const int jmax = j0 + min(jj0 + JB, jn) - 1;  // last column of the group
+        for (int i = 0; i < N; ++i) {
+          const cpx<real> wi = w[i];
+          const cpx<real> pi = p[i];
+#pragma unroll
+          for (int u = 0; u < JB; ++u) {
+            const int jj = jj0 + u;
+            if (jj < jn) {
+              const int j = j0 + jj;
+              if (i <= j) cmac<C>(q[u], wi, sA[i * JT + jj]);       // Q = W S^-1
+              cmac<C>(x[u], pi, sB[i * JT + jj]);                    // X += P beta C
+              if (!keepP && i >= j) cmac<C>(pn[u], pi, sC[i * JT + jj]);  // P S^dag
+            }
+          }
+          (void)jmax;
+        }
+        const long long gbase = base + (long long)row * N + j0;
+#pragma unroll
+        for (int u = 0; u < JB; ++u) {
+          const int jj = jj0 + u;
+          if (jj < jn) {
+            const long long gi = gbase + jj;
+            cpx<real> qn = cfin<C>(q[u]);
+            cpx<real> xs = cfin<C>(x[u]);
+            cpx<typename CX::acc> xa = cacc_from<CX>(XS::load_nc(X + gi));
+            CX::add(xa.re, conv<CX, C>::f(xs.re));
+            CX::add(xa.im, conv<CX, C>::f(xs.im));
+            XS::store(X + gi, cfin<CX>(xa));
+            SS::store(Q + gi, qn);
+            if (!keepP) {
+              // P = Q + P S^dag
+              cpx<acc> pf = pn[u];
+              C::add(pf.re, qn.re);
+              C::add(pf.im, qn.im);
+              SS::store(P + gi, cfin<C>(pf));
+            }
+          }
+        }
       }
     }
   }
@@ -402,9 +509,9 @@ static cudaError_t launch_bcg_update(void* Q, void* P, void* X, const double2* S
   using real = typename SS::comp::real;
   TileCfg t = tile_cfg(N, sizeof(cpx<real>), 2, 3);
   size_t sm = ((size_t)2 * t.TS * N * 3 + 3 * (size_t)N * t.JT) * sizeof(cpx<real>);
-  cudaFuncSetAttribute(k_bcg_update<SS, XS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  unsigned blocks = nblk(Vh, t.TS);
-  k_bcg_update<SS, XS><<<blocks, 256, sm, s>>>((typename SS::elem*)Q, (typename SS::elem*)P,
+  cudaFuncSetAttribute(k_bcg_update<SS, XS, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  unsigned blocks = gcap(Vh, t.TS, 152 * 8);
+  k_bcg_update<SS, XS, 4><<<blocks, 256, sm, s>>>((typename SS::elem*)Q, (typename SS::elem*)P,
                                                (typename XS::elem*)X, Sinv, BC, SH, N, Vh, t.TS,
                                                t.JT, gate);
   return cudaGetLastError();
@@ -440,40 +547,43 @@ __global__ void __launch_bounds__(256)
   cpx<rreal>* sA = sR + TS * N * 3;                                 // Cinv chunk (fine)
   cpx<real>* sP = reinterpret_cast<cpx<real>*>(sA + N * JT);       // P tile (sloppy)
   cpx<real>* sC = sP + TS * N * 3;                                  // SH chunk (sloppy)
-  const long long site0 = (long long)blockIdx.x * TS;
-  const int ns = (int)min((long long)TS, (long long)Vh - site0);
-  const long long base = site0 * N * 3;
-  const int nel = ns * N * 3;
-  for (int idx = threadIdx.x; idx < nel; idx += blockDim.x) {
-    sR[idx] = RS::load_nc(R + base + idx);
-    if (!init) sP[idx] = SS::load_nc(P + base + idx);
-  }
-  for (int j0 = 0; j0 < N; j0 += JT) {
-    const int jn = min(JT, N - j0);
+  for (long long tile = blockIdx.x; tile * TS < Vh; tile += gridDim.x) {
+    const long long site0 = tile * TS;
+    const int ns = (int)min((long long)TS, (long long)Vh - site0);
+    const long long base = site0 * N * 3;
+    const int nel = ns * N * 3;
     __syncthreads();
-    stage_coef<CR>(sA, Cinv, N, j0, jn, JT);
-    if (!init) stage_coef<C>(sC, SH, N, j0, jn, JT);
-    __syncthreads();
-    const int nout = ns * jn * 3;
-    for (int o = threadIdx.x; o < nout; o += blockDim.x) {
-      const int sidx = o / (jn * 3);
-      const int rem = o - sidx * jn * 3;
-      const int jj = rem / 3;
-      const int c = rem - jj * 3;
-      const int j = j0 + jj;
-      const cpx<rreal>* r = sR + sidx * N * 3 + c;
-      cpx<typename CR::acc> q = czero<CR>();
-      for (int i = 0; i <= j; ++i) cmac<CR>(q, r[i * 3], sA[i * JT + jj]);
-      cpx<rreal> qf = cfin<CR>(q);
-      cpx<real> qn = {conv<C, CR>::f(qf.re), conv<C, CR>::f(qf.im)};
-      const long long gi = base + ((long long)sidx * N + j) * 3 + c;
-      SS::store(Q + gi, qn);
-      cpx<typename C::acc> pn = cacc_from<C>(qn);
-      if (!init) {
-        const cpx<real>* p = sP + sidx * N * 3 + c;
-        for (int i = 0; i < N; ++i) cmac<C>(pn, p[i * 3], sC[i * JT + jj]);
+    for (int idx = threadIdx.x; idx < nel; idx += blockDim.x) {
+      sR[idx] = RS::load_nc(R + base + idx);
+      if (!init) sP[idx] = SS::load_nc(P + base + idx);
+    }
+    for (int j0 = 0; j0 < N; j0 += JT) {
+      const int jn = min(JT, N - j0);
+      __syncthreads();
+      stage_coef<CR>(sA, Cinv, N, j0, jn, JT);
+      if (!init) stage_coef<C>(sC, SH, N, j0, jn, JT);
+      __syncthreads();
+      const int nout = ns * jn * 3;
+      for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+        const int sidx = o / (jn * 3);
+        const int rem = o - sidx * jn * 3;
+        const int c = rem / jn;
+        const int jj = rem - c * jn;
+        const int j = j0 + jj;
+        const cpx<rreal>* r = sR + (sidx * 3 + c) * N;
+        cpx<typename CR::acc> q = czero<CR>();
+        for (int i = 0; i <= j; ++i) cmac<CR>(q, r[i], sA[i * JT + jj]);
+        cpx<rreal> qf = cfin<CR>(q);
+        cpx<real> qn = {conv<C, CR>::f(qf.re), conv<C, CR>::f(qf.im)};
+        const long long gi = base + ((long long)sidx * 3 + c) * N + j;
+        SS::store(Q + gi, qn);
+        cpx<typename C::acc> pn = cacc_from<C>(qn);
+        if (!init) {
+          const cpx<real>* p = sP + (sidx * 3 + c) * N;
+          for (int i = 0; i < N; ++i) cmac<C>(pn, p[i], sC[i * JT + jj]);
+        }
+        SS::store(P + gi, cfin<C>(pn));
       }
-      SS::store(P + gi, cfin<C>(pn));
     }
   }
 }
@@ -490,7 +600,7 @@ static cudaError_t launch_restart(const void* R, void* Q, void* P, const double2
               ((size_t)t.TS * N * 3 + (size_t)N * t.JT) * sizeof(cpx<real>);
   cudaFuncSetAttribute(k_restart_update<RS, SS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)sm);
-  k_restart_update<RS, SS><<<nblk(Vh, t.TS), 256, sm, s>>>(
+  k_restart_update<RS, SS><<<gcap(Vh, t.TS, 152 * 4), 256, sm, s>>>(
       (const typename RS::elem*)R, (typename SS::elem*)Q, (typename SS::elem*)P, Cinv, SH, init, N,
       Vh, t.TS, t.JT, gate);
   return cudaGetLastError();
@@ -516,25 +626,26 @@ __global__ void k_accumulate(typename YS::elem* __restrict__ Y, typename XS::ele
   using CY = typename YS::comp;
   using CX = typename XS::comp;
   if (gate_closed(gate)) return;
-  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= n) return;
-  cpx<typename CX::real> x = XS::load_nc(X + idx);
-  cpx<typename CY::acc> y = cacc_from<CY>(YS::load_nc(Y + idx));
-  CY::add(y.re, conv<CY, CX>::f(x.re));
-  CY::add(y.im, conv<CY, CX>::f(x.im));
-  YS::store(Y + idx, cfin<CY>(y));
-  cpx<typename CX::real> z = {CX::rzero(), CX::rzero()};
-  XS::store(X + idx, z);
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    cpx<typename CX::real> x = XS::load_nc(X + idx);
+    cpx<typename CY::acc> y = cacc_from<CY>(YS::load_nc(Y + idx));
+    CY::add(y.re, conv<CY, CX>::f(x.re));
+    CY::add(y.im, conv<CY, CX>::f(x.im));
+    YS::store(Y + idx, cfin<CY>(y));
+    cpx<typename CX::real> z = {CX::rzero(), CX::rzero()};
+    XS::store(X + idx, z);
+  }
 }
 
 cudaError_t accumulate(FieldKind yk, FieldKind xk, void* Y, void* X, size_t n, Gate gate,
                        cudaStream_t s) {
   if (yk == FK_F64 && xk == FK_DF)
-    k_accumulate<StoreF64, StoreDF><<<nblk(n, 256), 256, 0, s>>>((double2*)Y, (float4*)X, n, gate);
+    k_accumulate<StoreF64, StoreDF><<<gcap(n, 256), 256, 0, s>>>((double2*)Y, (float4*)X, n, gate);
   else if (yk == FK_F64 && xk == FK_F64)
-    k_accumulate<StoreF64, StoreF64><<<nblk(n, 256), 256, 0, s>>>((double2*)Y, (double2*)X, n, gate);
+    k_accumulate<StoreF64, StoreF64><<<gcap(n, 256), 256, 0, s>>>((double2*)Y, (double2*)X, n, gate);
   else if (yk == FK_DF && xk == FK_DF)
-    k_accumulate<StoreDF, StoreDF><<<nblk(n, 256), 256, 0, s>>>((float4*)Y, (float4*)X, n, gate);
+    k_accumulate<StoreDF, StoreDF><<<gcap(n, 256), 256, 0, s>>>((float4*)Y, (float4*)X, n, gate);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();
@@ -545,17 +656,17 @@ template <class DS, class SS>
 __global__ void k_convert(const typename SS::elem* __restrict__ in, typename DS::elem* __restrict__ out,
                           long long n, Gate gate) {
   if (gate_closed(gate)) return;
-  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= n) return;
-  out[idx] = DS::from_double2(SS::to_double2(in[idx]));
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x)
+    out[idx] = DS::from_double2(SS::to_double2(in[idx]));
 }
 
 cudaError_t convert_field(FieldKind from, FieldKind to, const void* in, void* out, size_t n,
                           Gate gate, cudaStream_t s) {
   if (from == FK_F64 && to == FK_DF)
-    k_convert<StoreDF, StoreF64><<<nblk(n, 256), 256, 0, s>>>((const double2*)in, (float4*)out, n, gate);
+    k_convert<StoreDF, StoreF64><<<gcap(n, 256), 256, 0, s>>>((const double2*)in, (float4*)out, n, gate);
   else if (from == FK_F64 && to == FK_F32)
-    k_convert<StoreF32, StoreF64><<<nblk(n, 256), 256, 0, s>>>((const double2*)in, (float2*)out, n, gate);
+    k_convert<StoreF32, StoreF64><<<gcap(n, 256), 256, 0, s>>>((const double2*)in, (float2*)out, n, gate);
   else if (from == to)
     return cudaMemcpyAsync(out, in, n * elem_bytes(to), cudaMemcpyDeviceToDevice, s);
   else
@@ -587,14 +698,14 @@ __global__ void __launch_bounds__(256)
     for (int o = threadIdx.x; o < ns * jn * 3; o += blockDim.x) {
       const int sidx = o / (jn * 3);
       const int rem = o - sidx * jn * 3;
-      const int jj = rem / 3;
-      const int c = rem - jj * 3;
+      const int c = rem / jn;
+      const int jj = rem - c * jn;
       const int j = j0 + jj;
-      const long long gi = base + ((long long)sidx * N + j) * 3 + c;
-      const cpx<real>* x = sX + sidx * N * 3 + c;
+      const long long gi = base + ((long long)sidx * 3 + c) * N + j;
+      const cpx<real>* x = sX + (sidx * 3 + c) * N;
       cpx<acc> y = (mode == 0) ? cacc_from<C>(S::load_nc(Y + gi)) : czero<C>();
       const int iend = (mode == 1) ? j + 1 : N;
-      for (int i = 0; i < iend; ++i) cmac<C>(y, x[i * 3], sA[i * JT + jj]);
+      for (int i = 0; i < iend; ++i) cmac<C>(y, x[i], sA[i * JT + jj]);
       S::store(Y + gi, cfin<C>(y));
     }
   }
@@ -679,14 +790,15 @@ __global__ void k_cg_xpay(typename S::elem* __restrict__ p, const typename S::el
   using C = typename S::comp;
   using real = typename C::real;
   if (gate_closed(gate)) return;
-  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
   const real beta = C::from_double(*beta_p);
-  cpx<typename C::acc> v = cacc_from<C>(S::load(r + i));
-  cpx<real> pv = S::load_nc(p + i);
-  C::mac(v.re, beta, pv.re);
-  C::mac(v.im, beta, pv.im);
-  S::store(p + i, cfin<C>(v));
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    cpx<typename C::acc> v = cacc_from<C>(S::load(r + i));
+    cpx<real> pv = S::load_nc(p + i);
+    C::mac(v.re, beta, pv.re);
+    C::mac(v.im, beta, pv.im);
+    S::store(p + i, cfin<C>(v));
+  }
 }
 
 cudaError_t cg_axpy_norm(FieldKind k, FieldKind xk, void* x, void* r, const void* p,
@@ -712,13 +824,13 @@ cudaError_t cg_xpay(FieldKind k, void* p, const void* r, const double* beta, int
   long long n = 3LL * Vh;
   switch (k) {
     case FK_DF:
-      k_cg_xpay<StoreDF><<<nblk(n, 256), 256, 0, s>>>((float4*)p, (const float4*)r, beta, n, gate);
+      k_cg_xpay<StoreDF><<<gcap(n, 256), 256, 0, s>>>((float4*)p, (const float4*)r, beta, n, gate);
       break;
     case FK_F32:
-      k_cg_xpay<StoreF32><<<nblk(n, 256), 256, 0, s>>>((float2*)p, (const float2*)r, beta, n, gate);
+      k_cg_xpay<StoreF32><<<gcap(n, 256), 256, 0, s>>>((float2*)p, (const float2*)r, beta, n, gate);
       break;
     case FK_F64:
-      k_cg_xpay<StoreF64><<<nblk(n, 256), 256, 0, s>>>((double2*)p, (const double2*)r, beta, n, gate);
+      k_cg_xpay<StoreF64><<<gcap(n, 256), 256, 0, s>>>((double2*)p, (const double2*)r, beta, n, gate);
       break;
   }
   return cudaGetLastError();

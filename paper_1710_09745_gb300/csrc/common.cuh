@@ -190,6 +190,12 @@ struct StoreDF {  // {re.hi, im.hi, re.lo, im.lo}: one 128-bit word per complex
 struct StoreF32 {
   using elem = float2;
   using comp = CompF32;
+  // two consecutive complex numbers with one 128-bit load (16-byte aligned)
+  static __device__ __forceinline__ void load2(const elem* p, cpx<float>& a, cpx<float>& b) {
+    float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    a = {v.x, v.y};
+    b = {v.z, v.w};
+  }
   static __device__ __forceinline__ cpx<float> load(const elem* p) {
     float2 v = __ldg(p);
     return {v.x, v.y};
@@ -288,6 +294,32 @@ __device__ __forceinline__ int neighbour_cb(const Geom& g, const int c[4], int m
   y[mu] = v;
   int lex = y[0] + g.L[0] * (y[1] + g.L[1] * (y[2] + g.L[2] * y[3]));
   return lex >> 1;
+}
+
+// Coordinates as scalars (no arrays, so nothing is indexed at run time and
+// nothing spills to local memory).
+__device__ __forceinline__ void site_xyzt(const Geom& g, int cb, int p, int& x, int& y, int& z,
+                                          int& t) {
+  int xh = cb % g.hx;
+  int r = cb / g.hx;
+  y = r % g.L[1];
+  r /= g.L[1];
+  z = r % g.L[2];
+  t = r / g.L[2];
+  x = 2 * xh + ((y + z + t + p) & 1);
+}
+
+// checkerboard index of (x,y,z,t) + k * mu (periodic), lex = lexicographic
+// index of (x,y,z,t)
+__device__ __forceinline__ int neighbour_cb_s(const Geom& g, int lex, int x, int y, int z, int t,
+                                              int mu, int k) {
+  const int c = mu == 0 ? x : mu == 1 ? y : mu == 2 ? z : t;
+  const int L = mu == 0 ? g.L[0] : mu == 1 ? g.L[1] : mu == 2 ? g.L[2] : g.L[3];
+  const int st = mu == 0 ? 1 : mu == 1 ? g.L[0] : mu == 2 ? g.L[0] * g.L[1] : g.L[0] * g.L[1] * g.L[2];
+  int v = c + k;
+  while (v >= L) v -= L;
+  while (v < 0) v += L;
+  return (lex + (v - c) * st) >> 1;
 }
 
 // hop table: direction d = 4*mu + q, q = 0..3 -> k = +1, -1, +3, -3

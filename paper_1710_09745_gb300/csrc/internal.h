@@ -44,7 +44,11 @@ enum DslashEpi {
 cudaError_t pack_links(FieldKind k, const double2* fat, const double2* lng, void* out,
                        const Geom& g, int antiperiodic_t, cudaStream_t s);
 size_t links_bytes(FieldKind k, const Geom& g);  // both parities
-// links points at the start of the packed array for both parities
+// links points at the start of the packed array for both parities.
+// R: right-hand sides per thread (1, 2, 4, 8); R | DSLASH_TMA selects the
+// bulk-copy pipelined kernel (the plain kernel runs instead when the
+// pipelined one cannot, e.g. FP32 rows that are not 16-byte multiples).
+static constexpr int DSLASH_TMA = 0x100;
 cudaError_t dslash(FieldKind k, int R, int epi, const void* links, const void* in, void* out,
                    const void* c1, const void* c2, double m2, const Geom& g, int out_parity,
                    int N, Gate gate, cudaStream_t s);

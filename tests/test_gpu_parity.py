@@ -27,6 +27,35 @@ def test_dslash_parity(prec, N, parity):
     assert gh.rel_err(out, ref) < gh.TOL[prec]
 
 
+TMA = 256
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("variant", [1, 2, 4, 8, TMA + 1, TMA + 2, TMA + 4, TMA + 8])
+@pytest.mark.parametrize("N,parity", [(2, 0), (5, 1), (16, 0), (16, 1), (33, 1)])
+def test_dslash_every_kernel_variant(prec, variant, N, parity):
+    """Each stencil kernel (register tile R, plain or bulk-copy pipelined)
+    against the oracle; unsupported pipelined cases fall back to plain."""
+    s, fat, lng = gh.make_solver(DIMS, 0.1, prec=prec, seed=1011, max_rhs=max(N, 16),
+                                 dslash_variant=variant)
+    psi = hi.gaussian_sources(DIMS, N, seed=99 + N)
+    out = gh.to_np(s.dslash(psi, parity))
+    ref = hisq.dslash(DIMS, fat, lng, psi, parity)
+    assert gh.rel_err(out, ref) < gh.TOL[prec]
+
+
+@pytest.mark.parametrize("variant", [TMA + 2, TMA + 4])
+def test_solve_with_pipelined_stencil(variant):
+    dims = (8, 8, 8, 8)
+    s, fat, lng = gh.make_solver(dims, 0.05, seed=1012, max_rhs=8, dslash_variant=variant)
+    b = hi.gaussian_sources(dims, 8, seed=2012)
+    X, info = s.solve(b, tol=1e-10)
+    assert info["status"] == 0
+    r = b - hisq.apply_A(dims, fat, lng, 0.05, gh.to_np(X))
+    rel = np.linalg.norm(r.reshape(8, -1), axis=1) / np.linalg.norm(b.reshape(8, -1), axis=1)
+    assert rel.max() <= 1e-10
+
+
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("N", [1, 5, 8])
 @pytest.mark.parametrize("antiperiodic", [False, True])
