@@ -100,7 +100,8 @@ typedef struct {
                           events (fills the ms_stencil fields of the stats) */
   int dslash_variant;  /* stencil kernel: 0 = autotuned on first use (default);
                           else R in {1, 2, 4, 8} right-hand sides per thread,
-                          plus 256 for the bulk-copy pipelined kernel */
+                          plus 256 for the bulk-copy (TMA) pipelined kernel or
+                          512 for the per-thread cp.async prefetch kernel */
 } blockcg_params;
 
 typedef struct {

@@ -224,7 +224,8 @@ int stencil_R(blockcg_ctx* h, FieldKind k, int N, const void* links, const void*
     return best;
   }
   Gate g0{nullptr, GATE_ALWAYS};
-  const int cands[8] = {1, 2, 4, 8, 1 | DSLASH_TMA, 2 | DSLASH_TMA, 4 | DSLASH_TMA, 8 | DSLASH_TMA};
+  const int cands[12] = {1, 2, 4, 8, 1 | DSLASH_TMA, 2 | DSLASH_TMA, 4 | DSLASH_TMA, 8 | DSLASH_TMA,
+                         1 | DSLASH_ASYNC, 2 | DSLASH_ASYNC, 4 | DSLASH_ASYNC, 8 | DSLASH_ASYNC};
   for (int R : cands) {
     if ((R & 0xff) > 1 && (R & 0xff) > N) continue;
     if (dslash(k, R, EPI_NONE, links, in, out, nullptr, nullptr, 0.0, h->g, 1, N, g0, h->stream) !=
@@ -397,7 +398,7 @@ blockcg_status blockcg_create(blockcg_t* out, const int dims[4], double mass,
       prm.check_every < 0 || (int)prm.prec < 0 || (int)prm.prec > 2)
     return BLOCKCG_ERR_ARG;
   {
-    int r = prm.dslash_variant & ~DSLASH_TMA;
+    int r = prm.dslash_variant & ~(DSLASH_TMA | DSLASH_ASYNC);
     if (prm.dslash_variant != 0 && r != 1 && r != 2 && r != 4 && r != 8) return BLOCKCG_ERR_ARG;
   }
   blockcg_ctx* h = new blockcg_ctx();

@@ -414,9 +414,12 @@ __global__ void __launch_bounds__(256)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (gate_closed(gate)) return;
   const bool keepP = gate.st != nullptr && ((const volatile SolverStatus*)gate.st)->ru_pending;
+  // W and P tiles with a row stride of N + 1 complex numbers, so that the
+  // rows read by the lanes of a warp fall into different shared-memory banks
+  const int RS = N + 1;
   cpx<real>* sW = reinterpret_cast<cpx<real>*>(smem_raw);
-  cpx<real>* sP = sW + TS * N * 3;
-  cpx<real>* sA = sP + TS * N * 3;  // Sinv chunk  [N][JT]
+  cpx<real>* sP = sW + TS * 3 * RS;
+  cpx<real>* sA = sP + TS * 3 * RS;  // Sinv chunk  [N][JT]
   cpx<real>* sB = sA + N * JT;      // BC chunk
   cpx<real>* sC = sB + N * JT;      // SH chunk
   const bool one_chunk = (JT >= N);
@@ -432,8 +435,9 @@ __global__ void __launch_bounds__(256)
     const int nel = ns * N * 3;
     __syncthreads();
     for (int idx = threadIdx.x; idx < nel; idx += blockDim.x) {
-      sW[idx] = SS::load_nc(Q + base + idx);
-      sP[idx] = SS::load_nc(P + base + idx);
+      const int rr = idx / N, cc = idx - rr * N;
+      sW[rr * RS + cc] = SS::load_nc(Q + base + idx);
+      sP[rr * RS + cc] = SS::load_nc(P + base + idx);
     }
     for (int j0 = 0; j0 < N; j0 += JT) {
       const int jn = min(JT, N - j0);
@@ -445,13 +449,16 @@ __global__ void __launch_bounds__(256)
       }
       __syncthreads();
       const int ng = (jn + JB - 1) / JB;  // column groups
-      const int nout = ns * 3 * ng;
+      const int nrows = ns * 3;
+      const int nout = nrows * ng;
+      // column group major: the lanes of a warp share the group (and hence
+      // the triangular loop bounds) and differ only in the row
       for (int o = threadIdx.x; o < nout; o += blockDim.x) {
-        const int row = o / ng;  // (site, colour)
-        const int jg = o - row * ng;
+        const int jg = o / nrows;
+        const int row = o - jg * nrows;  // (site, colour)
         const int jj0 = jg * JB;
-        const cpx<real>* w = sW + row * N;
-        const cpx<real>* p = sP + row * N;
+        const cpx<real>* w = sW + row * RS;
+        const cpx<real>* p = sP + row * RS;
         cpx<acc> q[JB], x[JB], pn[JB];
 #pragma unroll
         for (int u = 0; u < JB; ++u) {
@@ -459,21 +466,69 @@ __global__ void __launch_bounds__(256)
           x[u] = czero<C>();
           pn[u] = czero<C>();
         }
-        const int jmax = j0 + min(jj0 + JB, jn) - 1;  // last column of the group
-        for (int i = 0; i < N; ++i) {
-          const cpx<real> wi = w[i];
-          const cpx<real> pi = p[i];
+        // i ranges: [0, jlo) feeds Q and X of every column of the group;
+        // [jlo, jlo + JB) is the diagonal band (per-column conditions);
+        // [jlo + JB, N) feeds X and P S^dag of every column
+        const int jlo = j0 + jj0;
+        const bool full = (jj0 + JB <= jn);
+        const int i_band_end = min(N, jlo + JB);
+        if (full) {
+          for (int i = 0; i < jlo; ++i) {
+            const cpx<real> wi = w[i];
+            const cpx<real> pi = p[i];
+            const cpx<real>* ca = sA + i * JT + jj0;
+            const cpx<real>* cb = sB + i * JT + jj0;
 #pragma unroll
-          for (int u = 0; u < JB; ++u) {
-            const int jj = jj0 + u;
-            if (jj < jn) {
-              const int j = j0 + jj;
-              if (i <= j) cmac<C>(q[u], wi, sA[i * JT + jj]);       // Q = W S^-1
-              cmac<C>(x[u], pi, sB[i * JT + jj]);                    // X += P beta C
-              if (!keepP && i >= j) cmac<C>(pn[u], pi, sC[i * JT + jj]);  // P S^dag
+            for (int u = 0; u < JB; ++u) {
+              cmac<C>(q[u], wi, ca[u]);
+              cmac<C>(x[u], pi, cb[u]);
             }
           }
-          (void)jmax;
+          for (int i = jlo; i < i_band_end; ++i) {
+            const cpx<real> wi = w[i];
+            const cpx<real> pi = p[i];
+#pragma unroll
+            for (int u = 0; u < JB; ++u) {
+              const int j = jlo + u;
+              if (i <= j) cmac<C>(q[u], wi, sA[i * JT + jj0 + u]);
+              cmac<C>(x[u], pi, sB[i * JT + jj0 + u]);
+              if (!keepP && i >= j) cmac<C>(pn[u], pi, sC[i * JT + jj0 + u]);
+            }
+          }
+          if (!keepP) {
+            for (int i = i_band_end; i < N; ++i) {
+              const cpx<real> pi = p[i];
+              const cpx<real>* cb = sB + i * JT + jj0;
+              const cpx<real>* cc = sC + i * JT + jj0;
+#pragma unroll
+              for (int u = 0; u < JB; ++u) {
+                cmac<C>(x[u], pi, cb[u]);
+                cmac<C>(pn[u], pi, cc[u]);
+              }
+            }
+          } else {
+            for (int i = i_band_end; i < N; ++i) {
+              const cpx<real> pi = p[i];
+              const cpx<real>* cb = sB + i * JT + jj0;
+#pragma unroll
+              for (int u = 0; u < JB; ++u) cmac<C>(x[u], pi, cb[u]);
+            }
+          }
+        } else {  // ragged last group
+          for (int i = 0; i < N; ++i) {
+            const cpx<real> wi = w[i];
+            const cpx<real> pi = p[i];
+#pragma unroll
+            for (int u = 0; u < JB; ++u) {
+              const int jj = jj0 + u;
+              if (jj < jn) {
+                const int j = j0 + jj;
+                if (i <= j) cmac<C>(q[u], wi, sA[i * JT + jj]);
+                cmac<C>(x[u], pi, sB[i * JT + jj]);
+                if (!keepP && i >= j) cmac<C>(pn[u], pi, sC[i * JT + jj]);
+              }
+            }
+          }
         }
         const long long gbase = base + (long long)row * N + j0;
 #pragma unroll
@@ -507,8 +562,8 @@ static cudaError_t launch_bcg_update(void* Q, void* P, void* X, const double2* S
                                      const double2* BC, const double2* SH, int N, int Vh,
                                      Gate gate, cudaStream_t s) {
   using real = typename SS::comp::real;
-  TileCfg t = tile_cfg(N, sizeof(cpx<real>), 2, 3);
-  size_t sm = ((size_t)2 * t.TS * N * 3 + 3 * (size_t)N * t.JT) * sizeof(cpx<real>);
+  TileCfg t = tile_cfg(N + 1, sizeof(cpx<real>), 2, 3);
+  size_t sm = ((size_t)2 * t.TS * (N + 1) * 3 + 3 * (size_t)N * t.JT) * sizeof(cpx<real>);
   cudaFuncSetAttribute(k_bcg_update<SS, XS, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   unsigned blocks = gcap(Vh, t.TS, 152 * 8);
   k_bcg_update<SS, XS, 4><<<blocks, 256, sm, s>>>((typename SS::elem*)Q, (typename SS::elem*)P,
@@ -563,12 +618,13 @@ __global__ void __launch_bounds__(256)
       stage_coef<CR>(sA, Cinv, N, j0, jn, JT);
       if (!init) stage_coef<C>(sC, SH, N, j0, jn, JT);
       __syncthreads();
-      const int nout = ns * jn * 3;
+      const int nrows = ns * 3;
+      const int nout = nrows * jn;
       for (int o = threadIdx.x; o < nout; o += blockDim.x) {
-        const int sidx = o / (jn * 3);
-        const int rem = o - sidx * jn * 3;
-        const int c = rem / jn;
-        const int jj = rem - c * jn;
+        const int jj = o / nrows;  // column major: uniform triangular bounds per warp
+        const int rw = o - jj * nrows;
+        const int sidx = rw / 3;
+        const int c = rw - sidx * 3;
         const int j = j0 + jj;
         const cpx<rreal>* r = sR + (sidx * 3 + c) * N;
         cpx<typename CR::acc> q = czero<CR>();
@@ -695,11 +751,12 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
     stage_coef<C>(sA, a, N, j0, jn, JT);
     __syncthreads();
-    for (int o = threadIdx.x; o < ns * jn * 3; o += blockDim.x) {
-      const int sidx = o / (jn * 3);
-      const int rem = o - sidx * jn * 3;
-      const int c = rem / jn;
-      const int jj = rem - c * jn;
+    const int nrows = ns * 3;
+    for (int o = threadIdx.x; o < nrows * jn; o += blockDim.x) {
+      const int jj = o / nrows;  // column major: uniform triangular bounds per warp
+      const int rw = o - jj * nrows;
+      const int sidx = rw / 3;
+      const int c = rw - sidx * 3;
       const int j = j0 + jj;
       const long long gi = base + ((long long)sidx * 3 + c) * N + j;
       const cpx<real>* x = sX + (sidx * 3 + c) * N;

@@ -49,6 +49,8 @@ size_t links_bytes(FieldKind k, const Geom& g);  // both parities
 // bulk-copy pipelined kernel (the plain kernel runs instead when the
 // pipelined one cannot, e.g. FP32 rows that are not 16-byte multiples).
 static constexpr int DSLASH_TMA = 0x100;
+// R | DSLASH_ASYNC selects the per-thread cp.async prefetch kernel
+static constexpr int DSLASH_ASYNC = 0x200;
 cudaError_t dslash(FieldKind k, int R, int epi, const void* links, const void* in, void* out,
                    const void* c1, const void* c2, double m2, const Geom& g, int out_parity,
                    int N, Gate gate, cudaStream_t s);

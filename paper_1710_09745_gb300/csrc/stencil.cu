@@ -374,6 +374,207 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Per-thread asynchronous prefetch stencil.  Same work split as k_dslash, but
+// every thread keeps DEPTH - 1 hops of its own operands in flight with
+// cp.async into a private shared-memory ring (the T threads of a site share
+// the site's nine link elements, each copying every T-th one), so the loads
+// of later hops overlap the arithmetic of the current one without a
+// CTA-wide barrier.  Requires T to divide the block size.
+__device__ __forceinline__ void cp_async_bytes(void* dst, const void* src, int bytes) {
+  const uint32_t d = smem_u32(dst);
+  if (bytes == 16)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N_>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N_) : "memory");
+}
+
+static constexpr int ASYNC_TPB = 128;
+
+template <class S, int RV, int V, int EPI, int DEPTH>
+__global__ void __launch_bounds__(ASYNC_TPB)
+    k_dslash_async(const typename S::elem* __restrict__ links, const typename S::elem* __restrict__ in,
+                   typename S::elem* __restrict__ out, const typename S::elem* __restrict__ c1,
+                   const typename S::elem* __restrict__ c2, double m2d, Geom g, int parity, int N,
+                   int T, Gate gate) {
+  using E = typename S::elem;
+  using C = typename S::comp;
+  using real = typename C::real;
+  using acc = typename C::acc;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  if (gate_closed(gate)) return;
+  const int NS = N / V;
+  const int SPT = 3 * RV * V;                 // spinor elements per thread per hop
+  const int sites_cta = ASYNC_TPB / T;
+  // ring: [DEPTH][sites_cta][9] links, then [DEPTH][ASYNC_TPB][SPT] spinors
+  E* sL = reinterpret_cast<E*>(smem_raw);
+  E* sS = sL + DEPTH * sites_cta * 9;
+  const int tid = threadIdx.x;
+  const int ls = tid / T;  // local site in the block
+  const int k = tid - ls * T;
+  const long long total = (long long)g.Vh * T;
+  const real m2 = C::from_double(m2d);
+  const int nr = (NS - k + T - 1) / T;
+  for (long long gid0 = (long long)blockIdx.x * ASYNC_TPB; gid0 < total;
+       gid0 += (long long)gridDim.x * ASYNC_TPB) {
+    const long long gid = gid0 + tid;
+    const bool live = gid < total;
+    const int site = live ? (int)(gid / T) : 0;
+    int x, y, z, t;
+    site_xyzt(g, site, parity, x, y, z, t);
+    const int lex = x + g.L[0] * (y + g.L[1] * (z + g.L[2] * t));
+    const typename S::elem* lp = links + link_offset(g, parity, site);
+    auto issue = [&](int d) {
+      if (live) {
+        const int buf = d % DEPTH;
+        E* l = sL + (buf * sites_cta + ls) * 9;
+        for (int e = k; e < 9; e += T) cp_async_bytes(l + e, lp + (d * 9 + e) * LINK_W, sizeof(E));
+        const int nb = neighbour_cb_s(g, lex, x, y, z, t, d >> 2, hop_k(d & 3));
+        const E* ip = in + (long long)nb * N * 3 + k * V;
+        E* sp = sS + ((long long)buf * ASYNC_TPB + tid) * SPT;
+#pragma unroll
+        for (int r = 0; r < RV; ++r)
+          if (r < nr)
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+              cp_async_bytes(sp + (r * 3 + b) * V, ip + b * N + r * T * V, V * sizeof(E));
+      }
+      cp_async_commit();
+    };
+    cpx<acc> a[RV][V][3];
+#pragma unroll
+    for (int r = 0; r < RV; ++r)
+#pragma unroll
+      for (int w = 0; w < V; ++w)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) a[r][w][i] = czero<C>();
+#pragma unroll
+    for (int d = 0; d < DEPTH - 1; ++d) issue(d);
+#pragma unroll 1
+    for (int d = 0; d < 16; ++d) {
+      if (d + DEPTH - 1 < 16) issue(d + DEPTH - 1);
+      else cp_async_commit();
+      cp_async_wait<DEPTH - 1>();
+      __syncwarp();
+      if (live) {
+        const int buf = d % DEPTH;
+        const E* l = sL + (buf * sites_cta + ls) * 9;
+        cpx<real> U[9];
+#pragma unroll
+        for (int e = 0; e < 9; ++e) U[e] = S::load_nc(l + e);
+        const E* sp = sS + ((long long)buf * ASYNC_TPB + tid) * SPT;
+#pragma unroll
+        for (int r = 0; r < RV; ++r) {
+          if (r < nr) {
+            cpx<real> v[3][V];
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+#pragma unroll
+              for (int w = 0; w < V; ++w) v[b][w] = S::load_nc(sp + (r * 3 + b) * V + w);
+#pragma unroll
+            for (int w = 0; w < V; ++w)
+#pragma unroll
+              for (int i = 0; i < 3; ++i) {
+                cmac<C>(a[r][w][i], U[i * 3 + 0], v[0][w]);
+                cmac<C>(a[r][w][i], U[i * 3 + 1], v[1][w]);
+                cmac<C>(a[r][w][i], U[i * 3 + 2], v[2][w]);
+              }
+          }
+        }
+      }
+      __syncwarp();
+    }
+    if (live) {
+      const long long ob = (long long)site * N * 3 + k * V;
+#pragma unroll
+      for (int r = 0; r < RV; ++r) {
+        if (r < nr) {
+#pragma unroll
+          for (int w = 0; w < V; ++w)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+              const long long oi = ob + i * N + r * T * V + w;
+              cpx<acc> vv = a[r][w][i];
+              if (EPI != EPI_NONE) {
+                C::neg(vv.re);
+                C::neg(vv.im);
+                cpx<real> cc = S::load(c1 + oi);
+                C::mac(vv.re, m2, cc.re);
+                C::mac(vv.im, m2, cc.im);
+                if (EPI == EPI_RESIDUAL) {
+                  C::neg(vv.re);
+                  C::neg(vv.im);
+                  cpx<real> bb = S::load(c2 + oi);
+                  C::add(vv.re, bb.re);
+                  C::add(vv.im, bb.im);
+                }
+              }
+              S::store(out + oi, cfin<C>(vv));
+            }
+        }
+      }
+    }
+  }
+}
+
+template <class S, int RV, int V, int EPI>
+static bool launch_async_t(const void* links, const void* in, void* out, const void* c1,
+                           const void* c2, double m2, const Geom& g, int parity, int N, Gate gate,
+                           cudaStream_t s) {
+  using E = typename S::elem;
+  const int NS = N / V;
+  const int T = (NS + RV - 1) / RV;
+  if (T > ASYNC_TPB || ASYNC_TPB % T) return false;
+  if ((V * sizeof(E)) != 8 && (V * sizeof(E)) != 16) return false;
+  constexpr int DEPTH = 3;
+  const size_t sm = ((size_t)DEPTH * (ASYNC_TPB / T) * 9 + (size_t)DEPTH * ASYNC_TPB * 3 * RV * V) * sizeof(E);
+  auto kern = k_dslash_async<S, RV, V, EPI, DEPTH>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+    return false;
+  long long total = (long long)g.Vh * T;
+  long long want = (total + ASYNC_TPB - 1) / ASYNC_TPB;
+  unsigned blocks = (unsigned)(want < 152 * 16 ? want : 152 * 16);
+  kern<<<blocks, ASYNC_TPB, sm, s>>>((const E*)links, (const E*)in, (E*)out, (const E*)c1,
+                                     (const E*)c2, m2, g, parity, N, T, gate);
+  return true;
+}
+
+template <class S, int RV, int V>
+static bool launch_async_r(int epi, const void* links, const void* in, void* out, const void* c1,
+                           const void* c2, double m2, const Geom& g, int parity, int N, Gate gate,
+                           cudaStream_t s) {
+  switch (epi) {
+    case EPI_NONE: return launch_async_t<S, RV, V, EPI_NONE>(links, in, out, c1, c2, m2, g, parity, N, gate, s);
+    case EPI_NORMAL: return launch_async_t<S, RV, V, EPI_NORMAL>(links, in, out, c1, c2, m2, g, parity, N, gate, s);
+    default: return launch_async_t<S, RV, V, EPI_RESIDUAL>(links, in, out, c1, c2, m2, g, parity, N, gate, s);
+  }
+}
+
+template <class S>
+static bool launch_async_s(int R, int epi, const void* links, const void* in, void* out,
+                           const void* c1, const void* c2, double m2, const Geom& g, int parity,
+                           int N, Gate gate, cudaStream_t s) {
+  constexpr bool F32 = std::is_same<S, StoreF32>::value;
+  if (F32 && (N % 2) == 0 && R >= 2) {
+    switch (R) {
+      case 2: return launch_async_r<S, 1, F32 ? 2 : 1>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, s);
+      case 4: return launch_async_r<S, 2, F32 ? 2 : 1>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, s);
+      default: return launch_async_r<S, 4, F32 ? 2 : 1>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, s);
+    }
+  }
+  switch (R) {
+    case 1: return launch_async_r<S, 1, 1>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, s);
+    case 2: return launch_async_r<S, 2, 1>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, s);
+    case 4: return launch_async_r<S, 4, 1>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, s);
+    default: return launch_async_r<S, 8, 1>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, s);
+  }
+}
+
 // smem site stride (elements): 3N padded so that consecutive sites start 16
 // banks apart, and a multiple of 16 bytes
 static int tma_site_stride(size_t eb, int N) {
@@ -539,6 +740,18 @@ static void launch_dslash_s(int R, int epi, const void* links, const void* in, v
 cudaError_t dslash(FieldKind k, int R, int epi, const void* links, const void* in, void* out,
                    const void* c1, const void* c2, double m2, const Geom& g, int out_parity,
                    int N, Gate gate, cudaStream_t s) {
+  if (R & DSLASH_ASYNC) {
+    const int r = R & 0xff;
+    bool ok = false;
+    switch (k) {
+      case FK_DF: ok = launch_async_s<StoreDF>(r, epi, links, in, out, c1, c2, m2, g, out_parity, N, gate, s); break;
+      case FK_F32: ok = launch_async_s<StoreF32>(r, epi, links, in, out, c1, c2, m2, g, out_parity, N, gate, s); break;
+      case FK_F64: ok = launch_async_s<StoreF64>(r, epi, links, in, out, c1, c2, m2, g, out_parity, N, gate, s); break;
+    }
+    if (ok) return cudaGetLastError();
+    cudaGetLastError();
+    R = r;
+  }
   if (R & DSLASH_TMA) {
     const int r = R & 0xff;
     SolverStatus* errst = const_cast<SolverStatus*>(gate.st);

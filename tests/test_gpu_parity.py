@@ -28,14 +28,17 @@ def test_dslash_parity(prec, N, parity):
 
 
 TMA = 256
+ASYNC = 512
 
 
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("variant", [1, 2, 4, 8, TMA + 1, TMA + 2, TMA + 4, TMA + 8])
+@pytest.mark.parametrize("variant", [1, 2, 4, 8, TMA + 1, TMA + 2, TMA + 4, TMA + 8,
+                                     ASYNC + 1, ASYNC + 2, ASYNC + 4, ASYNC + 8])
 @pytest.mark.parametrize("N,parity", [(2, 0), (5, 1), (16, 0), (16, 1), (33, 1)])
 def test_dslash_every_kernel_variant(prec, variant, N, parity):
-    """Each stencil kernel (register tile R, plain or bulk-copy pipelined)
-    against the oracle; unsupported pipelined cases fall back to plain."""
+    """Each stencil kernel (register tile R; plain, bulk-copy pipelined or
+    cp.async prefetching) against the oracle; unsupported pipelined cases
+    fall back to the plain kernel."""
     s, fat, lng = gh.make_solver(DIMS, 0.1, prec=prec, seed=1011, max_rhs=max(N, 16),
                                  dslash_variant=variant)
     psi = hi.gaussian_sources(DIMS, N, seed=99 + N)
@@ -44,7 +47,7 @@ def test_dslash_every_kernel_variant(prec, variant, N, parity):
     assert gh.rel_err(out, ref) < gh.TOL[prec]
 
 
-@pytest.mark.parametrize("variant", [TMA + 2, TMA + 4])
+@pytest.mark.parametrize("variant", [TMA + 2, TMA + 4, ASYNC + 2, ASYNC + 4])
 def test_solve_with_pipelined_stencil(variant):
     dims = (8, 8, 8, 8)
     s, fat, lng = gh.make_solver(dims, 0.05, seed=1012, max_rhs=8, dslash_variant=variant)
