@@ -227,7 +227,7 @@ def dslash_only(a):
     dev = torch.device("cuda", 0)
     h = BlockCG(dims, fat.to(dev), lng.to(dev), a.mass, prec=a.prec, max_rhs=max(a.sweep), device=dev)
     hbm_peak, _ = load_peaks()
-    bpr = {"f64": 8, "f64_native": 8, "mixed_f32": 4}[a.prec]
+    bpr = {"f64": 8, "f64_native": 8, "mixed_f32": 4, "mixed_f16": 2, "mixed_bf16": 2}[a.prec]
     rows = {}
     for n in a.sweep:
         ms = h.bench_dslash(n, reps=max(a.steps, 1) * 10)
@@ -308,7 +308,7 @@ def main():
     ms_total = sum(i["ms_total"] for i in infos)
     avg_launch_ms = ms_st / max(n_st, 1)
     hbm_peak, peak_src = load_peaks()
-    bytes_per_real = {"f64": 8, "f64_native": 8, "mixed_f32": 4}[a.prec]
+    bytes_per_real = {"f64": 8, "f64_native": 8, "mixed_f32": 4, "mixed_f16": 2, "mixed_bf16": 2}[a.prec]
     alg_bytes = (288 + 12 * N) * bytes_per_real * Vh
     alg_flops = STENCIL_FLOPS * N * Vh
     if a.prec == "f64":
@@ -358,7 +358,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"f64": "f64(double-float)", "f64_native": "f64", "mixed_f32": "f32+f64"}[a.prec],
+        "dtype": {"f64": "f64(double-float)", "f64_native": "f64", "mixed_f32": "f32+f64",
+                  "mixed_f16": "f16+f32+f64", "mixed_bf16": "bf16+f32+f64"}[a.prec],
         "data": "synthetic",
         "config": {"workload": workload_name(a), "dims": list(dims), "mass": a.mass, "n_rhs": N,
                    "tol": a.tol, "prec": a.prec, "parallelism": f"replicas x{world}",

@@ -79,11 +79,23 @@ typedef enum {
  *  F64_NATIVE  native FP64 storage and arithmetic in the iterations too (slow
  *              on GPUs with a reduced FP64 rate; for verification).
  *  MIXED_F32   sloppy P, Q, AP, T and links in FP32 with FP32 arithmetic; X
- *              in double-float.  */
+ *              in double-float.
+ *  MIXED_F16   as MIXED_F32 with P, Q, AP, T and links stored as IEEE FP16
+ *              (2^10 x value, see below) and FP32 arithmetic.
+ *  MIXED_BF16  as MIXED_F16 with bfloat16 storage (no factor).  Its 8-bit
+ *              significand lets the sloppy recursion stagnate before the
+ *              residual drops by ru_delta, so ru_every defaults to 10 for
+ *              this form when the caller leaves it 0.
+ *  FP16 storage keeps 2^10 times the value: the block vectors of the
+ *  iteration are normalised (components ~ (3 V/2)^-1/2), so the fixed
+ *  power-of-two factor keeps them near 1 and clear of FP16's subnormal range
+ *  without per-site scale arrays.  */
 typedef enum {
   BLOCKCG_PREC_F64 = 0,
   BLOCKCG_PREC_F64_NATIVE = 1,
-  BLOCKCG_PREC_MIXED_F32 = 2
+  BLOCKCG_PREC_MIXED_F32 = 2,
+  BLOCKCG_PREC_MIXED_F16 = 3,
+  BLOCKCG_PREC_MIXED_BF16 = 4
 } blockcg_prec;
 
 typedef struct {

@@ -14,7 +14,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libblockcg.so")
 
-PREC = {"f64": 0, "f64_native": 1, "mixed_f32": 2}
+PREC = {"f64": 0, "f64_native": 1, "mixed_f32": 2, "mixed_f16": 3, "mixed_bf16": 4}
 
 STATUS = {
     0: "BLOCKCG_OK", 1: "BLOCKCG_ERR_ARG", 2: "BLOCKCG_ERR_CUDA", 3: "BLOCKCG_ERR_NOMEM",

@@ -395,7 +395,7 @@ blockcg_status blockcg_create(blockcg_t* out, const int dims[4], double mass,
   blockcg_default_params(&prm);
   if (p) prm = *p;
   if (prm.max_iter < 1 || prm.ru_delta < 0 || !(prm.ru_delta < 1) || prm.ru_every < 0 ||
-      prm.check_every < 0 || (int)prm.prec < 0 || (int)prm.prec > 2)
+      prm.check_every < 0 || (int)prm.prec < 0 || (int)prm.prec > 4)
     return BLOCKCG_ERR_ARG;
   {
     int r = prm.dslash_variant & ~(DSLASH_TMA | DSLASH_ASYNC);
@@ -416,7 +416,12 @@ blockcg_status blockcg_create(blockcg_t* out, const int dims[4], double mass,
     case BLOCKCG_PREC_F64: h->sloppy = FK_DF; h->upd = FK_DF; break;
     case BLOCKCG_PREC_F64_NATIVE: h->sloppy = FK_F64; h->upd = FK_F64; break;
     case BLOCKCG_PREC_MIXED_F32: h->sloppy = FK_F32; h->upd = FK_DF; break;
+    case BLOCKCG_PREC_MIXED_F16: h->sloppy = FK_H16; h->upd = FK_DF; break;
+    case BLOCKCG_PREC_MIXED_BF16: h->sloppy = FK_BF16; h->upd = FK_DF; break;
   }
+  // bfloat16's 8-bit significand lets the sloppy recursion stagnate before
+  // the residual falls by ru_delta; a periodic reliable update keeps it going
+  if (prm.prec == BLOCKCG_PREC_MIXED_BF16 && h->p.ru_every == 0) h->p.ru_every = 10;
   h->gauge = nullptr;
   h->gauge_bytes = 0;
   h->links_fine = h->links_sloppy = nullptr;

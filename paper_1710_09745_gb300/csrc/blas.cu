@@ -67,6 +67,12 @@ cudaError_t to_internal(FieldKind k, const double2* user, void* internal, int N,
     case FK_F64:
       k_to_internal<StoreF64><<<nblk(total, 256), 256, 0, s>>>(user, (double2*)internal, N, Vh);
       break;
+    case FK_H16:
+      k_to_internal<StoreH16><<<nblk(total, 256), 256, 0, s>>>(user, (__half2*)internal, N, Vh);
+      break;
+    case FK_BF16:
+      k_to_internal<StoreBF16><<<nblk(total, 256), 256, 0, s>>>(user, (__nv_bfloat162*)internal, N, Vh);
+      break;
   }
   return cudaGetLastError();
 }
@@ -83,6 +89,12 @@ cudaError_t from_internal(FieldKind k, const void* internal, double2* user, int 
       break;
     case FK_F64:
       k_from_internal<StoreF64><<<nblk(total, 256), 256, 0, s>>>((const double2*)internal, user, N, Vh);
+      break;
+    case FK_H16:
+      k_from_internal<StoreH16><<<nblk(total, 256), 256, 0, s>>>((const __half2*)internal, user, N, Vh);
+      break;
+    case FK_BF16:
+      k_from_internal<StoreBF16><<<nblk(total, 256), 256, 0, s>>>((const __nv_bfloat162*)internal, user, N, Vh);
       break;
   }
   return cudaGetLastError();
@@ -286,6 +298,8 @@ cudaError_t gram_partials(FieldKind k, const void* X, const void* Y, int N, int 
     case FK_DF: launch_gram<StoreDF>(X, Y, N, Vh, hermitian, partials, nblocks, gate, s); break;
     case FK_F32: launch_gram<StoreF32>(X, Y, N, Vh, hermitian, partials, nblocks, gate, s); break;
     case FK_F64: launch_gram<StoreF64>(X, Y, N, Vh, hermitian, partials, nblocks, gate, s); break;
+    case FK_H16: launch_gram<StoreH16>(X, Y, N, Vh, hermitian, partials, nblocks, gate, s); break;
+    case FK_BF16: launch_gram<StoreBF16>(X, Y, N, Vh, hermitian, partials, nblocks, gate, s); break;
   }
   return cudaGetLastError();
 }
@@ -371,6 +385,16 @@ cudaError_t w_update(FieldKind k, void* Q, const void* AP, const double2* beta, 
     case FK_F32: {
       size_t sm = (size_t)N * N * sizeof(cpx<float>);
       k_w_update<StoreF32><<<gcap(total, th, 152 * 8), th, sm, s>>>((float2*)Q, (const float2*)AP, beta, N, Vh, gate);
+      break;
+    }
+    case FK_H16: {
+      size_t sm = (size_t)N * N * sizeof(cpx<float>);
+      k_w_update<StoreH16><<<gcap(total, th, 152 * 8), th, sm, s>>>((__half2*)Q, (const __half2*)AP, beta, N, Vh, gate);
+      break;
+    }
+    case FK_BF16: {
+      size_t sm = (size_t)N * N * sizeof(cpx<float>);
+      k_w_update<StoreBF16><<<gcap(total, th, 152 * 8), th, sm, s>>>((__nv_bfloat162*)Q, (const __nv_bfloat162*)AP, beta, N, Vh, gate);
       break;
     }
     case FK_F64: {
@@ -581,6 +605,10 @@ cudaError_t bcg_update(FieldKind sk, FieldKind xk, void* Q, void* P, void* X, co
     return launch_bcg_update<StoreF32, StoreDF>(Q, P, X, Sinv, BC, SH, N, Vh, gate, s);
   if (sk == FK_F64 && xk == FK_F64)
     return launch_bcg_update<StoreF64, StoreF64>(Q, P, X, Sinv, BC, SH, N, Vh, gate, s);
+  if (sk == FK_H16 && xk == FK_DF)
+    return launch_bcg_update<StoreH16, StoreDF>(Q, P, X, Sinv, BC, SH, N, Vh, gate, s);
+  if (sk == FK_BF16 && xk == FK_DF)
+    return launch_bcg_update<StoreBF16, StoreDF>(Q, P, X, Sinv, BC, SH, N, Vh, gate, s);
   return cudaErrorInvalidValue;
 }
 
@@ -671,6 +699,10 @@ cudaError_t restart_update(FieldKind rk, FieldKind sk, const void* R, void* Q, v
     return launch_restart<StoreF64, StoreF32>(R, Q, P, Cinv, SH, init, N, Vh, gate, s);
   if (rk == FK_F64 && sk == FK_F64)
     return launch_restart<StoreF64, StoreF64>(R, Q, P, Cinv, SH, init, N, Vh, gate, s);
+  if (rk == FK_F64 && sk == FK_H16)
+    return launch_restart<StoreF64, StoreH16>(R, Q, P, Cinv, SH, init, N, Vh, gate, s);
+  if (rk == FK_F64 && sk == FK_BF16)
+    return launch_restart<StoreF64, StoreBF16>(R, Q, P, Cinv, SH, init, N, Vh, gate, s);
   return cudaErrorInvalidValue;
 }
 
@@ -723,6 +755,10 @@ cudaError_t convert_field(FieldKind from, FieldKind to, const void* in, void* ou
     k_convert<StoreDF, StoreF64><<<gcap(n, 256), 256, 0, s>>>((const double2*)in, (float4*)out, n, gate);
   else if (from == FK_F64 && to == FK_F32)
     k_convert<StoreF32, StoreF64><<<gcap(n, 256), 256, 0, s>>>((const double2*)in, (float2*)out, n, gate);
+  else if (from == FK_F64 && to == FK_H16)
+    k_convert<StoreH16, StoreF64><<<gcap(n, 256), 256, 0, s>>>((const double2*)in, (__half2*)out, n, gate);
+  else if (from == FK_F64 && to == FK_BF16)
+    k_convert<StoreBF16, StoreF64><<<gcap(n, 256), 256, 0, s>>>((const double2*)in, (__nv_bfloat162*)out, n, gate);
   else if (from == to)
     return cudaMemcpyAsync(out, in, n * elem_bytes(to), cudaMemcpyDeviceToDevice, s);
   else
@@ -785,6 +821,8 @@ cudaError_t block_caxpy(FieldKind k, const void* X, const double2* a, void* Y, i
   switch (k) {
     case FK_DF: return launch_block_mul<StoreDF>(X, a, Y, N, Vh, 0, s);
     case FK_F32: return launch_block_mul<StoreF32>(X, a, Y, N, Vh, 0, s);
+    case FK_H16: return launch_block_mul<StoreH16>(X, a, Y, N, Vh, 0, s);
+    case FK_BF16: return launch_block_mul<StoreBF16>(X, a, Y, N, Vh, 0, s);
     default: return launch_block_mul<StoreF64>(X, a, Y, N, Vh, 0, s);
   }
 }
@@ -794,6 +832,8 @@ cudaError_t block_trmul(FieldKind k, const void* M, const double2* Rinv, void* Q
   switch (k) {
     case FK_DF: return launch_block_mul<StoreDF>(M, Rinv, Q, N, Vh, 1, s);
     case FK_F32: return launch_block_mul<StoreF32>(M, Rinv, Q, N, Vh, 1, s);
+    case FK_H16: return launch_block_mul<StoreH16>(M, Rinv, Q, N, Vh, 1, s);
+    case FK_BF16: return launch_block_mul<StoreBF16>(M, Rinv, Q, N, Vh, 1, s);
     default: return launch_block_mul<StoreF64>(M, Rinv, Q, N, Vh, 1, s);
   }
 }
@@ -868,6 +908,13 @@ cudaError_t cg_axpy_norm(FieldKind k, FieldKind xk, void* x, void* r, const void
   else if (k == FK_F32 && xk == FK_DF)
     k_cg_axpy_norm<StoreF32, StoreDF><<<nblocks, 256, 0, s>>>(
         (float4*)x, (float2*)r, (const float2*)p, (const float2*)Ap, alpha, partials, n, gate);
+  else if (k == FK_H16 && xk == FK_DF)
+    k_cg_axpy_norm<StoreH16, StoreDF><<<nblocks, 256, 0, s>>>(
+        (float4*)x, (__half2*)r, (const __half2*)p, (const __half2*)Ap, alpha, partials, n, gate);
+  else if (k == FK_BF16 && xk == FK_DF)
+    k_cg_axpy_norm<StoreBF16, StoreDF><<<nblocks, 256, 0, s>>>(
+        (float4*)x, (__nv_bfloat162*)r, (const __nv_bfloat162*)p, (const __nv_bfloat162*)Ap, alpha,
+        partials, n, gate);
   else if (k == FK_F64 && xk == FK_F64)
     k_cg_axpy_norm<StoreF64, StoreF64><<<nblocks, 256, 0, s>>>(
         (double2*)x, (double2*)r, (const double2*)p, (const double2*)Ap, alpha, partials, n, gate);
@@ -888,6 +935,12 @@ cudaError_t cg_xpay(FieldKind k, void* p, const void* r, const double* beta, int
       break;
     case FK_F64:
       k_cg_xpay<StoreF64><<<gcap(n, 256), 256, 0, s>>>((double2*)p, (const double2*)r, beta, n, gate);
+      break;
+    case FK_H16:
+      k_cg_xpay<StoreH16><<<gcap(n, 256), 256, 0, s>>>((__half2*)p, (const __half2*)r, beta, n, gate);
+      break;
+    case FK_BF16:
+      k_cg_xpay<StoreBF16><<<gcap(n, 256), 256, 0, s>>>((__nv_bfloat162*)p, (const __nv_bfloat162*)r, beta, n, gate);
       break;
   }
   return cudaGetLastError();

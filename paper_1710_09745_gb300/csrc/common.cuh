@@ -233,6 +233,55 @@ struct StoreF64 {
   static __device__ __forceinline__ double2 to_double2(elem v) { return v; }
 };
 
+// 16-bit sloppy storage with FP32 arithmetic.  FP16 stores 2^10 x value:
+// Krylov block vectors are normalised, so their components are ~L^-1/2 and
+// the fixed power-of-two factor keeps them near 1, far above FP16's
+// subnormal range, without per-site scale arrays; the factor is exact in
+// both directions.  BF16 has FP32's exponent range and needs no factor.
+struct StoreH16 {
+  using elem = __half2;
+  using comp = CompF32;
+  static constexpr float SCALE = 1024.f;
+  static constexpr float INV = 1.f / 1024.f;
+  static __device__ __forceinline__ cpx<float> cvt(__half2 h) {
+    float2 f = __half22float2(h);
+    return {f.x * INV, f.y * INV};
+  }
+  static __device__ __forceinline__ cpx<float> load(const elem* p) { return cvt(__ldg(p)); }
+  static __device__ __forceinline__ cpx<float> load_nc(const elem* p) { return cvt(*p); }
+  static __device__ __forceinline__ void store(elem* p, const cpx<float>& a) {
+    *p = __floats2half2_rn(a.re * SCALE, a.im * SCALE);
+  }
+  static __device__ __forceinline__ elem from_double2(double2 z) {
+    return __floats2half2_rn(__double2float_rn(z.x) * SCALE, __double2float_rn(z.y) * SCALE);
+  }
+  static __device__ __forceinline__ double2 to_double2(elem v) {
+    float2 f = __half22float2(v);
+    return make_double2((double)f.x * INV, (double)f.y * INV);
+  }
+};
+
+struct StoreBF16 {
+  using elem = __nv_bfloat162;
+  using comp = CompF32;
+  static __device__ __forceinline__ cpx<float> cvt(__nv_bfloat162 h) {
+    float2 f = __bfloat1622float2(h);
+    return {f.x, f.y};
+  }
+  static __device__ __forceinline__ cpx<float> load(const elem* p) { return cvt(__ldg(p)); }
+  static __device__ __forceinline__ cpx<float> load_nc(const elem* p) { return cvt(*p); }
+  static __device__ __forceinline__ void store(elem* p, const cpx<float>& a) {
+    *p = __floats2bfloat162_rn(a.re, a.im);
+  }
+  static __device__ __forceinline__ elem from_double2(double2 z) {
+    return __floats2bfloat162_rn(__double2float_rn(z.x), __double2float_rn(z.y));
+  }
+  static __device__ __forceinline__ double2 to_double2(elem v) {
+    float2 f = __bfloat1622float2(v);
+    return make_double2((double)f.x, (double)f.y);
+  }
+};
+
 // Conversions between compute types (used where a sloppy block meets a
 // full-precision one, e.g. X += P (beta C) with P in FP32 and X in df).
 template <class To, class From>

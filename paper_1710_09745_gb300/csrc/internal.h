@@ -9,9 +9,11 @@
 namespace bcg {
 
 // Field storage kinds (element = one complex number).
-enum FieldKind { FK_DF = 0, FK_F32 = 1, FK_F64 = 2 };
+enum FieldKind { FK_DF = 0, FK_F32 = 1, FK_F64 = 2, FK_H16 = 3, FK_BF16 = 4 };
 
-inline size_t elem_bytes(FieldKind k) { return k == FK_F32 ? 8 : 16; }
+inline size_t elem_bytes(FieldKind k) {
+  return k == FK_F32 ? 8 : (k == FK_H16 || k == FK_BF16) ? 4 : 16;
+}
 
 // Kernel gating by the device status word, so that a host loop can enqueue
 // whole iterations without reading back the convergence state.
@@ -54,6 +56,17 @@ static constexpr int DSLASH_ASYNC = 0x200;
 cudaError_t dslash(FieldKind k, int R, int epi, const void* links, const void* in, void* out,
                    const void* c1, const void* c2, double m2, const Geom& g, int out_parity,
                    int N, Gate gate, cudaStream_t s);
+
+// per-kind stencil entry points (stencil_<kind>.cu)
+#define BCG_DSLASH_KIND_DECL(name)                                                             \
+  cudaError_t name(int R, int epi, const void* links, const void* in, void* out, const void* c1, \
+                   const void* c2, double m2, const Geom& g, int out_parity, int N, Gate gate,  \
+                   cudaStream_t s)
+BCG_DSLASH_KIND_DECL(dslash_df);
+BCG_DSLASH_KIND_DECL(dslash_f32);
+BCG_DSLASH_KIND_DECL(dslash_f64);
+BCG_DSLASH_KIND_DECL(dslash_h16);
+BCG_DSLASH_KIND_DECL(dslash_bf16);
 
 // ---- blas.cu
 cudaError_t to_internal(FieldKind k, const double2* user, void* internal, int N, int Vh,

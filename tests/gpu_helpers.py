@@ -10,7 +10,10 @@ import hisq_inputs as hi
 # from the arithmetic: a stencil output sums 48 complex products, so the
 # rounding bound is ~48 * u * max|term| with u = 2^-48 (double-float),
 # 2^-53 (FP64) or 2^-24 (FP32), and a factor ~4 of slack.
-TOL = {"f64": 1e-12, "f64_native": 1e-13, "mixed_f32": 2e-5}
+TOL = {"f64": 1e-12, "f64_native": 1e-13, "mixed_f32": 2e-5,
+       # 16-bit storage: each element rounded to 2^-11 (FP16) or 2^-8 (BF16)
+       # relative, ~sqrt(48) growth over the 48 terms of a stencil output
+       "mixed_f16": 1e-2, "mixed_bf16": 5e-2}
 
 
 def torch_mod():

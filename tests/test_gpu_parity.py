@@ -59,6 +59,63 @@ def test_solve_with_pipelined_stencil(variant):
     assert rel.max() <= 1e-10
 
 
+PRECS16 = ["mixed_f16", "mixed_bf16"]
+
+
+@pytest.mark.parametrize("prec", PRECS16)
+@pytest.mark.parametrize("variant", [0, 1, 2, 4, 8, TMA + 4, ASYNC + 4])
+@pytest.mark.parametrize("N,parity", [(1, 0), (3, 1), (8, 0), (16, 1)])
+def test_dslash_16bit(prec, variant, N, parity):
+    """16-bit storage with FP32 arithmetic; inputs at the magnitude of the
+    solver's normalised block vectors."""
+    s, fat, lng = gh.make_solver(DIMS, 0.1, prec=prec, seed=1013, max_rhs=16,
+                                 dslash_variant=variant)
+    psi = hi.gaussian_sources(DIMS, N, seed=120 + N) / np.sqrt(3 * psi_sites(DIMS))
+    out = gh.to_np(s.dslash(psi, parity))
+    ref = hisq.dslash(DIMS, fat, lng, psi, parity)
+    assert gh.rel_err(out, ref) < gh.TOL[prec]
+
+
+def psi_sites(dims):
+    return int(np.prod(dims)) // 2
+
+
+@pytest.mark.parametrize("prec", PRECS16)
+def test_apply_and_blas_16bit(prec):
+    N = 8
+    s, fat, lng = gh.make_solver(DIMS, 0.05, prec=prec, seed=1014, max_rhs=N)
+    sc = 1.0 / np.sqrt(3 * psi_sites(DIMS))
+    v = hi.gaussian_sources(DIMS, N, seed=130) * sc
+    w = hi.gaussian_sources(DIMS, N, seed=131) * sc
+    assert gh.rel_err(gh.to_np(s.apply_MdagM(v)), hisq.apply_A(DIMS, fat, lng, 0.05, v)) < gh.TOL[prec]
+    K = gh.to_np(s.block_cdot(v, w))
+    Kref = oblock.block_cdot(oblock.as_columns(v), oblock.as_columns(w))
+    assert np.abs(K - Kref).max() < gh.TOL[prec] * 0.1
+    Q, R = s.thin_qr(v)
+    Qr, Rr = oblock.thin_qr(oblock.as_columns(v))
+    assert gh.rel_err(gh.to_np(R), Rr) < gh.TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS16)
+def test_solve_16bit_reliable_updates(prec):
+    """Sloppy 16-bit iterations, FP64 reliable updates: the true residual still
+    reaches 1e-10 (Algorithm 3)."""
+    dims = (8, 8, 8, 8)
+    mass = 0.05
+    s, fat, lng = gh.make_solver(dims, mass, prec=prec, seed=1015, max_rhs=8)
+    b = hi.gaussian_sources(dims, 8, seed=2015)
+    X, info = s.solve(b, tol=1e-10)
+    assert info["status"] == 0, info
+    r = b - hisq.apply_A(dims, fat, lng, mass, gh.to_np(X))
+    rel = np.linalg.norm(r.reshape(8, -1), axis=1) / np.linalg.norm(b.reshape(8, -1), axis=1)
+    assert rel.max() <= 1e-10
+    Xc, ic = s.solve_cg(b[:2], tol=1e-10)
+    assert ic["status"] == 0, ic
+    rc = b[:2] - hisq.apply_A(dims, fat, lng, mass, gh.to_np(Xc))
+    relc = np.linalg.norm(rc.reshape(2, -1), axis=1) / np.linalg.norm(b[:2].reshape(2, -1), axis=1)
+    assert relc.max() <= 1e-10
+
+
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("N", [1, 5, 8])
 @pytest.mark.parametrize("antiperiodic", [False, True])
