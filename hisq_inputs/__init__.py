@@ -99,12 +99,14 @@ def unit_links(dims, long_coeff: float = LONG_COEFF):
 
 
 def random_links_torch(dims, seed: int, device, eps: float = EPS, long_coeff: float = LONG_COEFF,
-                       chunk: int = 1 << 22):
+                       chunk: int | None = None):
     """Same recipe as random_links, drawn with torch on `device` for lattices too
     large for NumPy set-up (different random stream than random_links)."""
     import torch
 
     V = volume(dims)
+    if chunk is None:
+        chunk = (1 << 21) if torch.device(device).type == "cuda" else (1 << 22)
     gen = torch.Generator(device=device)
     gen.manual_seed(seed)
     lam = torch.as_tensor(gell_mann() / 2, device=device)
@@ -115,9 +117,14 @@ def random_links_torch(dims, seed: int, device, eps: float = EPS, long_coeff: fl
             e = min(4 * V, s + chunk)
             w = torch.randn((e - s, 8), generator=gen, dtype=torch.float64, device=device)
             h = torch.einsum("na,aij->nij", w.to(torch.complex128), lam)
-            ev, q = torch.linalg.eigh(h)
-            ph = torch.exp(1j * eps * ev.to(torch.complex128))
-            u[s:e] = torch.einsum("nij,nj,nkj->nik", q, ph, q.conj())
+            if torch.device(device).type == "cuda":
+                # batched eigh on CUDA needs a huge workspace; the batched
+                # matrix exponential of i*eps*H gives the same SU(3) matrix
+                u[s:e] = torch.linalg.matrix_exp(1j * eps * h)
+            else:
+                ev, q = torch.linalg.eigh(h)
+                ph = torch.exp(1j * eps * ev.to(torch.complex128))
+                u[s:e] = torch.einsum("nij,nj,nkj->nik", q, ph, q.conj())
         fields.append(u.view(4, V, 3, 3))
     fat, lng = fields
     return fat, lng * long_coeff
