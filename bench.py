@@ -382,29 +382,34 @@ def main():
                               "true_rel_res_max": ic["true_rel_res_max"],
                               "block_speedup": (ic["ms_total"] / N) / value,
                               "stencil_avg_launch_ms": ic["ms_stencil"] / max(ic["n_stencil"], 1)}
-        # mixed-precision form
-        sm = BlockCG(dims, fat, lng, a.mass, prec="mixed_f32", max_rhs=max(N, 32), profile=True,
-                     device=dev)
-        sm.solve(B, tol=a.tol)
-        _, im = sm.solve(B, tol=a.tol)
-        _, imc = sm.solve_cg(B[:4], tol=a.tol)
-        out["mixed"] = {"ms_per_rhs": im["ms_total"] / N, "iters": im["iters"],
+        # mixed-precision forms (Algorithm 3): FP32 and FP16 sloppy storage
+        for key, prec in (("mixed", "mixed_f32"), ("mixed_f16", "mixed_f16")):
+            sm = BlockCG(dims, fat, lng, a.mass, prec=prec, max_rhs=max(N, 32), profile=True,
+                         device=dev)
+            sm.solve(B, tol=a.tol)
+            _, im = sm.solve(B, tol=a.tol)
+            _, imc = sm.solve_cg(B[:4], tol=a.tol)
+            out[key] = {"ms_per_rhs": im["ms_total"] / N, "iters": im["iters"],
                         "reliable_updates": im["reliable_updates"],
                         "true_rel_res_max": im["true_rel_res_max"],
                         "cg_ms_per_rhs": imc["ms_total"] / 4, "cg_iters_per_rhs": imc["iters"] / 4,
                         "block_speedup": (imc["ms_total"] / 4) / (im["ms_total"] / N)}
-        # Dslash GB/s per N (Fig. 1 analogue): FP32 (mixed) and double-float stencils
+            if prec == "mixed_f32":
+                s32 = sm
+            else:
+                s16 = sm
+        # Dslash GB/s per N (Fig. 1 analogue) for each storage format
         sweep = {}
         for n in (1, 4, 8, 16, 32):
             row = {}
-            for name, h, bpr in (("f32", sm, 4), ("df", s, 8)):
+            for name, h, bpr in (("f32", s32, 4), ("f16", s16, 2), ("df", s, 8)):
                 ms = h.bench_dslash(n, reps=10)
                 gbs = (288 + 12 * n) * bpr * Vh / (ms * 1e-3) / 1e9
                 row[name] = {"ms": ms, "gbs": gbs, "hbm_frac": gbs / hbm_peak,
                              "gflops": STENCIL_FLOPS * n * Vh / (ms * 1e-3) / 1e9}
             sweep[str(n)] = row
         out["dslash"] = sweep
-        del sm
+        del s32, s16
         # CPU oracle on a bounded sample (rank 0, one GPU)
         if world == 1:
             os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))

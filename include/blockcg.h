@@ -81,15 +81,20 @@ typedef enum {
  *  MIXED_F32   sloppy P, Q, AP, T and links in FP32 with FP32 arithmetic; X
  *              in double-float.
  *  MIXED_F16   as MIXED_F32 with P, Q, AP, T and links stored as IEEE FP16
- *              (2^10 x value, see below) and FP32 arithmetic.
- *  MIXED_BF16  as MIXED_F16 with bfloat16 storage (no factor).  Its 8-bit
- *              significand lets the sloppy recursion stagnate before the
- *              residual drops by ru_delta, so ru_every defaults to 10 for
- *              this form when the caller leaves it 0.
- *  FP16 storage keeps 2^10 times the value: the block vectors of the
+ *              (2^4 x value, see below) and FP32 arithmetic.
+ *  MIXED_BF16  as MIXED_F16 with bfloat16 storage (no factor).
+ *  With 16-bit storage the sloppy recursion can stagnate (bfloat16's 8-bit
+ *  significand) or drift (FP16 on ill-conditioned problems) before the
+ *  residual drops by ru_delta, so ru_every defaults to 10 for both 16-bit
+ *  forms when the caller leaves it 0.  In every form a reliable update also
+ *  happens when the iterated residual grows 100x above the true residual of
+ *  the last update.
+ *  FP16 storage keeps 2^4 times the value: the block vectors of the
  *  iteration are normalised (components ~ (3 V/2)^-1/2), so the fixed
- *  power-of-two factor keeps them near 1 and clear of FP16's subnormal range
- *  without per-site scale arrays.  */
+ *  power-of-two factor keeps them clear of FP16's subnormal range while
+ *  leaving ~10^5 of headroom for the growth of the search block P, without
+ *  per-site scale arrays.  Data given to the operator entry points of a
+ *  MIXED_F16 handle must fit |value| < 4000.  */
 typedef enum {
   BLOCKCG_PREC_F64 = 0,
   BLOCKCG_PREC_F64_NATIVE = 1,

@@ -419,9 +419,12 @@ blockcg_status blockcg_create(blockcg_t* out, const int dims[4], double mass,
     case BLOCKCG_PREC_MIXED_F16: h->sloppy = FK_H16; h->upd = FK_DF; break;
     case BLOCKCG_PREC_MIXED_BF16: h->sloppy = FK_BF16; h->upd = FK_DF; break;
   }
-  // bfloat16's 8-bit significand lets the sloppy recursion stagnate before
-  // the residual falls by ru_delta; a periodic reliable update keeps it going
-  if (prm.prec == BLOCKCG_PREC_MIXED_BF16 && h->p.ru_every == 0) h->p.ru_every = 10;
+  // with 16-bit storage the sloppy recursion can stagnate (bfloat16's 8-bit
+  // significand) or drift (FP16 on ill-conditioned problems) before the
+  // residual falls by ru_delta; a periodic reliable update keeps it on track
+  if ((prm.prec == BLOCKCG_PREC_MIXED_BF16 || prm.prec == BLOCKCG_PREC_MIXED_F16) &&
+      h->p.ru_every == 0)
+    h->p.ru_every = 10;
   h->gauge = nullptr;
   h->gauge_bytes = 0;
   h->links_fine = h->links_sloppy = nullptr;

@@ -233,16 +233,19 @@ struct StoreF64 {
   static __device__ __forceinline__ double2 to_double2(elem v) { return v; }
 };
 
-// 16-bit sloppy storage with FP32 arithmetic.  FP16 stores 2^10 x value:
-// Krylov block vectors are normalised, so their components are ~L^-1/2 and
-// the fixed power-of-two factor keeps them near 1, far above FP16's
-// subnormal range, without per-site scale arrays; the factor is exact in
-// both directions.  BF16 has FP32's exponent range and needs no factor.
+// 16-bit sloppy storage with FP32 arithmetic.  FP16 stores 2^4 x value:
+// Krylov block vectors are normalised, so the components of Q are ~L^-1/2
+// (1e-3 .. 1e-4 here); the fixed power-of-two factor lifts them well above
+// FP16's subnormal range while leaving ~10^5 of headroom for the growth of
+// the search block P (|P| ~ |r_k| / min_j |r_j| when the residual
+// oscillates) and for A P, without per-site scale arrays; the factor is
+// exact in both directions.  BF16 has FP32's exponent range and needs no
+// factor.
 struct StoreH16 {
   using elem = __half2;
   using comp = CompF32;
-  static constexpr float SCALE = 1024.f;
-  static constexpr float INV = 1.f / 1024.f;
+  static constexpr float SCALE = 16.f;
+  static constexpr float INV = 1.f / 16.f;
   static __device__ __forceinline__ cpx<float> cvt(__half2 h) {
     float2 f = __half22float2(h);
     return {f.x * INV, f.y * INV};

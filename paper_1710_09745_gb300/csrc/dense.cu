@@ -22,6 +22,9 @@
 namespace bcg {
 
 static constexpr int DENSE_THREADS = 256;
+// reliable update when the iterated residual exceeds this factor times the
+// true residual of the last update
+static constexpr double RU_GROWTH = 100.0;
 
 __device__ __forceinline__ double2 cm(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -212,6 +215,9 @@ __global__ void __launch_bounds__(DENSE_THREADS)
     if (rmax <= p.tol) ru = 1;
     else if (p.delta > 0.0 && rmax < p.delta * st->res_at_ru) ru = 1;
     else if (p.ru_every > 0 && (it % p.ru_every) == 0) ru = 1;
+    // the iterated residual has grown far above the last true one: the
+    // sloppy recursion is drifting, so recompute from the true residual
+    else if (rmax > RU_GROWTH * st->res_at_ru) ru = 1;
     st->ru_pending = ru;
   }
 }

@@ -28,6 +28,7 @@ def ensure_built():
 
 def make_solver(dims, mass, prec="f64", max_rhs=16, seed=1000, links=None, **kw):
     ensure_built()
+    kw.setdefault("max_iter", 20000)
     from paper_1710_09745_gb300 import BlockCG
     if links is None:
         links = hi.random_links(dims, seed)

@@ -81,6 +81,24 @@ def test_solve_full_size_f64(workload):
     assert err < 1e-8, err
 
 
+@pytest.mark.parametrize("prec", ["mixed_f32", "mixed_f16"])
+def test_solve_full_size_mixed(workload, prec):
+    """The benchmark workload in the mixed forms: the search block P grows by
+    orders of magnitude on this ill-conditioned problem, which must stay
+    within the 16-bit storage range."""
+    fat, lng, b = workload
+    s, _, _ = gh.make_solver(DIMS, MASS, prec=prec, links=(fat, lng), max_rhs=N, max_iter=3000)
+    X, info = s.solve(b, tol=1e-10)
+    assert info["status"] == 0, info
+    assert info["true_rel_res_max"] <= 1e-10
+    X = gh.to_np(X)
+    sites = _sample_sites(DIMS, 32, seed=10)
+    r = b[3][sites >> 1] - hisq.apply_A_sites(DIMS, fat, lng, MASS, X[3], sites)
+    rms_r = np.sqrt(np.mean(np.abs(r) ** 2))
+    rms_b = np.sqrt(np.mean(np.abs(b[3][sites >> 1]) ** 2))
+    assert rms_r / rms_b < 3e-10
+
+
 def test_config_48x96_n32_mixed_f16():
     """48^3 x 96, m = 0.01, N = 32, FP16 sloppy storage, FP32 arithmetic,
     FP64 Grams / Cholesky / reliable update every 10 iterations, to 1e-10."""
@@ -91,7 +109,7 @@ def test_config_48x96_n32_mixed_f16():
     b = hi.gaussian_sources_torch(dims, n, 2300, "cuda")
     gh.ensure_built()
     from paper_1710_09745_gb300 import BlockCG
-    s = BlockCG(dims, fat, lng, MASS, prec="mixed_f16", max_rhs=n, ru_every=10)
+    s = BlockCG(dims, fat, lng, MASS, prec="mixed_f16", max_rhs=n, ru_every=10, max_iter=5000)
     X, info = s.solve(b, tol=1e-10)
     assert info["status"] == 0, info
     assert info["true_rel_res_max"] <= 1e-10
