@@ -81,7 +81,7 @@ struct Ws {
   double2* mats;
   double* bnorm;
   SolverStatus* st;
-  double* scal;  // rr, alpha, beta, zero
+  double* scal;  // CG scalars: rr, alpha, beta, gamma, alpha / gamma
   int* ierr;
   int nblocks;
   size_t total;
@@ -654,6 +654,8 @@ blockcg_status blockcg_solve_cg(blockcg_t h, const void* B, void* X, int n_rhs, 
   double* rr = w.scal + 0;
   double* alpha = w.scal + 1;
   double* beta = w.scal + 2;
+  double* gam = w.scal + 3;      // scale of the iteration's r and p
+  double* alpha_x = w.scal + 4;  // alpha / gamma, the coefficient of the x update
   double2* red = mat(w, M_K, 1);
   int nb_cg = 2 * 152;
   Gate g0{nullptr, GATE_ALWAYS};
@@ -692,8 +694,9 @@ blockcg_status blockcg_solve_cg(blockcg_t h, const void* B, void* X, int n_rhs, 
         SL(1, dslash(fk, 1, EPI_RESIDUAL, h->links_fine, tf, rf, y, b, m2, h->g, 0, 1, ga, s));
         TL(TC_GRAM, gram_partials(fk, rf, rf, 1, Vh, 1, w.partials, w.nblocks, ga, s));
         TL(TC_GRAM, gram_reduce(w.partials, w.nblocks, 1, 1, red, ga, s));
-        TL(TC_DENSE, cg_restart_check(red, rr, beta, w.bnorm, tol, n_restart == 0, w.st, s));
-        TL(TC_STREAM, convert_field(fk, sk, rf, r, col, ga, s));
+        TL(TC_DENSE, cg_restart_check(red, rr, beta, gam, w.bnorm, (double)col, tol,
+                                      n_restart == 0, w.st, s));
+        TL(TC_STREAM, convert_field(fk, sk, rf, r, col, gam, ga, s));
         TL(TC_STREAM, cg_xpay(sk, p, r, beta, Vh, ga, s));
         restart = false;
         ++n_restart;
@@ -714,10 +717,10 @@ blockcg_status blockcg_solve_cg(blockcg_t h, const void* B, void* X, int n_rhs, 
         SL(0, dslash(sk, 1, EPI_NORMAL, h->links_sloppy, t, Ap, p, nullptr, m2, h->g, 0, 1, gi, s));
         TL(TC_GRAM, gram_partials(sk, p, Ap, 1, Vh, 1, w.partials, w.nblocks, gi, s));
         TL(TC_GRAM, gram_reduce(w.partials, w.nblocks, 1, 1, red, gi, s));
-        TL(TC_DENSE, cg_scalar_alpha(red, rr, alpha, w.st, gi, s));
-        TL(TC_STREAM, cg_axpy_norm(sk, xk, x, r, p, Ap, alpha, w.partials, nb_cg, Vh, gi, s));
+        TL(TC_DENSE, cg_scalar_alpha(red, rr, gam, alpha, alpha_x, w.st, gi, s));
+        TL(TC_STREAM, cg_axpy_norm(sk, xk, x, r, p, Ap, alpha, alpha_x, w.partials, nb_cg, Vh, gi, s));
         TL(TC_GRAM, gram_reduce(w.partials, nb_cg, 1, 1, red + 1, gi, s));
-        TL(TC_DENSE, cg_scalar_beta(red + 1, rr, beta, w.bnorm, tol, h->p.ru_delta, w.st, gi, s));
+        TL(TC_DENSE, cg_scalar_beta(red + 1, rr, beta, w.bnorm, gam, tol, h->p.ru_delta, w.st, gi, s));
         TL(TC_STREAM, cg_xpay(sk, p, r, beta, Vh, gi, s));
       }
       launched += n;

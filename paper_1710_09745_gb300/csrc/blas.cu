@@ -742,24 +742,31 @@ cudaError_t accumulate(FieldKind yk, FieldKind xk, void* Y, void* X, size_t n, G
 // ---------------------------------------------------- kind conversion ----
 template <class DS, class SS>
 __global__ void k_convert(const typename SS::elem* __restrict__ in, typename DS::elem* __restrict__ out,
-                          long long n, Gate gate) {
+                          long long n, const double* __restrict__ scale, Gate gate) {
   if (gate_closed(gate)) return;
+  const double f = scale ? *scale : 1.0;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
-       idx += (long long)gridDim.x * blockDim.x)
-    out[idx] = DS::from_double2(SS::to_double2(in[idx]));
+       idx += (long long)gridDim.x * blockDim.x) {
+    double2 v = SS::to_double2(in[idx]);
+    v.x *= f;
+    v.y *= f;
+    out[idx] = DS::from_double2(v);
+  }
 }
 
 cudaError_t convert_field(FieldKind from, FieldKind to, const void* in, void* out, size_t n,
-                          Gate gate, cudaStream_t s) {
+                          const double* scale, Gate gate, cudaStream_t s) {
   if (from == FK_F64 && to == FK_DF)
-    k_convert<StoreDF, StoreF64><<<gcap(n, 256), 256, 0, s>>>((const double2*)in, (float4*)out, n, gate);
+    k_convert<StoreDF, StoreF64><<<gcap(n, 256), 256, 0, s>>>((const double2*)in, (float4*)out, n, scale, gate);
   else if (from == FK_F64 && to == FK_F32)
-    k_convert<StoreF32, StoreF64><<<gcap(n, 256), 256, 0, s>>>((const double2*)in, (float2*)out, n, gate);
+    k_convert<StoreF32, StoreF64><<<gcap(n, 256), 256, 0, s>>>((const double2*)in, (float2*)out, n, scale, gate);
   else if (from == FK_F64 && to == FK_H16)
-    k_convert<StoreH16, StoreF64><<<gcap(n, 256), 256, 0, s>>>((const double2*)in, (__half2*)out, n, gate);
+    k_convert<StoreH16, StoreF64><<<gcap(n, 256), 256, 0, s>>>((const double2*)in, (__half2*)out, n, scale, gate);
   else if (from == FK_F64 && to == FK_BF16)
-    k_convert<StoreBF16, StoreF64><<<gcap(n, 256), 256, 0, s>>>((const double2*)in, (__nv_bfloat162*)out, n, gate);
-  else if (from == to)
+    k_convert<StoreBF16, StoreF64><<<gcap(n, 256), 256, 0, s>>>((const double2*)in, (__nv_bfloat162*)out, n, scale, gate);
+  else if (from == FK_F64 && to == FK_F64)
+    k_convert<StoreF64, StoreF64><<<gcap(n, 256), 256, 0, s>>>((const double2*)in, (double2*)out, n, scale, gate);
+  else if (from == to && !scale)
     return cudaMemcpyAsync(out, in, n * elem_bytes(to), cudaMemcpyDeviceToDevice, s);
   else
     return cudaErrorInvalidValue;
@@ -845,15 +852,15 @@ template <class S, class XS>
 __global__ void __launch_bounds__(256)
     k_cg_axpy_norm(typename XS::elem* __restrict__ x, typename S::elem* __restrict__ r,
                    const typename S::elem* __restrict__ p, const typename S::elem* __restrict__ Ap,
-                   const double* __restrict__ alpha_p, double2* __restrict__ partials, long long n,
-                   Gate gate) {
+                   const double* __restrict__ alpha_p, const double* __restrict__ alpha_x,
+                   double2* __restrict__ partials, long long n, Gate gate) {
   using C = typename S::comp;
   using CX = typename XS::comp;
   using real = typename C::real;
   using acc = typename C::acc;
   __shared__ double red[256];
   if (gate_closed(gate)) return;
-  const typename CX::real alphax = CX::from_double(*alpha_p);
+  const typename CX::real alphax = CX::from_double(*alpha_x);
   const real nalpha = C::from_double(-*alpha_p);
   acc nrm = C::zero();
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -899,25 +906,25 @@ __global__ void k_cg_xpay(typename S::elem* __restrict__ p, const typename S::el
 }
 
 cudaError_t cg_axpy_norm(FieldKind k, FieldKind xk, void* x, void* r, const void* p,
-                         const void* Ap, const double* alpha, double2* partials, int nblocks, int Vh,
-                         Gate gate, cudaStream_t s) {
+                         const void* Ap, const double* alpha, const double* alpha_x,
+                         double2* partials, int nblocks, int Vh, Gate gate, cudaStream_t s) {
   long long n = 3LL * Vh;
   if (k == FK_DF && xk == FK_DF)
     k_cg_axpy_norm<StoreDF, StoreDF><<<nblocks, 256, 0, s>>>(
-        (float4*)x, (float4*)r, (const float4*)p, (const float4*)Ap, alpha, partials, n, gate);
+        (float4*)x, (float4*)r, (const float4*)p, (const float4*)Ap, alpha, alpha_x, partials, n, gate);
   else if (k == FK_F32 && xk == FK_DF)
     k_cg_axpy_norm<StoreF32, StoreDF><<<nblocks, 256, 0, s>>>(
-        (float4*)x, (float2*)r, (const float2*)p, (const float2*)Ap, alpha, partials, n, gate);
+        (float4*)x, (float2*)r, (const float2*)p, (const float2*)Ap, alpha, alpha_x, partials, n, gate);
   else if (k == FK_H16 && xk == FK_DF)
     k_cg_axpy_norm<StoreH16, StoreDF><<<nblocks, 256, 0, s>>>(
-        (float4*)x, (__half2*)r, (const __half2*)p, (const __half2*)Ap, alpha, partials, n, gate);
+        (float4*)x, (__half2*)r, (const __half2*)p, (const __half2*)Ap, alpha, alpha_x, partials, n, gate);
   else if (k == FK_BF16 && xk == FK_DF)
     k_cg_axpy_norm<StoreBF16, StoreDF><<<nblocks, 256, 0, s>>>(
-        (float4*)x, (__nv_bfloat162*)r, (const __nv_bfloat162*)p, (const __nv_bfloat162*)Ap, alpha,
+        (float4*)x, (__nv_bfloat162*)r, (const __nv_bfloat162*)p, (const __nv_bfloat162*)Ap, alpha, alpha_x,
         partials, n, gate);
   else if (k == FK_F64 && xk == FK_F64)
     k_cg_axpy_norm<StoreF64, StoreF64><<<nblocks, 256, 0, s>>>(
-        (double2*)x, (double2*)r, (const double2*)p, (const double2*)Ap, alpha, partials, n, gate);
+        (double2*)x, (double2*)r, (const double2*)p, (const double2*)Ap, alpha, alpha_x, partials, n, gate);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();

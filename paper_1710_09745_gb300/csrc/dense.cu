@@ -347,7 +347,8 @@ cudaError_t dense_chol_upper(const double2* H, double2* R, double2* Rinv, int N,
 
 // ------------------------------------------------------------ CG scalars ----
 __global__ void k_cg_alpha(const double2* __restrict__ pAp, const double* __restrict__ rr,
-                           double* __restrict__ alpha, SolverStatus* st, int gmode) {
+                           const double* __restrict__ gam, double* __restrict__ alpha,
+                           double* __restrict__ alpha_x, SolverStatus* st, int gmode) {
   if (dense_gate_closed(st, gmode)) return;
   double d = pAp[0].x;
   if (!isfinite(d)) {
@@ -358,23 +359,26 @@ __global__ void k_cg_alpha(const double2* __restrict__ pAp, const double* __rest
     st->error = BLOCKCG_ERR_BREAKDOWN;
     return;
   }
-  *alpha = *rr / d;
+  const double a = *rr / d;
+  *alpha = a;
+  *alpha_x = a / *gam;  // x is kept unscaled: x += (alpha / gamma) (gamma p)
 }
 
 __global__ void k_cg_beta(const double2* __restrict__ rr_new_sum, double* __restrict__ rr,
-                          double* __restrict__ beta, const double* __restrict__ bnorm, double tol,
-                          double delta, SolverStatus* st, int gmode) {
+                          double* __restrict__ beta, const double* __restrict__ bnorm,
+                          const double* __restrict__ gam, double tol, double delta,
+                          SolverStatus* st, int gmode) {
   if (dense_gate_closed(st, gmode)) return;
   double bnorm2 = bnorm[0] * bnorm[0];
-  double rn = rr_new_sum[0].x;
+  double rn = rr_new_sum[0].x;  // |gamma r|^2
   int it = st->iters + 1;
   st->iters = it;
-  st->res_max = sqrt(rn / bnorm2);
   if (!isfinite(rn)) {
     st->error = BLOCKCG_ERR_NONFINITE;
     return;
   }
-  double rel = sqrt(rn / bnorm2);
+  double rel = sqrt(rn / bnorm2) / *gam;
+  st->res_max = rel;
   // converged, or dropped by delta since the last reliable update: the host
   // runs a reliable update, which recomputes r and then forms beta from the
   // true residual (cg_restart_check); rr keeps the previous |r|^2 for that
@@ -386,24 +390,30 @@ __global__ void k_cg_beta(const double2* __restrict__ rr_new_sum, double* __rest
   *rr = rn;
 }
 
-cudaError_t cg_scalar_alpha(const double2* pAp, const double* rr, double* alpha,
-                            SolverStatus* st, Gate gate, cudaStream_t s) {
-  k_cg_alpha<<<1, 1, 0, s>>>(pAp, rr, alpha, st, gate.mode);
+cudaError_t cg_scalar_alpha(const double2* pAp, const double* rr, const double* gam, double* alpha,
+                            double* alpha_x, SolverStatus* st, Gate gate, cudaStream_t s) {
+  k_cg_alpha<<<1, 1, 0, s>>>(pAp, rr, gam, alpha, alpha_x, st, gate.mode);
   return cudaGetLastError();
 }
 
 cudaError_t cg_scalar_beta(const double2* rr_new_sum, double* rr, double* beta,
-                           const double* bnorm, double tol, double delta, SolverStatus* st,
-                           Gate gate, cudaStream_t s) {
-  k_cg_beta<<<1, 1, 0, s>>>(rr_new_sum, rr, beta, bnorm, tol, delta, st, gate.mode);
+                           const double* bnorm, const double* gam, double tol, double delta,
+                           SolverStatus* st, Gate gate, cudaStream_t s) {
+  k_cg_beta<<<1, 1, 0, s>>>(rr_new_sum, rr, beta, bnorm, gam, tol, delta, st, gate.mode);
   return cudaGetLastError();
 }
 
+// The iteration works on gamma r and gamma p, gamma a power of two chosen at
+// every reliable update so that the entries of gamma r have unit root mean
+// square: CG's alpha and beta do not change under a common scaling of r and
+// p, and 16-bit storage keeps the shrinking residual within its exponent
+// range.  rr holds |gamma r|^2.
 __global__ void k_cg_restart_check(const double2* __restrict__ rr_sum, double* __restrict__ rr,
-                                   double* __restrict__ beta, const double* __restrict__ bnorm,
-                                   double tol, int init, SolverStatus* st) {
+                                   double* __restrict__ beta, double* __restrict__ gam,
+                                   const double* __restrict__ bnorm, double n_elems, double tol,
+                                   int init, SolverStatus* st) {
   if (st->error) return;
-  double rn = rr_sum[0].x;
+  double rn = rr_sum[0].x;  // true |r|^2
   double rel = sqrt(rn) / bnorm[0];
   st->true_res_max = rel;
   st->res_max = rel;
@@ -416,15 +426,20 @@ __global__ void k_cg_restart_check(const double2* __restrict__ rr_sum, double* _
     st->done = 1;
     return;
   }
-  // p = r + beta p with beta from the true residual (p = r at the start)
-  *beta = init ? 0.0 : rn / *rr;
-  *rr = rn;
+  const double g_new = exp2(rint(log2(sqrt(n_elems / rn))));
+  // p = r + beta p with beta from the true residual (p = r at the start);
+  // in scaled form gamma' p' = gamma' r + beta (gamma' / gamma) (gamma p)
+  const double g_old = *gam;
+  *beta = init ? 0.0 : (rn * g_old * g_old / *rr) * (g_new / g_old);
+  *rr = rn * g_new * g_new;
+  *gam = g_new;
   st->ru_pending = 0;
 }
 
-cudaError_t cg_restart_check(const double2* rr_sum, double* rr, double* beta, const double* bnorm,
-                             double tol, int init, SolverStatus* st, cudaStream_t s) {
-  k_cg_restart_check<<<1, 1, 0, s>>>(rr_sum, rr, beta, bnorm, tol, init, st);
+cudaError_t cg_restart_check(const double2* rr_sum, double* rr, double* beta, double* gam,
+                             const double* bnorm, double n_elems, double tol, int init,
+                             SolverStatus* st, cudaStream_t s) {
+  k_cg_restart_check<<<1, 1, 0, s>>>(rr_sum, rr, beta, gam, bnorm, n_elems, tol, init, st);
   return cudaGetLastError();
 }
 

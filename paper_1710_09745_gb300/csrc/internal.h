@@ -93,9 +93,10 @@ cudaError_t restart_update(FieldKind rk, FieldKind sk, const void* R, void* Q, v
 // Y (kind yk) += X (kind xk) ; X = 0
 cudaError_t accumulate(FieldKind yk, FieldKind xk, void* Y, void* X, size_t n_elems, Gate gate,
                        cudaStream_t s);
-// same-layout conversion between kinds (F64 -> DF, F64 -> F32, or a copy)
+// same-layout conversion between kinds (F64 -> any kind, or a copy), each
+// value multiplied by *scale when scale is not null
 cudaError_t convert_field(FieldKind from, FieldKind to, const void* in, void* out, size_t n_elems,
-                          Gate gate, cudaStream_t s);
+                          const double* scale, Gate gate, cudaStream_t s);
 // Y += X a (generic block caxpy)
 cudaError_t block_caxpy(FieldKind k, const void* X, const double2* a, void* Y, int N, int Vh,
                         cudaStream_t s);
@@ -103,9 +104,10 @@ cudaError_t block_caxpy(FieldKind k, const void* X, const double2* a, void* Y, i
 cudaError_t block_trmul(FieldKind k, const void* M, const double2* Rinv, void* Q, int N, int Vh,
                         cudaStream_t s);
 // CG (N = 1) helpers
+// x += alpha_x p ; r -= alpha Ap ; per-CTA partial sums of |r|^2
 cudaError_t cg_axpy_norm(FieldKind k, FieldKind xk, void* x, void* r, const void* p, const void* Ap,
-                         const double* alpha, double2* partials, int nblocks, int Vh, Gate gate,
-                         cudaStream_t s);
+                         const double* alpha, const double* alpha_x, double2* partials,
+                         int nblocks, int Vh, Gate gate, cudaStream_t s);
 cudaError_t cg_xpay(FieldKind k, void* p, const void* r, const double* beta, int Vh, Gate gate,
                     cudaStream_t s);
 cudaError_t copy_field(void* dst, const void* src, size_t bytes, cudaStream_t s);
@@ -134,16 +136,21 @@ cudaError_t dense_bnorm(const double2* Gb, double* bnorm, int N, SolverStatus* s
 // R upper with R^dag R = H, Rinv = R^-1; *err = blockcg_status
 cudaError_t dense_chol_upper(const double2* H, double2* R, double2* Rinv, int N, int* err,
                              cudaStream_t s);
-// CG scalars: alpha = rr / pAp ; on the second call beta = rr_new / rr, convergence
-cudaError_t cg_scalar_alpha(const double2* pAp, const double* rr, double* alpha,
-                            SolverStatus* st, Gate gate, cudaStream_t s);
+// CG scalars on the scaled iteration (gamma r, gamma p; rr = |gamma r|^2):
+// alpha = rr / pAp and alpha_x = alpha / gamma; on the second call
+// beta = rr_new / rr and the convergence / reliable-update test
+cudaError_t cg_scalar_alpha(const double2* pAp, const double* rr, const double* gam, double* alpha,
+                            double* alpha_x, SolverStatus* st, Gate gate, cudaStream_t s);
 cudaError_t cg_scalar_beta(const double2* rr_new_sum, double* rr, double* beta,
-                           const double* bnorm, double tol, double delta, SolverStatus* st,
-                           Gate gate, cudaStream_t s);
-// after a true-residual recomputation: done if it meets tol; else
-// beta = |r|^2 / rr (0 when init), rr = |r|^2, and the pending check is
-// cleared so that iterations resume
-cudaError_t cg_restart_check(const double2* rr_sum, double* rr, double* beta, const double* bnorm,
-                             double tol, int init, SolverStatus* st, cudaStream_t s);
+                           const double* bnorm, const double* gam, double tol, double delta,
+                           SolverStatus* st, Gate gate, cudaStream_t s);
+// after a true-residual recomputation: done if it meets tol; else a new
+// power-of-two gamma (unit RMS entries of gamma r for n_elems complex
+// entries), beta for p = r + beta p from the true residual in scaled form
+// (0 when init), rr = |gamma r|^2, and the pending check is cleared so that
+// iterations resume
+cudaError_t cg_restart_check(const double2* rr_sum, double* rr, double* beta, double* gam,
+                             const double* bnorm, double n_elems, double tol, int init,
+                             SolverStatus* st, cudaStream_t s);
 
 }  // namespace bcg
