@@ -27,8 +27,9 @@ def lib():
         L.oracle_apply_A_sites.argtypes = [P, P, P, I, D, P, P, ct.c_long, P]
         L.oracle_cg.argtypes = [P, P, P, I, D, P, P, I, D, I, P, P]
         L.oracle_cg_iterates.argtypes = [P, P, P, I, D, P, P, I]
+        L.oracle_link_grad.argtypes = [P, P, P, I, P, P, I, P, P]
         for f in (L.oracle_dslash, L.oracle_apply_A, L.oracle_apply_A_sites, L.oracle_cg,
-                  L.oracle_cg_iterates):
+                  L.oracle_cg_iterates, L.oracle_link_grad):
             f.restype = I
         _lib = L
     return _lib
@@ -128,3 +129,22 @@ def cg_iterates(dims, fat, lng, mass: float, b, n_iter: int, antiperiodic_t: boo
                                   _p(b), _p(x), int(n_iter))
     assert rc == 0, rc
     return x
+
+
+def link_grad(dims, fat, lng, x, lam, antiperiodic_t: bool = False):
+    """Gradient (dL/dRe + i dL/dIm) of a real loss with respect to the fat and
+    long links, given x = A^-1 phi and the adjoint lam = A^-1 dL/dx (even-site
+    blocks [N][V/2][3]); returns (gfat, glong), each [4][V][3][3]."""
+    fat, lng = _check_links(dims, fat, lng)
+    x = _c(x)
+    lam = _c(lam)
+    if x.ndim == 2:
+        x, lam = x[None], lam[None]
+    assert x.shape == lam.shape
+    gf = np.empty_like(fat)
+    gl = np.empty_like(lng)
+    d = _dims(dims)
+    rc = lib().oracle_link_grad(_p(d), _p(fat), _p(lng), int(antiperiodic_t), _p(x), _p(lam),
+                                x.shape[0], _p(gf), _p(gl))
+    assert rc == 0, rc
+    return gf, gl

@@ -330,3 +330,79 @@ int oracle_cg_iterates(const int dims[4], const cplx* fat, const cplx* lng, int 
   free(Ap);
   return 0;
 }
+
+/*
+ * Gradient of a real loss L with respect to the fat and long links (the
+ * derivative convention of complex automatic differentiation: for each link
+ * entry u, G = dL/dRe(u) + i dL/dIm(u), so that dL = Re sum conj(G) du).
+ * Inputs: the even-site solution block x = A^-1 phi and the adjoint block
+ * lam = A^-1 g, g being the gradient of L with respect to x.
+ *
+ * Derivation (Sec. 2.2 operator): dx = -A^-1 dA x, so dL = -Re lam^dag dA x,
+ * and with dA = -(dD_eo D_oe + D_eo dD_oe), D anti-Hermitian (D_eo^dag =
+ * -D_oe, and the same for dD), y = D_oe x and mu = D_oe lam:
+ *     dL = Re[lam^dag dD_eo y] + Re[x^dag dD_eo mu].
+ * A link U_mu(z) (fat: k = 1, long: k = 3) enters D_eo as the forward hop of
+ * the even site z, or (z odd) as the backward hop of the even site z + k mu,
+ * with weight c = 1/2 eta_mu(z) s (s the hop's boundary sign; eta_mu does not
+ * depend on x_mu).  Hence
+ *     z even: G_mu(z) =  c sum_i [lam_i(z) y_i(z+k mu)^dag + x_i(z) mu_i(z+k mu)^dag]
+ *     z odd:  G_mu(z) = -c sum_i [y_i(z) lam_i(z+k mu)^dag + mu_i(z) x_i(z+k mu)^dag].
+ * gfat, glong: complex [4][V][3][3] (the links' layout), either may be NULL.
+ */
+int oracle_link_grad(const int dims[4], const cplx* fat, const cplx* lng, int antiperiodic_t,
+                     const cplx* x, const cplx* lam, int n_rhs, cplx* gfat, cplx* glong) {
+  lattice g;
+  if (make_lattice(&g, dims) || n_rhs < 0) return -1;
+  long n = (long)n_rhs * g.Vh * 3;
+  cplx* y = (cplx*)malloc(sizeof(cplx) * (n ? n : 1));
+  cplx* mu_ = (cplx*)malloc(sizeof(cplx) * (n ? n : 1));
+  if (!y || !mu_) {
+    free(y);
+    free(mu_);
+    return -2;
+  }
+  oracle_dslash(dims, fat, lng, antiperiodic_t, x, y, 1, n_rhs);   /* y  = D_oe x   */
+  oracle_dslash(dims, fat, lng, antiperiodic_t, lam, mu_, 1, n_rhs); /* mu = D_oe lam */
+  for (int which = 0; which < 2; ++which) {
+    cplx* G = which ? glong : gfat;
+    int k = which ? 3 : 1;
+    if (!G) continue;
+#pragma omp parallel for schedule(static)
+    for (long z = 0; z < g.V; ++z) {
+      int c[4], w[4];
+      coords_of(&g, z, c);
+      int even = parity_of(c) == 0;
+      for (int m = 0; m < 4; ++m) {
+        double s = hop(&g, c, m, k, antiperiodic_t, w);
+        long wl = lex_of(&g, w);
+        double cf = 0.5 * eta(m, c) * s;
+        cplx* out = G + ((long)m * g.V + z) * 9;
+        for (int a = 0; a < 9; ++a) out[a] = 0;
+        for (int i = 0; i < n_rhs; ++i) {
+          const long off = (long)i * g.Vh * 3;
+          /* even z: (lam, x) at z with (y, mu) at z + k mu;
+             odd z:  (y, mu) at z with (lam, x) at z + k mu */
+          const cplx *a1, *b1, *a2, *b2;
+          if (even) {
+            a1 = lam + off + (z >> 1) * 3;
+            b1 = y + off + (wl >> 1) * 3;
+            a2 = x + off + (z >> 1) * 3;
+            b2 = mu_ + off + (wl >> 1) * 3;
+          } else {
+            a1 = y + off + (z >> 1) * 3;
+            b1 = lam + off + (wl >> 1) * 3;
+            a2 = mu_ + off + (z >> 1) * 3;
+            b2 = x + off + (wl >> 1) * 3;
+          }
+          for (int r = 0; r < 3; ++r)
+            for (int q = 0; q < 3; ++q)
+              out[r * 3 + q] += (even ? cf : -cf) * (a1[r] * conj(b1[q]) + a2[r] * conj(b2[q]));
+        }
+      }
+    }
+  }
+  free(y);
+  free(mu_);
+  return 0;
+}
