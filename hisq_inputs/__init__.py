@@ -139,3 +139,24 @@ def gaussian_sources_torch(dims, n_rhs: int, seed: int, device):
     re = torch.randn((n_rhs, Vh, 3), generator=gen, dtype=torch.float64, device=device)
     im = torch.randn((n_rhs, Vh, 3), generator=gen, dtype=torch.float64, device=device)
     return torch.complex(re, im)
+
+
+def batch_problems(count: int = 64, seed: int = 4000, extents=(8, 12, 16),
+                   mass_range=(0.01, 0.2), n_range=(2, 16)):
+    """A seeded set of independent problems for the batched solver: for each,
+    a hypercubic lattice L^4 with L drawn from `extents`, a mass uniform in
+    `mass_range`, a block width uniform in `n_range` (inclusive), and the seeds
+    of its links and sources.  Returns a list of dicts with keys dims, mass,
+    n_rhs, link_seed, source_seed."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for p in range(count):
+        L = int(rng.choice(extents))
+        out.append({
+            "dims": (L, L, L, L),
+            "mass": float(rng.uniform(*mass_range)),
+            "n_rhs": int(rng.integers(n_range[0], n_range[1] + 1)),
+            "link_seed": seed + 10 * p + 1,
+            "source_seed": seed + 10 * p + 2,
+        })
+    return out

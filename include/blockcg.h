@@ -178,6 +178,28 @@ blockcg_status blockcg_dslash(blockcg_t h, const void* in, void* out, int n_rhs,
  * in and out must not overlap.  Errors as blockcg_dslash. */
 blockcg_status blockcg_apply_MdagM(blockcg_t h, const void* in, void* out, int n_rhs);
 
+/* Gradient of a real loss L(x) of the solution x = A^-1 phi with respect to
+ * the fat and long links, in the convention G = dL/dRe(u) + i dL/dIm(u) per
+ * link entry u (so dL = Re sum conj(G) du; the convention of complex
+ * automatic differentiation).  The paper only solves; this is the link part
+ * of the adjoint of a differentiable solve (operator of Sec. 2.2, Eq. 1).
+ *
+ * X: the solution block x; Lam: the adjoint block lam = A^-1 g, g the
+ * gradient of L with respect to x (a second solve with the same handle,
+ * A being Hermitian).  Both device, user layout [n_rhs][Vh][3] on even sites.
+ * With y = D_oe x and mu = D_oe lam (computed here in native FP64 on the
+ * handle's FP64 links):
+ *   dL = Re[lam^dag dD_eo y] + Re[x^dag dD_eo mu], so for the link U_mu(z)
+ *   (fat: k = 1, long: k = 3; c = eta_mu(z) s / 2, s the hop's boundary sign)
+ *   z even: G =  c sum_i [lam_i(z) y_i(z+k mu)^dag + x_i(z) mu_i(z+k mu)^dag]
+ *   z odd:  G = -c sum_i [y_i(z) lam_i(z+k mu)^dag + mu_i(z) x_i(z+k mu)^dag].
+ * grad_fat, grad_long: device complex128 [4][V][3][3] (the links' layout),
+ * overwritten; either may be NULL to skip it.  Uses the workspace (n_rhs
+ * within its size); enqueues and returns.  Errors: ERR_ARG, ERR_NOMEM,
+ * ERR_CUDA. */
+blockcg_status blockcg_link_grad(blockcg_t h, const void* X, const void* Lam, int n_rhs,
+                                 void* grad_fat, void* grad_long);
+
 /* K = X^dag Y (block cDotProduct, Sec. 5.4): X, Y even-site blocks in user
  * layout; K device complex128 [n_rhs][n_rhs] row-major (K[i][j] = X_i^dag Y_j). */
 blockcg_status blockcg_block_cdot(blockcg_t h, const void* X, const void* Y, int n_rhs, void* K);
@@ -244,6 +266,66 @@ blockcg_status blockcg_bench_dslash(blockcg_t h, int n_rhs, int fine, int reps,
  * BLOCKCG_ERR_CUDA if the symbol lookup or a launch fails. */
 blockcg_status blockcg_block_cdot_noalloc(const void* X, const void* Y, int n_rhs, long long vh,
                                           void* K, void* stream);
+
+/* ---- Batched solves ------------------------------------------------------
+ *
+ * Many independent problems (lattices, masses, block widths), each a handle
+ * created, loaded and given a workspace as above, solved together: the
+ * per-iteration kernel sequence of blockcg_solve (Algorithm 1 with the gated
+ * reliable update of Algorithm 3) for every problem runs on a stream of its
+ * own, so small lattices that cannot fill the GPU alone run side by side.
+ * With BLOCKCG_BATCH_GRAPH, one chunk of iterations of every active problem
+ * is captured once into a single CUDA graph and replayed until each problem
+ * has converged, failed or reached its max_iter (the graph is captured again
+ * when the set of active problems changes).  The stencil autotuner runs once
+ * per (lattice, storage kind, N) and its choice is shared by the batch.
+ * Results are the same as blockcg_solve on each handle.  The paper solves
+ * one block at a time; batching many problems is this library's extension. */
+typedef struct blockcg_batch* blockcg_batch_t;
+
+#define BLOCKCG_BATCH_MAX 4096
+#define BLOCKCG_BATCH_GRAPH 1 /* flags bit: replay a captured CUDA graph */
+
+typedef struct {
+  double ms_total;         /* device time of the whole batch (CUDA events) */
+  int chunk;               /* iterations per replay (min of the problems' check_every) */
+  long long graph_replays; /* graph launches (0 without BLOCKCG_BATCH_GRAPH) */
+  long long graph_captures;
+  long long graph_nodes;   /* nodes of the last captured graph */
+  long long launches;      /* kernel launches executed (graph kernel nodes counted per replay) */
+} blockcg_batch_stats;
+
+/* problems: n distinct handles (1 <= n <= BLOCKCG_BATCH_MAX; the batch keeps
+ * the pointers, the handles must outlive it and must not be used elsewhere
+ * while a batch solve runs).  stream: cudaStream_t (NULL = legacy default);
+ * batch solves start after the work enqueued on it before the call and the
+ * stream waits for their end.  The batch owns one stream per problem plus
+ * one of its own, a few events and n status words of pinned host memory.
+ * Errors: BLOCKCG_ERR_ARG (null or repeated handles, n out of range),
+ * BLOCKCG_ERR_CUDA. */
+blockcg_status blockcg_batch_create(blockcg_batch_t* out, const blockcg_t* problems, int n,
+                                    void* stream);
+
+/* Solve problem p for B[p] (device, user layout, n_rhs[p] columns) with
+ * initial guess / result X[p], to the true relative residual tol for every
+ * column.  flags: BLOCKCG_BATCH_GRAPH or 0 (plain launches, same kernels).
+ * stats (optional, n entries): per-problem iterations, reliable updates and
+ * true residual; ms_total is the batch's.  status (optional, n entries): the
+ * per-problem outcome as blockcg_solve would return it.  bstats optional.
+ * While it runs, each handle's kernels go to the batch's stream for it and
+ * the handle's profile flag is off; both are restored on return.
+ * Synchronises.  Returns BLOCKCG_OK if every problem converged, else the
+ * first problem's failure (argument errors before any work: that problem's
+ * check, e.g. BLOCKCG_ERR_ARG or BLOCKCG_ERR_NOMEM); blockcg_batch_last_error
+ * names the problem. */
+blockcg_status blockcg_batch_solve(blockcg_batch_t b, const void* const* B, void* const* X,
+                                   const int* n_rhs, double tol, int flags, blockcg_stats* stats,
+                                   int* status, blockcg_batch_stats* bstats);
+
+/* Release the batch's streams, events, graph and pinned memory (not the
+ * problems' handles). */
+void blockcg_batch_destroy(blockcg_batch_t b);
+const char* blockcg_batch_last_error(blockcg_batch_t b);
 
 /* Release the handle (host memory only; caller-owned device buffers stay). */
 void blockcg_destroy(blockcg_t h);

@@ -6,6 +6,6 @@ C ABI of include/blockcg.h).  This package only marshals arguments: it holds
 device memory and streams through PyTorch and calls the library.  There is no
 CPU fallback; without the built library every call raises.
 """
-from .binding import BlockCG, BlockCGError, load_library, PREC  # noqa: F401
+from .binding import BlockCG, BlockCGBatch, BlockCGError, load_library, PREC  # noqa: F401
 
-__all__ = ["BlockCG", "BlockCGError", "load_library", "PREC"]
+__all__ = ["BlockCG", "BlockCGBatch", "BlockCGError", "load_library", "PREC"]

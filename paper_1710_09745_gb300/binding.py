@@ -28,8 +28,12 @@ ABI_SYMBOLS = [
     "blockcg_workspace_bytes", "blockcg_set_workspace", "blockcg_dslash", "blockcg_apply_MdagM",
     "blockcg_block_cdot", "blockcg_block_caxpy", "blockcg_thin_qr", "blockcg_solve",
     "blockcg_solve_cg", "blockcg_bench_dslash", "blockcg_destroy", "blockcg_status_string",
-    "blockcg_last_error", "blockcg_block_cdot_noalloc",
+    "blockcg_last_error", "blockcg_block_cdot_noalloc", "blockcg_batch_create",
+    "blockcg_batch_solve", "blockcg_batch_destroy", "blockcg_batch_last_error",
+    "blockcg_link_grad",
 ]
+
+BATCH_GRAPH = 1
 
 
 class Params(ct.Structure):
@@ -45,6 +49,12 @@ class Stats(ct.Structure):
                 ("ms_stencil", ct.c_double), ("n_stencil_fine", ct.c_longlong),
                 ("ms_stencil_fine", ct.c_double), ("ms_gram", ct.c_double),
                 ("ms_stream", ct.c_double), ("ms_dense", ct.c_double)]
+
+
+class BatchStats(ct.Structure):
+    _fields_ = [("ms_total", ct.c_double), ("chunk", ct.c_int), ("graph_replays", ct.c_longlong),
+                ("graph_captures", ct.c_longlong), ("graph_nodes", ct.c_longlong),
+                ("launches", ct.c_longlong)]
 
 
 class BlockCGError(RuntimeError):
@@ -85,6 +95,12 @@ def load_library(path: str = LIB_PATH):
         "blockcg_destroy": (None, [P]),
         "blockcg_status_string": (ct.c_char_p, [I]),
         "blockcg_last_error": (ct.c_char_p, [P]),
+        "blockcg_batch_create": (I, [ct.POINTER(P), ct.POINTER(P), I, P]),
+        "blockcg_batch_solve": (I, [P, ct.POINTER(P), ct.POINTER(P), ct.POINTER(I), D, I,
+                                    ct.POINTER(Stats), ct.POINTER(I), ct.POINTER(BatchStats)]),
+        "blockcg_batch_destroy": (None, [P]),
+        "blockcg_link_grad": (I, [P, P, P, I, P, P]),
+        "blockcg_batch_last_error": (ct.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -134,19 +150,29 @@ class BlockCG:
                                      ct.c_void_p(self.stream.cuda_stream)), None)
         self.h = h
         self.mass = float(mass)
-        fat = self._dev(fat, (4, self.V, 3, 3))
-        lng = self._dev(lng, (4, self.V, 3, 3))
-        nb = L.blockcg_gauge_bytes(h)
-        self.gauge = torch.empty(nb, dtype=torch.uint8, device=self.device)
-        self._check(L.blockcg_load_gauge(h, ct.c_void_p(fat.data_ptr()), ct.c_void_p(lng.data_ptr()),
-                                         ct.c_void_p(self.gauge.data_ptr()), nb))
-        self._links_keepalive = (fat, lng)
+        self.gauge = None
+        self.load_gauge(fat, lng)
         self.max_rhs = int(max_rhs)
         wb = L.blockcg_workspace_bytes(h, self.max_rhs)
         if wb == 0:
             raise BlockCGError(1, "max_rhs out of range")
         self.workspace = torch.empty(wb, dtype=torch.uint8, device=self.device)
         self._check(L.blockcg_set_workspace(h, ct.c_void_p(self.workspace.data_ptr()), wb))
+
+    def load_gauge(self, fat, lng):
+        """(Re)load the fat and long links (complex128 (4, V, 3, 3)); the library
+        repacks them into its internal copies."""
+        torch = _torch()
+        L = self.lib
+        fat = self._dev(fat, (4, self.V, 3, 3))
+        lng = self._dev(lng, (4, self.V, 3, 3))
+        nb = L.blockcg_gauge_bytes(self.h)
+        if self.gauge is None:
+            self.gauge = torch.empty(nb, dtype=torch.uint8, device=self.device)
+        self._check(L.blockcg_load_gauge(self.h, ct.c_void_p(fat.data_ptr()),
+                                         ct.c_void_p(lng.data_ptr()),
+                                         ct.c_void_p(self.gauge.data_ptr()), nb))
+        self._links_keepalive = (fat, lng)
 
     # ---------------------------------------------------------------- utils
     def _check(self, rc, h="self"):
@@ -230,6 +256,23 @@ class BlockCG:
                                              ct.c_void_p(R.data_ptr()), n))
         return Q, R
 
+    def link_grad(self, X, Lam, fat: bool = True, lng: bool = True):
+        """Gradient (dL/dRe + i dL/dIm) of a real loss with respect to the fat
+        and long links, from the solution block X = A^-1 phi and the adjoint
+        block Lam = A^-1 dL/dX (blockcg_link_grad); returns (grad_fat,
+        grad_long), complex128 (4, V, 3, 3) tensors (None where not asked)."""
+        torch = _torch()
+        X, Lam = self._block(X), self._block(Lam)
+        if X.shape != Lam.shape:
+            raise ValueError("X and Lam must have the same shape")
+        gf = torch.empty((4, self.V, 3, 3), dtype=torch.complex128, device=self.device) if fat else None
+        gl = torch.empty((4, self.V, 3, 3), dtype=torch.complex128, device=self.device) if lng else None
+        self._check(self.lib.blockcg_link_grad(
+            self.h, ct.c_void_p(X.data_ptr()), ct.c_void_p(Lam.data_ptr()), X.shape[0],
+            ct.c_void_p(gf.data_ptr() if gf is not None else 0),
+            ct.c_void_p(gl.data_ptr() if gl is not None else 0)))
+        return gf, gl
+
     # -------------------------------------------------------------- solvers
     def _solve(self, fn, B, X0, tol):
         torch = _torch()
@@ -261,3 +304,71 @@ class BlockCG:
         self._check(self.lib.blockcg_bench_dslash(self.h, int(n_rhs), int(bool(fine)), int(reps),
                                                   ct.byref(ms)))
         return ms.value
+
+
+class BlockCGBatch:
+    """Independent problems solved together (blockcg_batch_create/solve): one
+    stream per problem and, with graph=True, one captured CUDA graph per chunk
+    of iterations of every active problem.  `solvers`: distinct BlockCG
+    handles (each with its own lattice, mass, links and workspace)."""
+
+    def __init__(self, solvers):
+        torch = _torch()
+        self.solvers = list(solvers)
+        if not self.solvers:
+            raise ValueError("empty batch")
+        L = load_library()
+        self.lib = L
+        self.device = self.solvers[0].device
+        self.stream = torch.cuda.current_stream(self.device)
+        n = len(self.solvers)
+        hs = (ct.c_void_p * n)(*[s.h for s in self.solvers])
+        b = ct.c_void_p()
+        rc = L.blockcg_batch_create(ct.byref(b), hs, n, ct.c_void_p(self.stream.cuda_stream))
+        if rc != 0:
+            raise BlockCGError(rc, "blockcg_batch_create failed")
+        self.b = b
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.blockcg_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, Bs, X0s=None, tol: float = 1e-10, graph: bool = True, raise_on_error=True):
+        """Solve problem p for Bs[p] (shape (N_p, V_p/2, 3)); returns (Xs, infos, batch_info).
+        Problems that do not converge within max_iter keep their iterate and
+        report status 6 in their info."""
+        torch = _torch()
+        n = len(self.solvers)
+        if len(Bs) != n:
+            raise ValueError(f"expected {n} right-hand-side blocks, got {len(Bs)}")
+        Bd = [s._block(B) for s, B in zip(self.solvers, Bs)]
+        if X0s is None:
+            Xd = [torch.zeros_like(B) for B in Bd]
+        else:
+            Xd = [s._block(X).clone() for s, X in zip(self.solvers, X0s)]
+        for s, B in zip(self.solvers, Bd):
+            if B.shape[0] > s.max_rhs:
+                raise ValueError(f"block width {B.shape[0]} exceeds the handle's max_rhs {s.max_rhs}")
+        Bp = (ct.c_void_p * n)(*[B.data_ptr() for B in Bd])
+        Xp = (ct.c_void_p * n)(*[X.data_ptr() for X in Xd])
+        Np = (ct.c_int * n)(*[B.shape[0] for B in Bd])
+        st = (Stats * n)()
+        status = (ct.c_int * n)()
+        bst = BatchStats()
+        rc = self.lib.blockcg_batch_solve(self.b, Bp, Xp, Np, float(tol), BATCH_GRAPH if graph else 0,
+                                          st, status, ct.byref(bst))
+        infos = [{"iters": st[p].iters, "reliable_updates": st[p].reliable_updates,
+                  "true_rel_res_max": st[p].true_rel_res_max, "status": status[p]} for p in range(n)]
+        binfo = {"ms_total": bst.ms_total, "chunk": bst.chunk, "graph_replays": bst.graph_replays,
+                 "graph_captures": bst.graph_captures, "graph_nodes": bst.graph_nodes,
+                 "launches": bst.launches, "status": rc}
+        if rc not in (0, 6) and raise_on_error:
+            raise BlockCGError(rc, self.lib.blockcg_batch_last_error(self.b).decode())
+        return Xd, infos, binfo

@@ -346,6 +346,57 @@ blockcg_status status_to_result(blockcg_ctx* h, const SolverStatus& st) {
   return BLOCKCG_OK;
 }
 
+blockcg_status check_solve_args(blockcg_ctx* h, const void* B, const void* X, int n_rhs,
+                                double tol) {
+  blockcg_status rc = check_ready(h, n_rhs);
+  if (rc) return rc;
+  if (!B || !X) return fail(h, BLOCKCG_ERR_ARG, "null pointer");
+  if (!(tol > 0) || !std::isfinite(tol)) return fail(h, BLOCKCG_ERR_ARG, "tol must be > 0");
+  return BLOCKCG_OK;
+}
+
+// autotune the stencils a block solve of width N uses (no-op once cached)
+void tune_block(blockcg_ctx* h, const Ws& w, int N) {
+  stencil_R(h, h->sloppy, N, h->links_sloppy, w.P, w.Ts);
+  stencil_R(h, h->fine, N, h->links_fine, w.Y, w.Tf);
+}
+
+// Algorithm 1 set-up: B and X in internal layout, |b_i|, X = 0 (update),
+// P = 0, and the initial R = B - A Y, thin QR and P = Q (an ungated restart)
+blockcg_status solve_begin(blockcg_ctx* h, const Ws& w, const void* B, const void* X, int N,
+                           double tol) {
+  cudaStream_t s = h->stream;
+  size_t nel = (size_t)h->g.Vh * N * 3;
+  Gate g0{nullptr, GATE_ALWAYS};
+  Gate ga{w.st, GATE_ACTIVE};
+  CK(cudaMemsetAsync(w.st, 0, sizeof(SolverStatus), s));
+  KL(to_internal(h->fine, (const double2*)B, w.B, N, h->g.Vh, s));
+  KL(to_internal(h->fine, (const double2*)X, w.Y, N, h->g.Vh, s));
+  CK(zero_field(h->upd, w.X, nel, s));
+  CK(zero_field(h->sloppy, w.P, nel, s));
+  KL(gram_partials(h->fine, w.B, w.B, N, h->g.Vh, 1, w.partials, w.nblocks, g0, s));
+  KL(gram_reduce(w.partials, w.nblocks, N, 1, mat(w, M_G, N), g0, s));
+  KL(dense_bnorm(mat(w, M_G, N), w.bnorm, N, w.st, s));
+  return restart_block(h, w, N, tol, 1, ga);
+}
+
+// after the iterations: at max_iter fold the last update into Y and take the
+// true residual; write Y to the caller's X.  *result = the solve's outcome.
+blockcg_status solve_end(blockcg_ctx* h, const Ws& w, void* X, int N, double tol,
+                         SolverStatus* hs, blockcg_status* result) {
+  Gate g0{nullptr, GATE_ALWAYS};
+  *result = status_to_result(h, *hs);
+  if (!*result && !hs->done) {
+    blockcg_status rc = restart_block(h, w, N, tol, 1, g0);
+    if (rc) return rc;
+    rc = read_status(h, w, hs);
+    if (rc) return rc;
+    *result = hs->done ? BLOCKCG_OK : fail(h, BLOCKCG_ERR_NOT_CONVERGED, "max_iter reached");
+  }
+  KL(from_internal(h->fine, w.Y, (double2*)X, N, h->g.Vh, h->stream));
+  return BLOCKCG_OK;
+}
+
 }  // namespace
 
 // ===================================================================== ABI
@@ -513,6 +564,27 @@ blockcg_status blockcg_apply_MdagM(blockcg_t h, const void* in, void* out, int n
   return BLOCKCG_OK;
 }
 
+blockcg_status blockcg_link_grad(blockcg_t h, const void* X, const void* Lam, int n_rhs,
+                                 void* grad_fat, void* grad_long) {
+  blockcg_status rc = check_ready(h, n_rhs);
+  if (rc) return rc;
+  if (!X || !Lam || (!grad_fat && !grad_long)) return fail(h, BLOCKCG_ERR_ARG, "null pointer");
+  const int N = n_rhs;
+  Ws w = carve(h, N, h->ws);
+  cudaStream_t s = h->stream;
+  Gate g0{nullptr, GATE_ALWAYS};
+  const int R = cached_R(h, h->fine, N);
+  // native FP64: B = X, Y = Lam (even); Tf = D_oe X, R = D_oe Lam (odd)
+  KL(to_internal(FK_F64, (const double2*)X, w.B, N, h->g.Vh, s));
+  KL(to_internal(FK_F64, (const double2*)Lam, w.Y, N, h->g.Vh, s));
+  KL(dslash(FK_F64, R, EPI_NONE, h->links_fine, w.B, w.Tf, nullptr, nullptr, 0.0, h->g, 1, N, g0, s));
+  KL(dslash(FK_F64, R, EPI_NONE, h->links_fine, w.Y, w.R, nullptr, nullptr, 0.0, h->g, 1, N, g0, s));
+  KL(link_grad((const double2*)w.B, (const double2*)w.Y, (const double2*)w.Tf,
+               (const double2*)w.R, (double2*)grad_fat, (double2*)grad_long, h->g, N,
+               h->p.antiperiodic_t, s));
+  return BLOCKCG_OK;
+}
+
 blockcg_status blockcg_block_cdot(blockcg_t h, const void* X, const void* Y, int n_rhs, void* K) {
   blockcg_status rc = check_ready(h, n_rhs);
   if (rc) return rc;
@@ -563,32 +635,18 @@ blockcg_status blockcg_thin_qr(blockcg_t h, const void* M, void* Q, void* R, int
 
 blockcg_status blockcg_solve(blockcg_t h, const void* B, void* X, int n_rhs, double tol,
                              blockcg_stats* stats) {
-  blockcg_status rc = check_ready(h, n_rhs);
+  blockcg_status rc = check_solve_args(h, B, X, n_rhs, tol);
   if (rc) return rc;
-  if (!B || !X) return fail(h, BLOCKCG_ERR_ARG, "null pointer");
-  if (!(tol > 0) || !std::isfinite(tol)) return fail(h, BLOCKCG_ERR_ARG, "tol must be > 0");
   const int N = n_rhs;
   Ws w = carve(h, N, h->ws);
   cudaStream_t s = h->stream;
-  size_t nel = (size_t)h->g.Vh * N * 3;
-  Gate g0{nullptr, GATE_ALWAYS};
-  Gate ga{w.st, GATE_ACTIVE};
   reset_instrumentation(h);
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   CK(cudaEventRecord(e0, s));
-  CK(cudaMemsetAsync(w.st, 0, sizeof(SolverStatus), s));
-  KL(to_internal(h->fine, (const double2*)B, w.B, N, h->g.Vh, s));
-  KL(to_internal(h->fine, (const double2*)X, w.Y, N, h->g.Vh, s));
-  CK(zero_field(h->upd, w.X, nel, s));
-  CK(zero_field(h->sloppy, w.P, nel, s));
-  KL(gram_partials(h->fine, w.B, w.B, N, h->g.Vh, 1, w.partials, w.nblocks, g0, s));
-  KL(gram_reduce(w.partials, w.nblocks, N, 1, mat(w, M_G, N), g0, s));
-  KL(dense_bnorm(mat(w, M_G, N), w.bnorm, N, w.st, s));
-  stencil_R(h, h->sloppy, N, h->links_sloppy, w.P, w.Ts);
-  stencil_R(h, h->fine, N, h->links_fine, w.Y, w.Tf);
-  rc = restart_block(h, w, N, tol, 1, ga);
+  tune_block(h, w, N);
+  rc = solve_begin(h, w, B, X, N, tol);
   if (rc) return rc;
   const int chunk = default_check_every(h, N);
   SolverStatus hs;
@@ -607,16 +665,9 @@ blockcg_status blockcg_solve(blockcg_t h, const void* B, void* X, int n_rhs, dou
     }
     launched += n;
   }
-  blockcg_status result = status_to_result(h, hs);
-  if (!result && !hs.done) {
-    // max_iter reached: fold the last update into Y and report the true residual
-    rc = restart_block(h, w, N, tol, 1, g0);
-    if (rc) return rc;
-    rc = read_status(h, w, &hs);
-    if (rc) return rc;
-    result = hs.done ? BLOCKCG_OK : fail(h, BLOCKCG_ERR_NOT_CONVERGED, "max_iter reached");
-  }
-  KL(from_internal(h->fine, w.Y, (double2*)X, N, h->g.Vh, s));
+  blockcg_status result = BLOCKCG_OK;
+  rc = solve_end(h, w, X, N, tol, &hs, &result);
+  if (rc) return rc;
   CK(cudaEventRecord(e1, s));
   CK(cudaEventSynchronize(e1));
   drain_events(h);
@@ -785,6 +836,403 @@ blockcg_status blockcg_bench_dslash(blockcg_t h, int n_rhs, int fine, int reps,
   cudaEventDestroy(e1);
   *ms_per_launch = ms / reps;
   return BLOCKCG_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched solves.  Each problem keeps its own handle (lattice, mass, links,
+// workspace, status word) and a stream of the batch.  With graphs, the whole
+// iteration loop runs on the device: one CUDA graph holds, per problem, a
+// WHILE node whose body is a short chunk of gated iterations followed by a
+// one-thread kernel that sets the loop condition from the problem's status
+// word (not converged, no error, iteration budget left).  All WHILE nodes are
+// roots, so the problems run side by side, and one graph launch solves the
+// whole batch with no host round trips; the graph is built once per
+// configuration (block widths, tolerance, buffers) and reused.  Without
+// graphs, the host enqueues chunks on the problems' streams and polls.
+
+struct blockcg_batch {
+  std::vector<blockcg_ctx*> probs;
+  cudaStream_t user;    // the caller's stream: the batch starts and ends in its order
+  cudaStream_t origin;  // the batch's own stream (capture is not possible on a legacy stream)
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> done_ev;
+  cudaEvent_t fork_ev;
+  SolverStatus* host_st;  // pinned, one per problem
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  std::string graph_key;                  // configuration the graph was built for
+  size_t graph_nodes;                     // kernels in all loop bodies
+  std::vector<long long> graph_launches;  // kernel launches of one loop trip (or chunk), per problem
+  std::map<std::string, int> tuned;       // stencil tuning shared across problems
+  std::string err;
+};
+
+namespace {
+
+blockcg_status bfail(blockcg_batch* b, blockcg_status s, const std::string& msg) {
+  b->err = msg;
+  return s;
+}
+
+#define BK(call)                                                                             \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return bfail(b, BLOCKCG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// a problem's error, with the problem's index
+blockcg_status pfail(blockcg_batch* b, int p, blockcg_status rc) {
+  return bfail(b, rc, "problem " + std::to_string(p) + ": " + b->probs[p]->err);
+}
+
+void drop_graph(blockcg_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  b->graph_key.clear();
+}
+
+std::string tune_key(const blockcg_ctx* h, FieldKind k, int N) {
+  char buf[96];
+  snprintf(buf, sizeof(buf), "%d.%d.%d.%d/%d/%d", h->dims[0], h->dims[1], h->dims[2], h->dims[3],
+           (int)k, N);
+  return buf;
+}
+
+// stencil tuning of one problem, reusing the result of any earlier problem
+// with the same lattice, storage kind and N
+void batch_tune(blockcg_batch* b, blockcg_ctx* h, const Ws& w, int N) {
+  const FieldKind kinds[2] = {h->sloppy, h->fine};
+  if (!h->p.dslash_variant)
+    for (FieldKind k : kinds) {
+      auto it = b->tuned.find(tune_key(h, k, N));
+      if (it != b->tuned.end()) h->tuned_R[(int)k * 128 + N] = it->second;
+    }
+  tune_block(h, w, N);
+  if (!h->p.dslash_variant)
+    for (FieldKind k : kinds) b->tuned[tune_key(h, k, N)] = h->tuned_R[(int)k * 128 + N];
+}
+
+// one chunk of iterations of every active problem, each on its stream,
+// followed by the copy of its status word and the join into the origin
+// stream; returns the first problem error
+blockcg_status enqueue_chunk(blockcg_batch* b, const std::vector<char>& active,
+                             const std::vector<int>& N, int chunk, double tol) {
+  const int n = (int)b->probs.size();
+  BK(cudaEventRecord(b->fork_ev, b->origin));
+  for (int p = 0; p < n; ++p) {
+    if (!active[p]) continue;
+    blockcg_ctx* h = b->probs[p];
+    Ws w = carve(h, N[p], h->ws);
+    BK(cudaStreamWaitEvent(b->streams[p], b->fork_ev, 0));
+    long long l0 = h->launches;
+    for (int i = 0; i < chunk; ++i) {
+      blockcg_status rc = iterate_block(h, w, N[p], tol);
+      if (rc) return pfail(b, p, rc);
+    }
+    b->graph_launches[p] = h->launches - l0;
+    BK(cudaMemcpyAsync(&b->host_st[p], w.st, sizeof(SolverStatus), cudaMemcpyDeviceToHost,
+                       b->streams[p]));
+    BK(cudaEventRecord(b->done_ev[p], b->streams[p]));
+    BK(cudaStreamWaitEvent(b->origin, b->done_ev[p], 0));
+  }
+  return BLOCKCG_OK;
+}
+
+// iterations per loop trip of a problem in the device-looped graph
+int loop_chunk(const blockcg_ctx* h, int N) {
+  int c = default_check_every(h, N);
+  return c < 4 ? c : 4;
+}
+
+std::string graph_key_of(const blockcg_batch* b, const std::vector<int>& N, double tol) {
+  std::string k;
+  char buf[160];
+  snprintf(buf, sizeof(buf), "%.17g|", tol);
+  k += buf;
+  for (size_t p = 0; p < b->probs.size(); ++p) {
+    const blockcg_ctx* h = b->probs[p];
+    snprintf(buf, sizeof(buf), "%d,%p,%p,%d,%d,%g,%d;", N[p], (const void*)h->ws, h->gauge,
+             h->p.max_iter, h->p.ru_every, h->p.ru_delta, h->p.dslash_variant);
+    k += buf;
+  }
+  return k;
+}
+
+// one graph, one WHILE node per problem; each body = loop_chunk gated
+// iterations + the loop-condition kernel
+blockcg_status build_loop_graph(blockcg_batch* b, const std::vector<int>& N, double tol) {
+  drop_graph(b);
+  BK(cudaGraphCreate(&b->graph, 0));
+  size_t kernels = 0;
+  for (size_t p = 0; p < b->probs.size(); ++p) {
+    blockcg_ctx* h = b->probs[p];
+    Ws w = carve(h, N[p], h->ws);
+    const int chunk = loop_chunk(h, N[p]);
+    const int max_trips = (h->p.max_iter + chunk - 1) / chunk + 2;
+    cudaGraphConditionalHandle hnd;
+    BK(cudaGraphConditionalHandleCreate(&hnd, b->graph, 1, cudaGraphCondAssignDefault));
+    // zeroed storage: the parameter union has no default constructor
+    alignas(cudaGraphNodeParams) unsigned char np_raw[sizeof(cudaGraphNodeParams)];
+    memset(np_raw, 0, sizeof(np_raw));
+    cudaGraphNodeParams* np = reinterpret_cast<cudaGraphNodeParams*>(np_raw);
+    np->type = cudaGraphNodeTypeConditional;
+    np->conditional.handle = hnd;
+    np->conditional.type = cudaGraphCondTypeWhile;
+    np->conditional.size = 1;
+    cudaGraphNode_t node;
+    BK(cudaGraphAddNode(&node, b->graph, nullptr, nullptr, 0, np));
+    cudaGraph_t body = np->conditional.phGraph_out[0];
+    BK(cudaStreamBeginCaptureToGraph(b->streams[p], body, nullptr, nullptr, 0,
+                                     cudaStreamCaptureModeRelaxed));
+    const long long l0 = h->launches;
+    blockcg_status rc = BLOCKCG_OK;
+    for (int i = 0; i < chunk && !rc; ++i) rc = iterate_block(h, w, N[p], tol);
+    cudaError_t e = cudaSuccess;
+    if (!rc) {
+      e = loop_condition(hnd, w.st, max_trips, b->streams[p]);
+      ++h->launches;
+    }
+    cudaGraph_t captured = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(b->streams[p], &captured);
+    if (rc) {
+      cudaGetLastError();
+      drop_graph(b);
+      return pfail(b, (int)p, rc);
+    }
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      cudaGetLastError();
+      drop_graph(b);
+      return bfail(b, BLOCKCG_ERR_CUDA,
+                   std::string("loop graph capture: ") +
+                       cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    b->graph_launches[p] = h->launches - l0;
+    kernels += (size_t)(h->launches - l0);
+  }
+  BK(cudaGraphInstantiate(&b->exec, b->graph, 0));
+  b->graph_nodes = kernels;
+  b->graph_key = graph_key_of(b, N, tol);
+  return BLOCKCG_OK;
+}
+
+// restores each handle's stream and profiling flag when a batch solve ends
+struct BatchGuard {
+  blockcg_batch* b;
+  std::vector<cudaStream_t> s;
+  std::vector<int> prof;
+  explicit BatchGuard(blockcg_batch* bb) : b(bb) {
+    for (blockcg_ctx* h : b->probs) {
+      s.push_back(h->stream);
+      prof.push_back(h->p.profile);
+    }
+    for (size_t p = 0; p < b->probs.size(); ++p) {
+      b->probs[p]->stream = b->streams[p];
+      b->probs[p]->p.profile = 0;
+    }
+  }
+  ~BatchGuard() {
+    for (size_t p = 0; p < b->probs.size(); ++p) {
+      b->probs[p]->stream = s[p];
+      b->probs[p]->p.profile = prof[p];
+    }
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+blockcg_status blockcg_batch_create(blockcg_batch_t* out, const blockcg_t* problems, int n,
+                                    void* stream) {
+  if (!out) return BLOCKCG_ERR_ARG;
+  *out = nullptr;
+  if (!problems || n < 1 || n > BLOCKCG_BATCH_MAX) return BLOCKCG_ERR_ARG;
+  for (int p = 0; p < n; ++p) {
+    if (!problems[p]) return BLOCKCG_ERR_ARG;
+    for (int q = 0; q < p; ++q)
+      if (problems[q] == problems[p]) return BLOCKCG_ERR_ARG;  // one workspace per problem
+  }
+  blockcg_batch* b = new blockcg_batch();
+  b->user = (cudaStream_t)stream;
+  b->origin = nullptr;
+  b->graph = nullptr;
+  b->exec = nullptr;
+  b->graph_nodes = 0;
+  b->host_st = nullptr;
+  b->fork_ev = nullptr;
+  b->probs.assign(problems, problems + n);
+  b->graph_launches.assign(n, 0);
+  bool ok = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaMallocHost((void**)&b->host_st, n * sizeof(SolverStatus)) == cudaSuccess;
+  for (int p = 0; ok && p < n; ++p) {
+    cudaStream_t s = nullptr;
+    cudaEvent_t e = nullptr;
+    ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok) b->streams.push_back(s);
+    ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    if (ok) b->done_ev.push_back(e);
+  }
+  if (!ok) {
+    cudaGetLastError();
+    blockcg_batch_destroy(b);
+    return BLOCKCG_ERR_CUDA;
+  }
+  memset(b->host_st, 0, n * sizeof(SolverStatus));
+  *out = b;
+  return BLOCKCG_OK;
+}
+
+void blockcg_batch_destroy(blockcg_batch_t b) {
+  if (!b) return;
+  drop_graph(b);
+  for (cudaStream_t s : b->streams) {
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  }
+  for (cudaEvent_t e : b->done_ev) cudaEventDestroy(e);
+  if (b->origin) {
+    cudaStreamSynchronize(b->origin);
+    cudaStreamDestroy(b->origin);
+  }
+  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+  if (b->host_st) cudaFreeHost(b->host_st);
+  delete b;
+}
+
+const char* blockcg_batch_last_error(blockcg_batch_t b) { return b ? b->err.c_str() : "null batch"; }
+
+blockcg_status blockcg_batch_solve(blockcg_batch_t b, const void* const* B, void* const* X,
+                                   const int* n_rhs, double tol, int flags, blockcg_stats* stats,
+                                   int* status, blockcg_batch_stats* bstats) {
+  if (!b) return BLOCKCG_ERR_ARG;
+  if (!B || !X || !n_rhs) return bfail(b, BLOCKCG_ERR_ARG, "null pointer");
+  const int n = (int)b->probs.size();
+  std::vector<int> N(n);
+  for (int p = 0; p < n; ++p) {
+    blockcg_status rc = check_solve_args(b->probs[p], B[p], X[p], n_rhs[p], tol);
+    if (rc) return pfail(b, p, rc);
+    N[p] = n_rhs[p];
+  }
+  const bool use_graph = (flags & BLOCKCG_BATCH_GRAPH) != 0;
+  BatchGuard guard(b);
+  cudaEvent_t e0, e1;
+  BK(cudaEventCreate(&e0));
+  BK(cudaEventCreate(&e1));
+  // the batch runs after the caller's earlier work on its stream
+  BK(cudaEventRecord(b->fork_ev, b->user));
+  BK(cudaStreamWaitEvent(b->origin, b->fork_ev, 0));
+  BK(cudaEventRecord(e0, b->origin));
+  BK(cudaEventRecord(b->fork_ev, b->origin));
+  long long launches = 0;
+  // stencil tuning first (timed launches, one problem at a time), then the
+  // set-up of every problem on its own stream
+  for (int p = 0; p < n; ++p) {
+    blockcg_ctx* h = b->probs[p];
+    reset_instrumentation(h);
+    BK(cudaStreamWaitEvent(b->streams[p], b->fork_ev, 0));
+    batch_tune(b, h, carve(h, N[p], h->ws), N[p]);
+  }
+  int chunk = 32;
+  for (int p = 0; p < n; ++p) {
+    blockcg_ctx* h = b->probs[p];
+    Ws w = carve(h, N[p], h->ws);
+    long long l0 = h->launches;
+    blockcg_status rc = solve_begin(h, w, B[p], X[p], N[p], tol);
+    if (rc) return pfail(b, p, rc);
+    launches += h->launches - l0;
+    BK(cudaEventRecord(b->done_ev[p], b->streams[p]));
+    BK(cudaStreamWaitEvent(b->origin, b->done_ev[p], 0));
+    int c = default_check_every(h, N[p]);
+    if (c < chunk) chunk = c;
+  }
+  long long replays = 0, captures = 0;
+  if (use_graph) {
+    // the whole iteration loop of every problem in one graph launch
+    if (!b->exec || b->graph_key != graph_key_of(b, N, tol)) {
+      blockcg_status rc = build_loop_graph(b, N, tol);
+      if (rc) return rc;
+      ++captures;
+    }
+    BK(cudaGraphLaunch(b->exec, b->origin));
+    ++replays;
+    for (int p = 0; p < n; ++p) {
+      Ws w = carve(b->probs[p], N[p], b->probs[p]->ws);
+      BK(cudaMemcpyAsync(&b->host_st[p], w.st, sizeof(SolverStatus), cudaMemcpyDeviceToHost,
+                         b->origin));
+    }
+    BK(cudaStreamSynchronize(b->origin));
+    for (int p = 0; p < n; ++p) launches += b->host_st[p].trips * b->graph_launches[p];
+  } else {
+    // host-driven: chunks on the problems' streams, status polled between them
+    std::vector<char> active(n, 1);
+    std::vector<int> launched(n, 0);
+    for (;;) {
+      int n_active = 0;
+      for (int p = 0; p < n; ++p) n_active += active[p];
+      if (!n_active) break;
+      blockcg_status rc = enqueue_chunk(b, active, N, chunk, tol);
+      if (rc) return rc;
+      BK(cudaStreamSynchronize(b->origin));
+      for (int p = 0; p < n; ++p) {
+        if (!active[p]) continue;
+        launches += b->graph_launches[p];
+        launched[p] += chunk;
+        const SolverStatus& hs = b->host_st[p];
+        if (hs.done || hs.error || hs.iters >= b->probs[p]->p.max_iter ||
+            launched[p] >= b->probs[p]->p.max_iter)
+          active[p] = 0;
+      }
+    }
+  }
+  // results: max_iter handling and the copy-out, each problem on its stream
+  blockcg_status first = BLOCKCG_OK;
+  for (int p = 0; p < n; ++p) {
+    blockcg_ctx* h = b->probs[p];
+    Ws w = carve(h, N[p], h->ws);
+    SolverStatus hs = b->host_st[p];
+    blockcg_status result = BLOCKCG_OK;
+    long long l0 = h->launches;
+    blockcg_status rc = solve_end(h, w, X[p], N[p], tol, &hs, &result);
+    if (rc) return pfail(b, p, rc);
+    launches += h->launches - l0;
+    if (status) status[p] = result;
+    if (result && !first) {
+      first = result;
+      b->err = "problem " + std::to_string(p) + ": " + h->err;
+    }
+    if (stats) {
+      memset(&stats[p], 0, sizeof(blockcg_stats));
+      stats[p].iters = hs.iters;
+      stats[p].reliable_updates = hs.reliable_updates;
+      stats[p].true_rel_res_max = hs.true_res_max;
+    }
+    BK(cudaEventRecord(b->done_ev[p], b->streams[p]));
+    BK(cudaStreamWaitEvent(b->origin, b->done_ev[p], 0));
+  }
+  BK(cudaEventRecord(e1, b->origin));
+  BK(cudaStreamWaitEvent(b->user, e1, 0));
+  BK(cudaEventSynchronize(e1));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (stats)
+    for (int p = 0; p < n; ++p) stats[p].ms_total = ms;
+  if (bstats) {
+    bstats->ms_total = ms;
+    bstats->chunk = use_graph ? loop_chunk(b->probs[0], N[0]) : chunk;
+    bstats->graph_replays = replays;
+    bstats->graph_captures = captures;
+    bstats->graph_nodes = (long long)b->graph_nodes;
+    bstats->launches = launches;
+  }
+  return first;
 }
 
 }  // extern "C"

@@ -385,7 +385,8 @@ struct SolverStatus {
   int error;           // blockcg_status code of a device-detected failure
   int iters;           // iterations performed
   int reliable_updates;
-  int pad[2];
+  int stopped;         // 1: max_iter iterations done; the gated kernels stop
+  int trips;           // device-side loop trips (batched solves)
   double res_max;      // max relative iterated residual after the last iteration
   double res_at_ru;    // max relative residual at the last reliable update
   double true_res_max; // max relative true residual at the last check

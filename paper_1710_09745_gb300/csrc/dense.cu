@@ -107,7 +107,7 @@ __device__ void load_mat(double2* dst, const double2* __restrict__ src, int N) {
 __device__ __forceinline__ bool dense_gate_closed(const SolverStatus* st, int mode) {
   if (mode == GATE_ALWAYS || st == nullptr) return false;
   const volatile SolverStatus* s = st;
-  if (s->done || s->error) return true;
+  if (s->done || s->error || s->stopped) return true;
   if (mode == GATE_RU && !s->ru_pending) return true;
   if (mode == GATE_ITER && s->ru_pending) return true;
   return false;
@@ -219,6 +219,8 @@ __global__ void __launch_bounds__(DENSE_THREADS)
     // sloppy recursion is drifting, so recompute from the true residual
     else if (rmax > RU_GROWTH * st->res_at_ru) ru = 1;
     st->ru_pending = ru;
+    // the iteration budget is spent: later chunks of gated launches do nothing
+    if (p.max_iter > 0 && it >= p.max_iter) st->stopped = 1;
   }
 }
 
@@ -440,6 +442,27 @@ cudaError_t cg_restart_check(const double2* rr_sum, double* rr, double* beta, do
                              const double* bnorm, double n_elems, double tol, int init,
                              SolverStatus* st, cudaStream_t s) {
   k_cg_restart_check<<<1, 1, 0, s>>>(rr_sum, rr, beta, gam, bnorm, n_elems, tol, init, st);
+  return cudaGetLastError();
+}
+
+// Loop condition of a batched solve's device-side iteration loop (a CUDA
+// graph WHILE node): continue while the problem has neither converged,
+// failed nor used its iteration budget, and never beyond max_trips trips.
+__global__ void k_loop_condition(cudaGraphConditionalHandle handle, SolverStatus* st,
+                                 int max_trips) {
+  const int trips = st->trips + 1;
+  st->trips = trips;
+  unsigned go = (st->done || st->error || st->stopped) ? 0u : 1u;
+  if (trips >= max_trips) {
+    if (go) st->stopped = 1;
+    go = 0u;
+  }
+  cudaGraphSetConditional(handle, go);
+}
+
+cudaError_t loop_condition(cudaGraphConditionalHandle handle, SolverStatus* st, int max_trips,
+                           cudaStream_t s) {
+  k_loop_condition<<<1, 1, 0, s>>>(handle, st, max_trips);
   return cudaGetLastError();
 }
 

@@ -29,7 +29,7 @@ struct Gate {
 __device__ __forceinline__ bool gate_closed(const Gate& g) {
   if (g.mode == GATE_ALWAYS || g.st == nullptr) return false;
   const volatile SolverStatus* s = g.st;
-  if (s->done || s->error) return true;
+  if (s->done || s->error || s->stopped) return true;
   if (g.mode == GATE_RU && !s->ru_pending) return true;
   if (g.mode == GATE_ITER && s->ru_pending) return true;
   return false;
@@ -152,5 +152,18 @@ cudaError_t cg_scalar_beta(const double2* rr_new_sum, double* rr, double* beta,
 cudaError_t cg_restart_check(const double2* rr_sum, double* rr, double* beta, double* gam,
                              const double* bnorm, double n_elems, double tol, int init,
                              SolverStatus* st, cudaStream_t s);
+
+// one-thread kernel ending a batched solve's device-side loop trip: sets the
+// WHILE condition to "not done, no error, not stopped" (stops after max_trips)
+cudaError_t loop_condition(cudaGraphConditionalHandle handle, SolverStatus* st, int max_trips,
+                           cudaStream_t s);
+
+// ---- grad.cu
+// gradient of a real loss with respect to the links (user layout [4][V][3][3],
+// either output may be null) from the internal native-FP64 blocks X, Lam (even)
+// and Y = D_oe X, Mu = D_oe Lam (odd)
+cudaError_t link_grad(const double2* X, const double2* Lam, const double2* Y, const double2* Mu,
+                      double2* gfat, double2* glong, const Geom& g, int N, int antiperiodic_t,
+                      cudaStream_t s);
 
 }  // namespace bcg

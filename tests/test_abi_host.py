@@ -102,3 +102,42 @@ def test_binding_fails_loudly_without_library(tmp_path):
             binding.load_library(str(tmp_path / "missing.so"))
         finally:
             binding._lib = None
+
+
+def test_batch_entry_points_validate_without_gpu(lib):
+    """Argument checks of the batch entry points run before any CUDA call."""
+    b = ct.c_void_p()
+    assert lib.blockcg_batch_create(ct.byref(b), None, 1, None) == 1
+    hs = (ct.c_void_p * 2)(None, None)
+    assert lib.blockcg_batch_create(ct.byref(b), hs, 0, None) == 1
+    assert lib.blockcg_batch_create(ct.byref(b), hs, 2, None) == 1  # null handles
+    assert lib.blockcg_batch_create(None, hs, 2, None) == 1
+    assert lib.blockcg_batch_solve(None, None, None, None, 1e-10, 1, None, None, None) == 1
+    lib.blockcg_batch_destroy(None)
+    assert lib.blockcg_batch_last_error(None) == b"null batch"
+
+
+def test_batch_rejects_repeated_handles(lib):
+    """Two entries with the same handle would share one workspace."""
+    h = ct.c_void_p()
+    d = (ct.c_int * 4)(4, 4, 4, 4)
+    assert lib.blockcg_create(ct.byref(h), d, 0.1, None, None) == 0
+    try:
+        hs = (ct.c_void_p * 2)(h, h)
+        b = ct.c_void_p()
+        assert lib.blockcg_batch_create(ct.byref(b), hs, 2, None) == 1
+    finally:
+        lib.blockcg_destroy(h)
+
+
+def test_link_grad_validates_without_gpu(lib):
+    h = ct.c_void_p()
+    d = (ct.c_int * 4)(4, 4, 4, 4)
+    assert lib.blockcg_link_grad(None, None, None, 1, None, None) == 1
+    assert lib.blockcg_create(ct.byref(h), d, 0.1, None, None) == 0
+    try:
+        # no gauge field and no workspace yet: refused before any device work
+        assert lib.blockcg_link_grad(h, None, None, 1, None, None) != 0
+        assert lib.blockcg_link_grad(h, None, None, 0, None, None) == 1
+    finally:
+        lib.blockcg_destroy(h)
