@@ -61,6 +61,10 @@ def parse_args():
     ap.add_argument("--dslash-only", action="store_true",
                     help="only the stencil sweep (Fig. 1 analogue) for --prec over --sweep")
     ap.add_argument("--sweep", type=int, nargs="+", default=[1, 4, 8, 16, 32])
+    ap.add_argument("--batched-only", action="store_true",
+                    help="only the batched leg (64 small problems, one CUDA graph)")
+    ap.add_argument("--autograd-only", action="store_true",
+                    help="only the differentiable-solve leg (16^4, N = 8)")
     return ap.parse_args()
 
 
@@ -214,6 +218,90 @@ def run_reference(a):
 
 
 # -------------------------------------------------------------------- ours
+def batched_leg(tol, dev, count=64):
+    """Many small independent problems solved together (blockcg_batch_solve):
+    one CUDA graph per chunk of iterations, against plain per-problem streams
+    and against solving the problems one after another."""
+    import torch
+    import hisq_inputs as hi
+    from paper_1710_09745_gb300 import BlockCG, BlockCGBatch
+    specs = hi.batch_problems(count, seed=4000)
+    solvers, Bs = [], []
+    for sp in specs:
+        fat, lng = hi.random_links_torch(sp["dims"], sp["link_seed"], dev)
+        solvers.append(BlockCG(sp["dims"], fat, lng, sp["mass"], prec="mixed_f32",
+                               max_rhs=sp["n_rhs"], device=dev))
+        Bs.append(torch.as_tensor(hi.gaussian_sources(sp["dims"], sp["n_rhs"],
+                                                      sp["source_seed"])).to(dev))
+    batch = BlockCGBatch(solvers)
+    batch.solve(Bs, tol=tol, graph=True)  # tuning and first captures
+    _, ig, bg = batch.solve(Bs, tol=tol, graph=True)
+    _, ip, bp = batch.solve(Bs, tol=tol, graph=False)
+    seq = 0.0
+    for s, B in zip(solvers, Bs):
+        _, i = s.solve(B, tol=tol)
+        seq += i["ms_total"]
+    batch.close()
+    nrhs = sum(sp["n_rhs"] for sp in specs)
+    return {"workload": f"{count} problems L^4, L in {{8,12,16}}, m ~ U[0.01,0.2], N in 2..16 "
+                        "(seed 4000), mixed FP32 to 1e-10",
+            "rhs": nrhs, "graph_ms": bg["ms_total"], "streams_ms": bp["ms_total"],
+            "sequential_ms": seq, "graph_ms_per_rhs": bg["ms_total"] / nrhs,
+            "sequential_ms_per_rhs": seq / nrhs, "speedup_vs_sequential": seq / bg["ms_total"],
+            "speedup_vs_streams": bp["ms_total"] / bg["ms_total"],
+            "graph_replays": bg["graph_replays"], "graph_captures": bg["graph_captures"],
+            "graph_nodes": bg["graph_nodes"], "chunk": bg["chunk"], "launches": bg["launches"],
+            "all_converged": all(i["status"] == 0 for i in ig + ip),
+            "true_rel_res_max": max(i["true_rel_res_max"] for i in ig)}
+
+
+def autograd_leg(dev, tol=1e-10):
+    """Differentiable solve: L = sum_i phi_i^dag A^-1 phi_i on 16^4, m = 0.05,
+    N = 8 (F64 form); one forward + backward (two block solves and the
+    link-gradient kernel), and the gradient kernel alone."""
+    import torch
+    import hisq_inputs as hi
+    from paper_1710_09745_gb300 import BlockCG
+    from paper_1710_09745_gb300.autograd import hisq_solve
+    dims, mass, N = (16, 16, 16, 16), 0.05, 8
+    fat, lng = hi.random_links_torch(dims, 1300, dev)
+    s = BlockCG(dims, fat, lng, mass, prec="f64", max_rhs=N, device=dev)
+    phi = torch.as_tensor(hi.gaussian_sources(dims, N, 1301)).to(dev)
+    f = fat.clone().requires_grad_(True)
+    l = lng.clone().requires_grad_(True)
+
+    def step():
+        f.grad = None
+        l.grad = None
+        x = hisq_solve(f, l, phi, s, tol=tol)
+        (phi.conj() * x).sum().real.backward()
+        return x
+
+    x = step()  # tuning
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    e0.record(stream)
+    for _ in range(reps):
+        x = step()
+    e1.record(stream)
+    e1.synchronize()
+    fb = e0.elapsed_time(e1) / reps
+    xd = x.detach()
+    s.link_grad(xd, xd)
+    e0.record(stream)
+    for _ in range(10):
+        s.link_grad(xd, xd)
+    e1.record(stream)
+    e1.synchronize()
+    lg = e0.elapsed_time(e1) / 10
+    V = 16 ** 4
+    return {"workload": "16^4 m=0.05 N=8, L = sum phi^dag A^-1 phi, F64 form to 1e-10",
+            "ms_forward_backward": fb, "ms_link_grad": lg,
+            "link_grad_gbs": (2 * 2 * 6 * (V // 2) * N * 8 + 2 * 4 * V * 18 * 8) / (lg * 1e-3) / 1e9,
+            "grad_finite": bool(torch.isfinite(f.grad).all().item())}
+
+
 def dslash_only(a):
     """Stencil GB/s per N for one precision (no solve); one JSON line."""
     import numpy as np
@@ -244,6 +332,12 @@ def main():
         return
     if a.dslash_only:
         dslash_only(a)
+        return
+    if a.batched_only or a.autograd_only:
+        import torch
+        dev = torch.device("cuda", 0)
+        leg = batched_leg(a.tol, dev) if a.batched_only else autograd_leg(dev)
+        print(json.dumps({"batched" if a.batched_only else "autograd": leg}))
         return
     world, rank, local = dist_env()
     import numpy as np
@@ -314,8 +408,14 @@ def main():
     if a.prec == "f64":
         peak = SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6 / DF_INSTR_PER_FLOP / 1e12
         achieved = alg_flops / (avg_launch_ms * 1e-3) / 1e12
+        # ncu dram__bytes_read.sum + dram__bytes_write.sum of one 32^4 N=16 launch of the
+        # tuned double-float stencil (k_dslash_async<StoreDF, 2, 1, 0, 3>), 2.0x the
+        # algorithmic bytes; only that workload and kernel version
+        full = tuple(dims) == (32, 32, 32, 32) and N == 16
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": 4.04e9 if full else None,
+                "traffic_note": "ncu DRAM read+write of one k_dslash_async<StoreDF,2,1,0,3> "
+                                "launch at 32^4 N=16 (algorithmic 2.013e9)" if full else None,
                 "kernel": "k_dslash<StoreDF> (double-float stencil)",
                 "peak_note": "FP32 issue rate 152 SM x 128 lanes x 2070 MHz / 6 instr per "
                              "FP64-equivalent flop (double-float); derived, not measured",
@@ -410,6 +510,8 @@ def main():
             sweep[str(n)] = row
         out["dslash"] = sweep
         del s32, s16
+        out["batched"] = batched_leg(a.tol, dev)
+        out["autograd"] = autograd_leg(dev)
         # CPU oracle on a bounded sample (rank 0, one GPU)
         if world == 1:
             os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))

@@ -15,6 +15,8 @@
 //    Algorithm 1 using the P of this iteration, Sec. 5.2) and the next search
 //    block P = Q + P S^dag (Algorithm 1).  Coefficient columns are staged in
 //    chunks of JT columns so that N = 64 fits in shared memory.
+#include <type_traits>
+
 #include "internal.h"
 
 namespace bcg {
@@ -22,6 +24,21 @@ namespace bcg {
 static inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 // grid for grid-stride kernels: enough CTAs to fill the GPU, never a huge
 // grid of trivial CTAs (a gated-off launch then costs a few microseconds)
+// streaming multiprocessors of the current device (152 on a GB300)
+static int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) {
+      cudaGetLastError();
+      v = 152;
+    }
+    n = v;
+  }
+  return n;
+}
+
 static inline unsigned gcap(long long n, int t, unsigned cap = 152 * 8) {
   unsigned b = nblk(n, t);
   return b < cap ? (b ? b : 1) : cap;
@@ -413,9 +430,8 @@ struct TileCfg {
   int TS, JT;
 };
 
-static TileCfg tile_cfg(int N, size_t real_cplx_bytes, int n_tiles, int n_coefs) {
-  // shared memory budget ~ 96 KB
-  const size_t budget = 96 * 1024;
+static TileCfg tile_cfg(int N, size_t real_cplx_bytes, int n_tiles, int n_coefs,
+                        size_t budget = 96 * 1024) {
   int JT = N < 16 ? N : 16;
   size_t coef = (size_t)n_coefs * N * JT * real_cplx_bytes;
   int TS = 32;
@@ -426,7 +442,7 @@ static TileCfg tile_cfg(int N, size_t real_cplx_bytes, int n_tiles, int n_coefs)
 // Each thread produces JB consecutive output columns j of one row (site,
 // colour), so every W and P value read from shared memory feeds JB outputs.
 template <class SS, class XS, int JB>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
     k_bcg_update(typename SS::elem* __restrict__ Q, typename SS::elem* __restrict__ P,
                  typename XS::elem* __restrict__ X, const double2* __restrict__ Sinv,
                  const double2* __restrict__ BC, const double2* __restrict__ SH, int N, int Vh,
@@ -586,13 +602,39 @@ static cudaError_t launch_bcg_update(void* Q, void* P, void* X, const double2* S
                                      const double2* BC, const double2* SH, int N, int Vh,
                                      Gate gate, cudaStream_t s) {
   using real = typename SS::comp::real;
-  TileCfg t = tile_cfg(N + 1, sizeof(cpx<real>), 2, 3);
+  // double-float: 2 output columns per thread keep the accumulators within the
+  // register budget of four resident blocks (no spills); other kinds use 4
+  constexpr int JB = std::is_same<SS, StoreDF>::value ? 2 : 4;
+  // shared memory per block <= ~56 KB so that four blocks fit (up to N = 16)
+  TileCfg t = tile_cfg(N + 1, sizeof(cpx<real>), 2, 3, N <= 16 ? 56 * 1024 : 96 * 1024);
   size_t sm = ((size_t)2 * t.TS * (N + 1) * 3 + 3 * (size_t)N * t.JT) * sizeof(cpx<real>);
-  cudaFuncSetAttribute(k_bcg_update<SS, XS, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  unsigned blocks = gcap(Vh, t.TS, 152 * 8);
-  k_bcg_update<SS, XS, 4><<<blocks, 256, sm, s>>>((typename SS::elem*)Q, (typename SS::elem*)P,
-                                               (typename XS::elem*)X, Sinv, BC, SH, N, Vh, t.TS,
-                                               t.JT, gate);
+  cudaFuncSetAttribute(k_bcg_update<SS, XS, JB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  // a block size that divides a tile's (row, column group) work units, so no
+  // pass over a tile runs with part of the block idle
+  const int jt = t.JT < N ? t.JT : N;
+  const int units = t.TS * 3 * ((jt + JB - 1) / JB);
+  int threads = 256;
+  if (units <= 256) {
+    threads = (units + 31) / 32 * 32;
+  } else {
+    for (int th = 256; th >= 64; th -= 32)
+      if (units % th == 0) {
+        threads = th;
+        break;
+      }
+  }
+  // a persistent grid of exactly the resident blocks (no partial last wave)
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bcg_update<SS, XS, JB>, threads, sm) !=
+          cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  unsigned blocks = gcap(Vh, t.TS, num_sms() * per_sm);
+  k_bcg_update<SS, XS, JB><<<blocks, threads, sm, s>>>((typename SS::elem*)Q, (typename SS::elem*)P,
+                                                (typename XS::elem*)X, Sinv, BC, SH, N, Vh, t.TS,
+                                                t.JT, gate);
   return cudaGetLastError();
 }
 

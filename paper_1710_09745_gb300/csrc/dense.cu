@@ -82,21 +82,34 @@ __device__ int chol_lower(double2* A, int N, int* flag) {
   return 0;
 }
 
-// Linv = L^-1 for lower-triangular L (shared memory); parallel over columns.
+// Linv = L^-1 for lower-triangular L (shared memory), by forward
+// substitution on the identity, right-looking: step k finishes row k
+// (divide by L_kk) and removes its contribution from every later row, so each
+// step is one parallel update of the whole block and the dependent chain is N
+// steps long (a column-parallel substitution would leave N threads with
+// O(N^2) dependent FP64 operations each).
 __device__ void tri_inv_lower(const double2* L, double2* Linv, int N) {
   const int tid = threadIdx.x;
-  for (int idx = tid; idx < N * N; idx += blockDim.x) Linv[idx] = make_double2(0.0, 0.0);
-  __syncthreads();
-  for (int j = tid; j < N; j += blockDim.x) {
-    Linv[j * N + j] = make_double2(1.0 / L[j * N + j].x, 0.0);
-    for (int i = j + 1; i < N; ++i) {
-      double2 s = make_double2(0.0, 0.0);
-      for (int l = j; l < i; ++l) s = cadd(s, cm(L[i * N + l], Linv[l * N + j]));
-      double inv = 1.0 / L[i * N + i].x;
-      Linv[i * N + j] = make_double2(-s.x * inv, -s.y * inv);
-    }
+  for (int idx = tid; idx < N * N; idx += blockDim.x) {
+    const int i = idx / N, j = idx - (idx / N) * N;
+    Linv[idx] = make_double2(i == j ? 1.0 : 0.0, 0.0);
   }
   __syncthreads();
+  for (int k = 0; k < N; ++k) {
+    const double inv = 1.0 / L[k * N + k].x;
+    for (int j = tid; j <= k; j += blockDim.x) {
+      const double2 v = Linv[k * N + j];
+      Linv[k * N + j] = make_double2(v.x * inv, v.y * inv);
+    }
+    __syncthreads();
+    // rows i > k, columns j <= k: Linv_ij -= L_ik Linv_kj
+    const int m = N - k - 1;
+    for (int idx = tid; idx < m * (k + 1); idx += blockDim.x) {
+      const int i = k + 1 + idx / (k + 1), j = idx - (idx / (k + 1)) * (k + 1);
+      Linv[i * N + j] = csub(Linv[i * N + j], cm(L[i * N + k], Linv[k * N + j]));
+    }
+    __syncthreads();
+  }
 }
 
 __device__ void load_mat(double2* dst, const double2* __restrict__ src, int N) {
