@@ -285,6 +285,9 @@ typedef struct blockcg_batch* blockcg_batch_t;
 
 #define BLOCKCG_BATCH_MAX 4096
 #define BLOCKCG_BATCH_GRAPH 1 /* flags bit: replay a captured CUDA graph */
+/* flags bits 8..15: iterations per device-loop trip with BLOCKCG_BATCH_GRAPH
+ * (0: min(check_every, 4)) */
+#define BLOCKCG_BATCH_TRIP_SHIFT 8
 
 typedef struct {
   double ms_total;         /* device time of the whole batch (CUDA events) */
@@ -308,7 +311,8 @@ blockcg_status blockcg_batch_create(blockcg_batch_t* out, const blockcg_t* probl
 
 /* Solve problem p for B[p] (device, user layout, n_rhs[p] columns) with
  * initial guess / result X[p], to the true relative residual tol for every
- * column.  flags: BLOCKCG_BATCH_GRAPH or 0 (plain launches, same kernels).
+ * column.  flags: BLOCKCG_BATCH_GRAPH or 0 (plain launches, same kernels),
+ * plus (k << BLOCKCG_BATCH_TRIP_SHIFT) for k iterations per loop trip.
  * stats (optional, n entries): per-problem iterations, reliable updates and
  * true residual; ms_total is the batch's.  status (optional, n entries): the
  * per-problem outcome as blockcg_solve would return it.  bstats optional.

@@ -340,7 +340,8 @@ class BlockCGBatch:
         except Exception:
             pass
 
-    def solve(self, Bs, X0s=None, tol: float = 1e-10, graph: bool = True, raise_on_error=True):
+    def solve(self, Bs, X0s=None, tol: float = 1e-10, graph: bool = True, raise_on_error=True,
+              trip: int = 0):
         """Solve problem p for Bs[p] (shape (N_p, V_p/2, 3)); returns (Xs, infos, batch_info).
         Problems that do not converge within max_iter keep their iterate and
         report status 6 in their info."""
@@ -362,7 +363,8 @@ class BlockCGBatch:
         st = (Stats * n)()
         status = (ct.c_int * n)()
         bst = BatchStats()
-        rc = self.lib.blockcg_batch_solve(self.b, Bp, Xp, Np, float(tol), BATCH_GRAPH if graph else 0,
+        flags = (BATCH_GRAPH if graph else 0) | ((int(trip) & 0xff) << 8)
+        rc = self.lib.blockcg_batch_solve(self.b, Bp, Xp, Np, float(tol), flags,
                                           st, status, ct.byref(bst))
         infos = [{"iters": st[p].iters, "reliable_updates": st[p].reliable_updates,
                   "true_rel_res_max": st[p].true_rel_res_max, "status": status[p]} for p in range(n)]

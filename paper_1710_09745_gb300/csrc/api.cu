@@ -943,16 +943,19 @@ blockcg_status enqueue_chunk(blockcg_batch* b, const std::vector<char>& active,
   return BLOCKCG_OK;
 }
 
-// iterations per loop trip of a problem in the device-looped graph
-int loop_chunk(const blockcg_ctx* h, int N) {
+// iterations per loop trip of a problem in the device-looped graph: the
+// caller's choice (flags bits 8..15), else min(check_every, 4)
+int loop_chunk(const blockcg_ctx* h, int N, int flags) {
+  const int req = (flags >> 8) & 0xff;
+  if (req > 0) return req;
   int c = default_check_every(h, N);
   return c < 4 ? c : 4;
 }
 
-std::string graph_key_of(const blockcg_batch* b, const std::vector<int>& N, double tol) {
+std::string graph_key_of(const blockcg_batch* b, const std::vector<int>& N, double tol, int flags) {
   std::string k;
   char buf[160];
-  snprintf(buf, sizeof(buf), "%.17g|", tol);
+  snprintf(buf, sizeof(buf), "%.17g|%d|", tol, flags);
   k += buf;
   for (size_t p = 0; p < b->probs.size(); ++p) {
     const blockcg_ctx* h = b->probs[p];
@@ -965,14 +968,15 @@ std::string graph_key_of(const blockcg_batch* b, const std::vector<int>& N, doub
 
 // one graph, one WHILE node per problem; each body = loop_chunk gated
 // iterations + the loop-condition kernel
-blockcg_status build_loop_graph(blockcg_batch* b, const std::vector<int>& N, double tol) {
+blockcg_status build_loop_graph(blockcg_batch* b, const std::vector<int>& N, double tol,
+                                int flags) {
   drop_graph(b);
   BK(cudaGraphCreate(&b->graph, 0));
   size_t kernels = 0;
   for (size_t p = 0; p < b->probs.size(); ++p) {
     blockcg_ctx* h = b->probs[p];
     Ws w = carve(h, N[p], h->ws);
-    const int chunk = loop_chunk(h, N[p]);
+    const int chunk = loop_chunk(h, N[p], flags);
     const int max_trips = (h->p.max_iter + chunk - 1) / chunk + 2;
     cudaGraphConditionalHandle hnd;
     BK(cudaGraphConditionalHandleCreate(&hnd, b->graph, 1, cudaGraphCondAssignDefault));
@@ -1016,7 +1020,7 @@ blockcg_status build_loop_graph(blockcg_batch* b, const std::vector<int>& N, dou
   }
   BK(cudaGraphInstantiate(&b->exec, b->graph, 0));
   b->graph_nodes = kernels;
-  b->graph_key = graph_key_of(b, N, tol);
+  b->graph_key = graph_key_of(b, N, tol, flags);
   return BLOCKCG_OK;
 }
 
@@ -1154,8 +1158,8 @@ blockcg_status blockcg_batch_solve(blockcg_batch_t b, const void* const* B, void
   long long replays = 0, captures = 0;
   if (use_graph) {
     // the whole iteration loop of every problem in one graph launch
-    if (!b->exec || b->graph_key != graph_key_of(b, N, tol)) {
-      blockcg_status rc = build_loop_graph(b, N, tol);
+    if (!b->exec || b->graph_key != graph_key_of(b, N, tol, flags)) {
+      blockcg_status rc = build_loop_graph(b, N, tol, flags);
       if (rc) return rc;
       ++captures;
     }
@@ -1226,7 +1230,7 @@ blockcg_status blockcg_batch_solve(blockcg_batch_t b, const void* const* B, void
     for (int p = 0; p < n; ++p) stats[p].ms_total = ms;
   if (bstats) {
     bstats->ms_total = ms;
-    bstats->chunk = use_graph ? loop_chunk(b->probs[0], N[0]) : chunk;
+    bstats->chunk = use_graph ? loop_chunk(b->probs[0], N[0], flags) : chunk;
     bstats->graph_replays = replays;
     bstats->graph_captures = captures;
     bstats->graph_nodes = (long long)b->graph_nodes;
