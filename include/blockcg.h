@@ -119,6 +119,15 @@ typedef struct {
                           else R in {1, 2, 4, 8} right-hand sides per thread,
                           plus 256 for the bulk-copy (TMA) pipelined kernel or
                           512 for the per-thread cp.async prefetch kernel */
+  int link_recon;      /* iteration links of the 32- and 16-bit forms: 0 = all 18
+                          reals per link (default); 12 = the first two rows only,
+                          the third rebuilt in the stencil as conj(row0 x row1)
+                          divided by the link's scale.  Needs every fat link to
+                          be c_f U and every long link c_l U with U in SU(3) and
+                          c_f, c_l real constants (e.g. 1 and -1/24), which
+                          blockcg_load_gauge checks (BLOCKCG_ERR_ARG otherwise);
+                          only with MIXED_F32 / MIXED_F16 / MIXED_BF16 (the
+                          FP64 links of the reliable updates stay complete) */
 } blockcg_params;
 
 typedef struct {
@@ -134,6 +143,9 @@ typedef struct {
   double ms_gram;          /* params.profile: Gram partials + reductions (Sec. 5.4) */
   double ms_stream;        /* params.profile: streaming block BLAS (Sec. 5.3) */
   double ms_dense;         /* params.profile: N x N algebra on the device */
+  int stencil_variant;     /* the iteration stencil's kernel choice (the
+                              params.dslash_variant encoding, plus 1024 for
+                              two-row links) */
 } blockcg_stats;
 
 /* Fill *p with the defaults listed above. */
@@ -155,8 +167,12 @@ size_t blockcg_gauge_bytes(blockcg_t h);
  * the 16 hop matrices of Eq. 1 with staggered phases, the factor 1/2, the
  * boundary sign and the backward-hop dagger and minus sign folded in, in
  * the storage formats the precision needs.  The caller may free fat/lng once
- * the stream has passed this call.  Errors: ERR_ARG (null), ERR_NOMEM
- * (storage too small), ERR_CUDA. */
+ * the stream has passed this call.  With params.link_recon = 12 it first
+ * checks on the device that all fat links are c_f U and all long links c_l U
+ * (U unitary with determinant 1, c real, taken from the first link of each
+ * kind; tolerance 1e-10 relative) and synchronises the stream to read the
+ * result.  Errors: ERR_ARG (null, or links not of that form with
+ * link_recon = 12), ERR_NOMEM (storage too small), ERR_CUDA. */
 blockcg_status blockcg_load_gauge(blockcg_t h, const void* fat, const void* lng, void* storage,
                                   size_t storage_bytes);
 

@@ -39,7 +39,7 @@ BATCH_GRAPH = 1
 class Params(ct.Structure):
     _fields_ = [("max_iter", ct.c_int), ("ru_delta", ct.c_double), ("ru_every", ct.c_int),
                 ("prec", ct.c_int), ("antiperiodic_t", ct.c_int), ("check_every", ct.c_int),
-                ("profile", ct.c_int), ("dslash_variant", ct.c_int)]
+                ("profile", ct.c_int), ("dslash_variant", ct.c_int), ("link_recon", ct.c_int)]
 
 
 class Stats(ct.Structure):
@@ -48,7 +48,8 @@ class Stats(ct.Structure):
                 ("launches", ct.c_longlong), ("n_stencil", ct.c_longlong),
                 ("ms_stencil", ct.c_double), ("n_stencil_fine", ct.c_longlong),
                 ("ms_stencil_fine", ct.c_double), ("ms_gram", ct.c_double),
-                ("ms_stream", ct.c_double), ("ms_dense", ct.c_double)]
+                ("ms_stream", ct.c_double), ("ms_dense", ct.c_double),
+                ("stencil_variant", ct.c_int)]
 
 
 class BatchStats(ct.Structure):
@@ -118,14 +119,17 @@ def _torch():
 class BlockCG:
     """Handle on one lattice + gauge field + mass (blockcg_create/load_gauge).
 
-    prec: "f64" (double-float FP64-accurate form), "f64_native", "mixed_f32".
+    prec: "f64" (double-float FP64-accurate form), "f64_native", "mixed_f32",
+    "mixed_f16", "mixed_bf16".
     max_rhs: the largest block width the workspace is sized for.
+    link_recon: 12 stores the iteration links of the mixed forms as two rows
+    (links must be real multiples of SU(3) matrices, checked on load).
     """
 
     def __init__(self, dims, fat, lng, mass: float, prec: str = "f64", max_rhs: int = 16,
                  max_iter: int = 100000, ru_delta: float = 0.1, ru_every: int = 0,
                  antiperiodic_t: bool = False, check_every: int = 0, profile: bool = False,
-                 dslash_variant: int = 0, device=None):
+                 dslash_variant: int = 0, link_recon: int = 0, device=None):
         torch = _torch()
         L = load_library()
         self.lib = L
@@ -142,6 +146,7 @@ class BlockCG:
         p.prec, p.antiperiodic_t, p.check_every = PREC[prec], int(bool(antiperiodic_t)), int(check_every)
         p.profile = int(bool(profile))
         p.dslash_variant = int(dslash_variant)
+        p.link_recon = int(link_recon)
         self.params = p
         self.prec = prec
         h = ct.c_void_p()
@@ -274,10 +279,19 @@ class BlockCG:
         return gf, gl
 
     # -------------------------------------------------------------- solvers
-    def _solve(self, fn, B, X0, tol):
+    def _solve(self, fn, B, X0, tol, out=None):
         torch = _torch()
         B = self._block(B)
-        X = torch.zeros_like(B) if X0 is None else self._block(X0).clone()
+        if out is not None:
+            # solve in place: out holds the initial guess and receives X
+            if (out.shape != B.shape or out.dtype != B.dtype or out.device != B.device
+                    or not out.is_contiguous()):
+                raise ValueError("out must be a contiguous tensor like B")
+            if X0 is not None:
+                out.copy_(self._block(X0))
+            X = out
+        else:
+            X = torch.zeros_like(B) if X0 is None else self._block(X0).clone()
         st = Stats()
         rc = fn(self.h, ct.c_void_p(B.data_ptr()), ct.c_void_p(X.data_ptr()), B.shape[0], float(tol),
                 ct.byref(st))
@@ -285,18 +299,22 @@ class BlockCG:
                 "true_rel_res_max": st.true_rel_res_max, "ms_total": st.ms_total, "status": rc,
                 "launches": st.launches, "n_stencil": st.n_stencil, "ms_stencil": st.ms_stencil,
                 "n_stencil_fine": st.n_stencil_fine, "ms_stencil_fine": st.ms_stencil_fine,
-                "ms_gram": st.ms_gram, "ms_stream": st.ms_stream, "ms_dense": st.ms_dense}
+                "ms_gram": st.ms_gram, "ms_stream": st.ms_stream, "ms_dense": st.ms_dense,
+                "stencil_variant": st.stencil_variant}
         if rc not in (0, 6):
             self._check(rc)
         return X, info
 
-    def solve(self, B, X0=None, tol: float = 1e-10):
-        """blockCGrQ (Algorithm 1 with reliable updates); returns (X, info)."""
-        return self._solve(self.lib.blockcg_solve, B, X0, tol)
+    def solve(self, B, X0=None, tol: float = 1e-10, out=None):
+        """blockCGrQ (Algorithm 1 with reliable updates); returns (X, info).
+        With out (a device tensor shaped like B) the solve runs in place: out
+        is the initial guess (or X0 is copied into it) and receives X, so no
+        block is allocated."""
+        return self._solve(self.lib.blockcg_solve, B, X0, tol, out)
 
-    def solve_cg(self, B, X0=None, tol: float = 1e-10):
-        """N sequential CG solves (baseline); returns (X, info)."""
-        return self._solve(self.lib.blockcg_solve_cg, B, X0, tol)
+    def solve_cg(self, B, X0=None, tol: float = 1e-10, out=None):
+        """N sequential CG solves (baseline); returns (X, info); out as in solve."""
+        return self._solve(self.lib.blockcg_solve_cg, B, X0, tol, out)
 
     def bench_dslash(self, n_rhs: int, reps: int = 20, fine: bool = False) -> float:
         """Mean device time (ms) of one block-stencil launch on n_rhs columns."""

@@ -211,12 +211,25 @@ int tile_R(int N) { return N >= 8 ? 4 : (N >= 2 ? 2 : 1); }
 // Register tile of the stencil for (kind, N): tuned once per handle by timing
 // every candidate R on the handle's own buffers (the register-tile tuning of
 // Sec. 5.2); in is read, out is scratch.  Falls back to tile_R on any error.
-int stencil_R(blockcg_ctx* h, FieldKind k, int N, const void* links, const void* in, void* out) {
-  if (h->p.dslash_variant) return h->p.dslash_variant;
+// the stencil flag of a kind's links: two-row storage for the iteration's
+// links when params.link_recon is set (the FP64 links are always complete)
+int recon_flag(const blockcg_ctx* h, FieldKind k) {
+  return (h->p.link_recon && k == h->sloppy && h->sloppy != h->fine) ? DSLASH_RECON : 0;
+}
+
+// Autotuned stencil choice for (kind, N), cached.  Each candidate is timed
+// over 3 launches of out = D in; with out2 the candidate is timed on the pair
+// the normal operator runs (out = D_oe in, then out2 = m^2 in - D_eo out), so
+// that a kernel whose fused epilogue is slow is not chosen on the first half
+// alone.
+int stencil_R(blockcg_ctx* h, FieldKind k, int N, const void* links, const void* in, void* out,
+              void* out2 = nullptr) {
+  const int rf = recon_flag(h, k);
+  if (h->p.dslash_variant) return h->p.dslash_variant | rf;
   const int key = (int)k * 128 + N;
   auto it = h->tuned_R.find(key);
   if (it != h->tuned_R.end()) return it->second;
-  int best = tile_R(N);
+  int best = tile_R(N) | rf;
   float best_ms = 1e30f;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
@@ -228,14 +241,24 @@ int stencil_R(blockcg_ctx* h, FieldKind k, int N, const void* links, const void*
                          1 | DSLASH_ASYNC, 2 | DSLASH_ASYNC, 4 | DSLASH_ASYNC, 8 | DSLASH_ASYNC};
   for (int R : cands) {
     if ((R & 0xff) > 1 && (R & 0xff) > N) continue;
-    if (dslash(k, R, EPI_NONE, links, in, out, nullptr, nullptr, 0.0, h->g, 1, N, g0, h->stream) !=
-        cudaSuccess) {
+    if (rf) {  // two-row links: the plain kernel only
+      if (R & (DSLASH_TMA | DSLASH_ASYNC)) continue;
+      R |= rf;
+    }
+    const double m2 = h->mass * h->mass;
+    auto run = [&]() {
+      cudaError_t e = dslash(k, R, EPI_NONE, links, in, out, nullptr, nullptr, 0.0, h->g, 1, N, g0,
+                             h->stream);
+      if (e == cudaSuccess && out2)
+        e = dslash(k, R, EPI_NORMAL, links, out, out2, in, nullptr, m2, h->g, 0, N, g0, h->stream);
+      return e;
+    };
+    if (run() != cudaSuccess) {
       cudaGetLastError();
       continue;
     }
     cudaEventRecord(e0, h->stream);
-    for (int i = 0; i < 3; ++i)
-      dslash(k, R, EPI_NONE, links, in, out, nullptr, nullptr, 0.0, h->g, 1, N, g0, h->stream);
+    for (int i = 0; i < 3; ++i) run();
     cudaEventRecord(e1, h->stream);
     if (cudaEventSynchronize(e1) != cudaSuccess) continue;
     float ms = 0.f;
@@ -253,9 +276,10 @@ int stencil_R(blockcg_ctx* h, FieldKind k, int N, const void* links, const void*
 }
 
 int cached_R(const blockcg_ctx* h, FieldKind k, int N) {
-  if (h->p.dslash_variant) return h->p.dslash_variant;
+  const int rf = recon_flag(h, k);
+  if (h->p.dslash_variant) return h->p.dslash_variant | rf;
   auto it = h->tuned_R.find((int)k * 128 + N);
-  return it != h->tuned_R.end() ? it->second : tile_R(N);
+  return it != h->tuned_R.end() ? it->second : (tile_R(N) | rf);
 }
 
 blockcg_status check_ready(blockcg_ctx* h, int N) {
@@ -274,7 +298,7 @@ const void* op_links(const blockcg_ctx* h) { return h->links_sloppy; }
 // A applied to an internal even-site block: out = m^2 in - D_eo D_oe in
 blockcg_status apply_A_internal(blockcg_ctx* h, FieldKind k, const void* links, const void* in,
                                 void* tmp_odd, void* out, int N, Gate gate) {
-  int R = stencil_R(h, k, N, links, in, tmp_odd);
+  int R = stencil_R(h, k, N, links, in, tmp_odd, out);
   double m2 = h->mass * h->mass;
   KL(dslash(k, R, EPI_NONE, links, in, tmp_odd, nullptr, nullptr, 0.0, h->g, 1, N, gate, h->stream));
   KL(dslash(k, R, EPI_NORMAL, links, tmp_odd, out, in, nullptr, m2, h->g, 0, N, gate, h->stream));
@@ -356,9 +380,11 @@ blockcg_status check_solve_args(blockcg_ctx* h, const void* B, const void* X, in
 }
 
 // autotune the stencils a block solve of width N uses (no-op once cached)
+// (after the set-up: P and Y hold data; AP, Ts, R and Tf are free until the
+// first iteration and the next reliable update rewrite them)
 void tune_block(blockcg_ctx* h, const Ws& w, int N) {
-  stencil_R(h, h->sloppy, N, h->links_sloppy, w.P, w.Ts);
-  stencil_R(h, h->fine, N, h->links_fine, w.Y, w.Tf);
+  stencil_R(h, h->sloppy, N, h->links_sloppy, w.P, w.Ts, w.AP);
+  stencil_R(h, h->fine, N, h->links_fine, w.Y, w.Tf, w.R);
 }
 
 // Algorithm 1 set-up: B and X in internal layout, |b_i|, X = 0 (update),
@@ -413,6 +439,7 @@ void blockcg_default_params(blockcg_params* p) {
   p->check_every = 0;
   p->profile = 0;
   p->dslash_variant = 0;
+  p->link_recon = 0;
 }
 
 const char* blockcg_status_string(blockcg_status s) {
@@ -452,6 +479,10 @@ blockcg_status blockcg_create(blockcg_t* out, const int dims[4], double mass,
     int r = prm.dslash_variant & ~(DSLASH_TMA | DSLASH_ASYNC);
     if (prm.dslash_variant != 0 && r != 1 && r != 2 && r != 4 && r != 8) return BLOCKCG_ERR_ARG;
   }
+  if (prm.link_recon != 0 && prm.link_recon != 12) return BLOCKCG_ERR_ARG;
+  if (prm.link_recon == 12 && prm.prec != BLOCKCG_PREC_MIXED_F32 &&
+      prm.prec != BLOCKCG_PREC_MIXED_F16 && prm.prec != BLOCKCG_PREC_MIXED_BF16)
+    return BLOCKCG_ERR_ARG;
   blockcg_ctx* h = new blockcg_ctx();
   for (int mu = 0; mu < 4; ++mu) {
     h->dims[mu] = dims[mu];
@@ -459,6 +490,8 @@ blockcg_status blockcg_create(blockcg_t* out, const int dims[4], double mass,
   }
   h->g.hx = dims[0] / 2;
   h->g.Vh = (int)(V / 2);
+  h->g.antiperiodic = prm.antiperiodic_t ? 1 : 0;
+  h->g.inv_c[0] = h->g.inv_c[1] = 0.f;
   h->mass = mass;
   h->p = prm;
   h->stream = (cudaStream_t)stream;
@@ -500,7 +533,8 @@ void blockcg_destroy(blockcg_t h) {
 size_t blockcg_gauge_bytes(blockcg_t h) {
   if (!h) return 0;
   size_t b = up(links_bytes(h->fine, h->g));
-  if (h->sloppy != h->fine) b += up(links_bytes(h->sloppy, h->g));
+  if (h->sloppy != h->fine) b += up(links_bytes(h->sloppy, h->g, h->p.link_recon));
+  if (h->p.link_recon) b += ALIGN;  // scratch of the link check
   return b;
 }
 
@@ -509,15 +543,37 @@ blockcg_status blockcg_load_gauge(blockcg_t h, const void* fat, const void* lng,
   if (!h) return BLOCKCG_ERR_ARG;
   if (!fat || !lng || !storage) return fail(h, BLOCKCG_ERR_ARG, "null pointer");
   if (storage_bytes < blockcg_gauge_bytes(h)) return fail(h, BLOCKCG_ERR_NOMEM, "gauge storage too small");
+  const int recon = h->p.link_recon;
+  if (recon) {
+    // two-row storage needs every link to be a real multiple of an SU(3)
+    // matrix, one multiple per kind: check on the device and read the scales
+    char* scratch = (char*)storage + blockcg_gauge_bytes(h) - ALIGN;
+    double* c = (double*)scratch;
+    int* bad = (int*)(scratch + 2 * sizeof(double));
+    CK(check_scaled_su3((const double2*)fat, (const double2*)lng, 2LL * h->g.Vh, 1e-10, c, bad,
+                        h->stream));
+    double hc[2];
+    int hbad = 1;
+    CK(cudaMemcpyAsync(hc, c, sizeof(hc), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (hbad || !(hc[0] != 0.0) || !(hc[1] != 0.0))
+      return fail(h, BLOCKCG_ERR_ARG,
+                  "link_recon = 12 needs every fat and long link to be c U, U in SU(3), "
+                  "c one real constant per kind");
+    // the packed hop matrices carry a further factor +-1/2 (see Geom)
+    h->g.inv_c[0] = (float)(2.0 / hc[0]);
+    h->g.inv_c[1] = (float)(2.0 / hc[1]);
+  }
   h->gauge = storage;
   h->gauge_bytes = storage_bytes;
   h->links_fine = storage;
   h->links_sloppy = (h->sloppy != h->fine) ? (char*)storage + up(links_bytes(h->fine, h->g)) : storage;
   CK(pack_links(h->fine, (const double2*)fat, (const double2*)lng, h->links_fine, h->g,
-                h->p.antiperiodic_t, h->stream));
+                h->p.antiperiodic_t, 0, h->stream));
   if (h->sloppy != h->fine)
     CK(pack_links(h->sloppy, (const double2*)fat, (const double2*)lng, h->links_sloppy, h->g,
-                  h->p.antiperiodic_t, h->stream));
+                  h->p.antiperiodic_t, recon, h->stream));
   h->gauge_loaded = true;
   return BLOCKCG_OK;
 }
@@ -645,9 +701,9 @@ blockcg_status blockcg_solve(blockcg_t h, const void* B, void* X, int n_rhs, dou
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   CK(cudaEventRecord(e0, s));
-  tune_block(h, w, N);
   rc = solve_begin(h, w, B, X, N, tol);
   if (rc) return rc;
+  tune_block(h, w, N);
   const int chunk = default_check_every(h, N);
   SolverStatus hs;
   memset(&hs, 0, sizeof(hs));
@@ -681,6 +737,7 @@ blockcg_status blockcg_solve(blockcg_t h, const void* B, void* X, int n_rhs, dou
     stats->true_rel_res_max = hs.true_res_max;
     stats->ms_total = ms;
     fill_stats(h, stats);
+    stats->stencil_variant = cached_R(h, h->sloppy, N);
   }
   return result;
 }
@@ -764,8 +821,10 @@ blockcg_status blockcg_solve_cg(blockcg_t h, const void* B, void* X, int n_rhs, 
       if (launched + n > h->p.max_iter) n = h->p.max_iter - launched;
       if (n <= 0) n = 1;
       for (int i = 0; i < n; ++i) {
-        SL(0, dslash(sk, 1, EPI_NONE, h->links_sloppy, p, t, nullptr, nullptr, 0.0, h->g, 1, 1, gi, s));
-        SL(0, dslash(sk, 1, EPI_NORMAL, h->links_sloppy, t, Ap, p, nullptr, m2, h->g, 0, 1, gi, s));
+        SL(0, dslash(sk, 1 | recon_flag(h, sk), EPI_NONE, h->links_sloppy, p, t, nullptr, nullptr, 0.0,
+                     h->g, 1, 1, gi, s));
+        SL(0, dslash(sk, 1 | recon_flag(h, sk), EPI_NORMAL, h->links_sloppy, t, Ap, p, nullptr, m2,
+                     h->g, 0, 1, gi, s));
         TL(TC_GRAM, gram_partials(sk, p, Ap, 1, Vh, 1, w.partials, w.nblocks, gi, s));
         TL(TC_GRAM, gram_reduce(w.partials, w.nblocks, 1, 1, red, gi, s));
         TL(TC_DENSE, cg_scalar_alpha(red, rr, gam, alpha, alpha_x, w.st, gi, s));

@@ -323,6 +323,11 @@ struct Geom {
   int L[4];  // Lx, Ly, Lz, Lt (all even)
   int hx;    // Lx / 2
   int Vh;    // sites per parity
+  // links stored as two rows (stencil calls flagged DSLASH_RECON): the third
+  // row is conj(row0 x row1) * eta_mu(x) * boundary sign * backward sign *
+  // inv_c[kind], inv_c = 1 / (c / 2) for the fat (0) and long (1) link scale c
+  int antiperiodic;
+  float inv_c[2];
 };
 
 // coordinates of the site with checkerboard index cb on parity p

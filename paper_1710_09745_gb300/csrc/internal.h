@@ -43,9 +43,15 @@ enum DslashEpi {
 };
 
 // ---- stencil.cu
+// recon: store the first two rows of every hop matrix only (6 elements)
 cudaError_t pack_links(FieldKind k, const double2* fat, const double2* lng, void* out,
-                       const Geom& g, int antiperiodic_t, cudaStream_t s);
-size_t links_bytes(FieldKind k, const Geom& g);  // both parities
+                       const Geom& g, int antiperiodic_t, int recon, cudaStream_t s);
+size_t links_bytes(FieldKind k, const Geom& g, int recon = 0);  // both parities
+// checks that every fat link is c_f U and every long link c_l U (U in SU(3),
+// c real and the same for all links of a kind, from the first link); writes
+// c_f, c_l to c[0], c[1] and a nonzero *bad otherwise
+cudaError_t check_scaled_su3(const double2* fat, const double2* lng, long long V, double tol,
+                             double* c, int* bad, cudaStream_t s);
 // links points at the start of the packed array for both parities.
 // R: right-hand sides per thread (1, 2, 4, 8); R | DSLASH_TMA selects the
 // bulk-copy pipelined kernel (the plain kernel runs instead when the
@@ -53,6 +59,9 @@ size_t links_bytes(FieldKind k, const Geom& g);  // both parities
 static constexpr int DSLASH_TMA = 0x100;
 // R | DSLASH_ASYNC selects the per-thread cp.async prefetch kernel
 static constexpr int DSLASH_ASYNC = 0x200;
+// R | DSLASH_RECON: links packed as two rows (pack_links recon); plain kernel
+// only, FP32 / FP16 / bfloat16 kinds
+static constexpr int DSLASH_RECON = 0x400;
 cudaError_t dslash(FieldKind k, int R, int epi, const void* links, const void* in, void* out,
                    const void* c1, const void* c2, double m2, const Geom& g, int out_parity,
                    int N, Gate gate, cudaStream_t s);

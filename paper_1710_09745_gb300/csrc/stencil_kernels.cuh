@@ -15,9 +15,26 @@ __host__ __device__ inline long long link_blocks(const Geom& g) {
   return ((long long)g.Vh + LINK_W - 1) / LINK_W;
 }
 
-// element offset of (parity p, site cb, hop 0, element 0)
-__device__ __forceinline__ long long link_offset(const Geom& g, int p, int cb) {
-  return ((long long)p * link_blocks(g) + cb / LINK_W) * (16 * 9 * LINK_W) + (cb % LINK_W);
+// element offset of (parity p, site cb, hop 0, element 0); E elements per
+// hop matrix (9, or 6 for two-row storage)
+__host__ __device__ __forceinline__ long long link_offset(const Geom& g, int p, int cb, int E = 9) {
+  return ((long long)p * link_blocks(g) + cb / LINK_W) * (16 * E * LINK_W) + (cb % LINK_W);
+}
+
+// third row of a hop matrix stored as two rows: conj(row0 x row1) times the
+// inverse of the matrix's real scale (see Geom)
+template <class R>
+__device__ __forceinline__ void rebuild_row2(cpx<R>* U, R inv) {
+  auto cmulsub = [](cpx<R> a, cpx<R> b, cpx<R> c, cpx<R> d) {  // a b - c d
+    return cpx<R>{a.re * b.re - a.im * b.im - (c.re * d.re - c.im * d.im),
+                  a.re * b.im + a.im * b.re - (c.re * d.im + c.im * d.re)};
+  };
+  const cpx<R> w0 = cmulsub(U[1], U[5], U[2], U[4]);
+  const cpx<R> w1 = cmulsub(U[2], U[3], U[0], U[5]);
+  const cpx<R> w2 = cmulsub(U[0], U[4], U[1], U[3]);
+  U[6] = cpx<R>{w0.re * inv, -w0.im * inv};
+  U[7] = cpx<R>{w1.re * inv, -w1.im * inv};
+  U[8] = cpx<R>{w2.re * inv, -w2.im * inv};
 }
 
 // One thread: output site `site`, vector slots j = k, k + T, ... (< N / V) of
@@ -91,7 +108,7 @@ struct VecLoad<StoreBF16, 4> {
 #define BCG_DSLASH_MINB 1
 #endif
 
-template <class S, int RV, int V, int EPI, int UNROLL_HOPS>
+template <class S, int RV, int V, int EPI, int UNROLL_HOPS, bool RC = false>
 __global__ void __launch_bounds__(BCG_DSLASH_TPB, BCG_DSLASH_MINB)
     k_dslash(const typename S::elem* __restrict__ links, const typename S::elem* __restrict__ in,
              typename S::elem* __restrict__ out, const typename S::elem* __restrict__ c1,
@@ -121,12 +138,23 @@ __global__ void __launch_bounds__(BCG_DSLASH_TPB, BCG_DSLASH_MINB)
 #pragma unroll
         for (int i = 0; i < 3; ++i) a[r][w][i] = czero<C>();
 
-    const typename S::elem* lp = links + link_offset(g, parity, site);
+    constexpr int LE = RC ? 6 : 9;  // stored elements per hop matrix
+    const typename S::elem* lp = links + link_offset(g, parity, site, LE);
     auto hop = [&](int d) {
-      const int nb = neighbour_cb_s(g, lex, x, y, z, t, d >> 2, hop_k(d & 3));
+      const int mu = d >> 2, kk = hop_k(d & 3);
+      const int nb = neighbour_cb_s(g, lex, x, y, z, t, mu, kk);
       cpx<real> U[9];
 #pragma unroll
-      for (int e = 0; e < 9; ++e) U[e] = S::load(lp + (d * 9 + e) * LINK_W);
+      for (int e = 0; e < LE; ++e) U[e] = S::load(lp + (d * LE + e) * LINK_W);
+      if constexpr (RC) {
+        // sign of the stored matrix's scale: staggered phase, boundary, backward hop
+        const int ps = mu == 0 ? 0 : mu == 1 ? x : mu == 2 ? x + y : x + y + z;
+        int sg = (ps & 1) ? -1 : 1;
+        if (kk < 0) sg = -sg;
+        if (g.antiperiodic && mu == 3 && (t + kk < 0 || t + kk >= g.L[3])) sg = -sg;
+        const real inv = (real)sg * (real)g.inv_c[(d & 2) ? 1 : 0];
+        rebuild_row2<real>(U, inv);
+      }
       const typename S::elem* ip = in + (long long)nb * N * 3 + k * V;
 #pragma unroll
       for (int r = 0; r < RV; ++r) {
@@ -660,7 +688,7 @@ static bool launch_tma_s(int R, int epi, const void* links, const void* in, void
 }
 
 
-template <class S, int RV, int V, int EPI>
+template <class S, int RV, int V, int EPI, bool RC = false>
 static void launch_dslash_t(const void* links, const void* in, void* out, const void* c1,
                             const void* c2, double m2, const Geom& g, int parity, int N,
                             Gate gate, cudaStream_t s) {
@@ -678,30 +706,30 @@ static void launch_dslash_t(const void* links, const void* in, void* out, const 
   int threads = BCG_DSLASH_TPB;
   long long want = (threads_total + threads - 1) / threads;
   unsigned blocks = (unsigned)(want < 152 * 32 ? want : 152 * 32);
-  k_dslash<S, RV, V, EPI, UNROLL><<<blocks, threads, 0, s>>>(
+  k_dslash<S, RV, V, EPI, UNROLL, RC><<<blocks, threads, 0, s>>>(
       (const E*)links, (const E*)in, (E*)out, (const E*)c1, (const E*)c2, m2, g, parity, N, T, gate);
 }
 
-template <class S, int RV, int V>
+template <class S, int RV, int V, bool RC = false>
 static void launch_dslash_r(int epi, const void* links, const void* in, void* out, const void* c1,
                             const void* c2, double m2, const Geom& g, int parity, int N,
                             Gate gate, cudaStream_t s) {
   switch (epi) {
     case EPI_NONE:
-      launch_dslash_t<S, RV, V, EPI_NONE>(links, in, out, c1, c2, m2, g, parity, N, gate, s);
+      launch_dslash_t<S, RV, V, EPI_NONE, RC>(links, in, out, c1, c2, m2, g, parity, N, gate, s);
       break;
     case EPI_NORMAL:
-      launch_dslash_t<S, RV, V, EPI_NORMAL>(links, in, out, c1, c2, m2, g, parity, N, gate, s);
+      launch_dslash_t<S, RV, V, EPI_NORMAL, RC>(links, in, out, c1, c2, m2, g, parity, N, gate, s);
       break;
     default:
-      launch_dslash_t<S, RV, V, EPI_RESIDUAL>(links, in, out, c1, c2, m2, g, parity, N, gate, s);
+      launch_dslash_t<S, RV, V, EPI_RESIDUAL, RC>(links, in, out, c1, c2, m2, g, parity, N, gate, s);
       break;
   }
 }
 
 // R = right-hand sides per thread.  FP32 with even N and R >= 2 uses 128-bit
 // loads of two right-hand sides (V = 2, RV = R / 2 slots).
-template <class S>
+template <class S, bool RC = false>
 static void launch_dslash_s(int R, int epi, const void* links, const void* in, void* out,
                      const void* c1, const void* c2, double m2, const Geom& g, int parity,
                      int N, Gate gate, cudaStream_t s) {
@@ -712,21 +740,21 @@ static void launch_dslash_s(int R, int epi, const void* links, const void* in, v
   constexpr int V2 = (F32 || H) ? 2 : 1;
   constexpr int V4 = H ? 4 : 1;
   if (H && (N % 4) == 0 && R >= 4) {
-    if (R == 4) return launch_dslash_r<S, 1, V4>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, s);
-    return launch_dslash_r<S, 2, V4>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, s);
+    if (R == 4) return launch_dslash_r<S, 1, V4, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, s);
+    return launch_dslash_r<S, 2, V4, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, s);
   }
   if ((F32 || H) && (N % 2) == 0 && R >= 2) {
     switch (R) {
-      case 2: return launch_dslash_r<S, 1, V2>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, s);
-      case 4: return launch_dslash_r<S, 2, V2>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, s);
-      default: return launch_dslash_r<S, 4, V2>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, s);
+      case 2: return launch_dslash_r<S, 1, V2, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, s);
+      case 4: return launch_dslash_r<S, 2, V2, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, s);
+      default: return launch_dslash_r<S, 4, V2, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, s);
     }
   }
   switch (R) {
-    case 1: return launch_dslash_r<S, 1, 1>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, s);
-    case 2: return launch_dslash_r<S, 2, 1>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, s);
-    case 4: return launch_dslash_r<S, 4, 1>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, s);
-    default: return launch_dslash_r<S, 8, 1>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, s);
+    case 1: return launch_dslash_r<S, 1, 1, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, s);
+    case 2: return launch_dslash_r<S, 2, 1, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, s);
+    case 4: return launch_dslash_r<S, 4, 1, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, s);
+    default: return launch_dslash_r<S, 8, 1, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, s);
   }
 }
 
@@ -738,6 +766,14 @@ template <class S>
 static cudaError_t dslash_kind(int R, int epi, const void* links, const void* in, void* out,
                                const void* c1, const void* c2, double m2, const Geom& g,
                                int out_parity, int N, Gate gate, cudaStream_t s) {
+  if (R & DSLASH_RECON) {  // two-row links: plain kernel, 32- and 16-bit kinds only
+    if constexpr (std::is_same<typename S::comp::real, float>::value) {
+      launch_dslash_s<S, true>(R & 0xff, epi, links, in, out, c1, c2, m2, g, out_parity, N, gate, s);
+      return cudaGetLastError();
+    } else {
+      return cudaErrorInvalidValue;
+    }
+  }
   if (R & DSLASH_ASYNC) {
     const int r = R & 0xff;
     if (launch_async_s<S>(r, epi, links, in, out, c1, c2, m2, g, out_parity, N, gate, s))

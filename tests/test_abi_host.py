@@ -141,3 +141,31 @@ def test_link_grad_validates_without_gpu(lib):
         assert lib.blockcg_link_grad(h, None, None, 0, None, None) == 1
     finally:
         lib.blockcg_destroy(h)
+
+
+def test_link_recon_parameter_checks(lib):
+    """Two-row links only with the 32- and 16-bit forms, and only 0 or 12;
+    they shrink the gauge storage of those forms."""
+    from paper_1710_09745_gb300.binding import Params, PREC
+    d = (ct.c_int * 4)(4, 4, 4, 4)
+    p = Params()
+    lib.blockcg_default_params(ct.byref(p))
+    assert p.link_recon == 0
+    sizes = {}
+    for prec, recon, ok in (("f64", 12, False), ("f64_native", 12, False), ("mixed_f32", 7, False),
+                            ("mixed_f32", 12, True), ("mixed_f16", 12, True),
+                            ("mixed_bf16", 12, True), ("mixed_f32", 0, True)):
+        lib.blockcg_default_params(ct.byref(p))
+        p.prec, p.link_recon = PREC[prec], recon
+        h = ct.c_void_p()
+        rc = lib.blockcg_create(ct.byref(h), d, 0.1, ct.byref(p), None)
+        assert (rc == 0) == ok, (prec, recon)
+        if ok:
+            sizes[(prec, recon)] = lib.blockcg_gauge_bytes(h)
+            lib.blockcg_destroy(h)
+    V = 256
+    fine = 2 * (V // 2 // 32) * 16 * 9 * 32 * 16          # FP64 links, both parities
+    f32_full = 2 * (V // 2 // 32) * 16 * 9 * 32 * 8
+    f32_two = 2 * (V // 2 // 32) * 16 * 6 * 32 * 8
+    assert sizes[("mixed_f32", 0)] == fine + f32_full
+    assert sizes[("mixed_f32", 12)] == fine + f32_two + 256

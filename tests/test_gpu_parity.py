@@ -351,3 +351,22 @@ def test_max_rhs_64():
     r = b - hisq.apply_A(dims, fat, lng, 0.2, gh.to_np(X))
     rel = np.linalg.norm(r.reshape(64, -1), axis=1) / np.linalg.norm(b.reshape(64, -1), axis=1)
     assert rel.max() <= 1e-10
+
+
+def test_solve_in_place_out_matches_allocating_solve():
+    """solve(..., out=T) uses T as the initial guess and writes X into it: the
+    result equals the allocating call bit for bit, and X0 is copied into out."""
+    import torch
+    s, fat, lng = gh.make_solver((4, 4, 4, 4), 0.1, prec="f64", seed=1090, max_rhs=4)
+    b = torch.as_tensor(hi.gaussian_sources((4, 4, 4, 4), 3, 2090)).cuda()
+    X1, i1 = s.solve(b, tol=1e-10)
+    out = torch.zeros_like(b)
+    X2, i2 = s.solve(b, tol=1e-10, out=out)
+    assert X2.data_ptr() == out.data_ptr()
+    assert torch.equal(X1, X2) and i1["iters"] == i2["iters"]
+    # a converged initial guess copied in through X0: no iterations needed
+    out2 = torch.empty_like(b)
+    X3, i3 = s.solve(b, X0=X1, tol=1e-10, out=out2)
+    assert X3.data_ptr() == out2.data_ptr() and i3["iters"] == 0
+    with pytest.raises(ValueError):
+        s.solve(b, out=torch.zeros((2, b.shape[1], 3), dtype=b.dtype, device=b.device))
