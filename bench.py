@@ -68,6 +68,27 @@ def parse_args():
     return ap.parse_args()
 
 
+def replica_source_seed(rank: int) -> int:
+    """Replicas only: every rank solves its own block of right-hand sides
+    (seed per rank); ranks share no data and no collective on the solve."""
+    return SRC_SEED + 1000 * rank
+
+
+def max_over_ranks(ms: float, world: int, device) -> float:
+    """The slowest rank's time (all_reduce MAX; NCCL on GPUs, gloo on CPU)."""
+    if world <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def per_rhs(elapsed_ms: float, steps: int, n_rhs: int, world: int) -> float:
+    """Whole-job ms per right-hand side: all ranks' RHS in the slowest rank's time."""
+    return elapsed_ms / (steps * n_rhs * world)
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -359,7 +380,7 @@ def main():
     fat_c, lng_c, b_np = cpu_inputs(a)
     if world > 1:  # independent replica per rank: its own sources
         import hisq_inputs as hi
-        b_np = hi.gaussian_sources(dims, N, SRC_SEED + 1000 * rank)
+        b_np = hi.gaussian_sources(dims, N, replica_source_seed(rank))
     fat = fat_c.to(dev)
     lng = lng_c.to(dev)
     B = torch.as_tensor(b_np).to(dev)
@@ -387,13 +408,9 @@ def main():
     e1.record(stream)
     barrier()
     clocks = clk.stop()
-    elapsed = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = max_over_ranks(e0.elapsed_time(e1), world, dev)
     ms_per_step = elapsed / a.steps
-    value = elapsed / (a.steps * N * world)
+    value = per_rhs(elapsed, a.steps, N, world)
     ok = all(i["status"] == 0 and i["true_rel_res_max"] <= a.tol for i in infos)
 
     # dominant kernel: the iteration's stencil, timed with events inside the solves
@@ -448,13 +465,9 @@ def main():
         X_host.copy_(Xd, non_blocking=True)
     e3.record(stream)
     barrier()
-    e2e_ms = e2.elapsed_time(e3)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2.elapsed_time(e3), world, dev)
     nbytes = B_host.numel() * B_host.element_size()
-    e2e = {"value": e2e_ms / (a.steps * N * world), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+    e2e = {"value": per_rhs(e2e_ms, a.steps, N, world), "unit": UNIT, "h2d_bytes_per_step": nbytes,
            "d2h_bytes_per_step": nbytes}
 
     out = {
@@ -518,6 +531,20 @@ def main():
             sweep[str(n)] = row
         out["dslash"] = sweep
         del s32, s16, s32r
+        # time to solution per RHS against the block width (F64 form, same
+        # sources: the first n columns of a 32-column block)
+        import hisq_inputs as hi
+        b32 = torch.as_tensor(hi.gaussian_sources(dims, 32, SRC_SEED)).to(dev)
+        sN = BlockCG(dims, fat, lng, a.mass, prec=a.prec, max_rhs=32, device=dev)
+        width = {}
+        for n in (1, 4, 8, 16, 32):
+            sN.solve(b32[:n], tol=a.tol)  # tuning for this width
+            _, iN = sN.solve(b32[:n], tol=a.tol)
+            width[str(n)] = {"ms_per_rhs": iN["ms_total"] / n, "iters": iN["iters"],
+                             "reliable_updates": iN["reliable_updates"],
+                             "true_rel_res_max": iN["true_rel_res_max"]}
+        out["block_width"] = width
+        del sN, b32
         out["batched"] = batched_leg(a.tol, dev)
         out["autograd"] = autograd_leg(dev)
         # CPU oracle on a bounded sample (rank 0, one GPU)
