@@ -552,14 +552,25 @@ def main():
             os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
             from oracle import build as obuild
             obuild.build()
-            sec_it, k = oracle_sample(dims, a.mass, fat_c.numpy(), lng_c.numpy(), b_np[0])
+            from oracle import hisq as ohisq
+            fat_n, lng_n = fat_c.numpy(), lng_c.numpy()
+            sec_it, k = oracle_sample(dims, a.mass, fat_n, lng_n, b_np[0])
             iters = ic["iters"] / N
             cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+            t0 = time.time()
+            ohisq.apply_A(dims, fat_n, lng_n, a.mass, b_np[:1])
+            apply_ms = (time.time() - t0) * 1e3
+            prev = ohisq.set_threads(1)  # the same oracle on one core, shorter sample
+            sec_it1, k1 = oracle_sample(dims, a.mass, fat_n, lng_n, b_np[0], budget_s=4.0)
+            ohisq.set_threads(prev)
             out["cpu_baseline"] = {
                 "value": sec_it * iters * 1e3, "unit": UNIT, "cores": cores, "kind": "oracle",
                 "sample": f"{k} oracle textbook-CG iterations on 1 source of the workload "
                           f"({sec_it * 1e3:.1f} ms each), extrapolated to {iters:.0f} iterations "
-                          f"(the GPU CG baseline's count to {a.tol:g})"}
+                          f"(the GPU CG baseline's count to {a.tol:g})",
+                "one_core": {"value": sec_it1 * iters * 1e3, "unit": UNIT, "cores": 1,
+                             "sample": f"{k1} iterations ({sec_it1 * 1e3:.1f} ms each)"},
+                "apply_A_ms_per_rhs": apply_ms}
     if rank == 0:
         print(json.dumps(out))
     if world > 1:

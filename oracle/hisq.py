@@ -28,8 +28,9 @@ def lib():
         L.oracle_cg.argtypes = [P, P, P, I, D, P, P, I, D, I, P, P]
         L.oracle_cg_iterates.argtypes = [P, P, P, I, D, P, P, I]
         L.oracle_link_grad.argtypes = [P, P, P, I, P, P, I, P, P]
+        L.oracle_set_threads.argtypes = [I]
         for f in (L.oracle_dslash, L.oracle_apply_A, L.oracle_apply_A_sites, L.oracle_cg,
-                  L.oracle_cg_iterates, L.oracle_link_grad):
+                  L.oracle_cg_iterates, L.oracle_link_grad, L.oracle_set_threads):
             f.restype = I
         _lib = L
     return _lib
@@ -148,3 +149,8 @@ def link_grad(dims, fat, lng, x, lam, antiperiodic_t: bool = False):
                                 x.shape[0], _p(gf), _p(gl))
     assert rc == 0, rc
     return gf, gl
+
+
+def set_threads(n: int) -> int:
+    """OpenMP threads of the oracle's loops; returns the previous setting."""
+    return lib().oracle_set_threads(int(n))

@@ -36,8 +36,24 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef double complex cplx;
+
+/* OpenMP threads of the parallel loops (timing the oracle on 1 core or all);
+ * returns the previous setting (1 without OpenMP) */
+int oracle_set_threads(int n) {
+#ifdef _OPENMP
+  int old = omp_get_max_threads();
+  if (n > 0) omp_set_num_threads(n);
+  return old;
+#else
+  (void)n;
+  return 1;
+#endif
+}
 
 typedef struct {
   int L[4];
