@@ -245,6 +245,12 @@ int stencil_R(blockcg_ctx* h, FieldKind k, int N, const void* links, const void*
       if (R & (DSLASH_TMA | DSLASH_ASYNC)) continue;
       R |= rf;
     }
+    // double-float with N >= 2: the cp.async kernel only.  Timed alone the
+    // plain kernel looks up to 4 % faster, but inside the solve (between the
+    // Gram, N x N and update kernels) it ran 12-15 % slower than that timing
+    // in repeated 32^4 N = 16 measurements, while the cp.async kernel ran as
+    // timed.
+    if (k == FK_DF && N >= 2 && !(R & DSLASH_ASYNC)) continue;
     const double m2 = h->mass * h->mass;
     auto run = [&]() {
       cudaError_t e = dslash(k, R, EPI_NONE, links, in, out, nullptr, nullptr, 0.0, h->g, 1, N, g0,
