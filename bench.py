@@ -508,6 +508,10 @@ def main():
             out[key] = {"ms_per_rhs": im["ms_total"] / N, "iters": im["iters"],
                         "reliable_updates": im["reliable_updates"],
                         "true_rel_res_max": im["true_rel_res_max"],
+                        "ms_breakdown": {k: im[k] for k in ("ms_stencil", "ms_stencil_fine",
+                                                            "ms_gram", "ms_stream", "ms_dense",
+                                                            "ms_total")},
+                        "stencil_variant": im["stencil_variant"],
                         "cg_ms_per_rhs": imc["ms_total"] / 4, "cg_iters_per_rhs": imc["iters"] / 4,
                         "block_speedup": (imc["ms_total"] / 4) / (im["ms_total"] / N)}
             if prec == "mixed_f32":

@@ -18,6 +18,7 @@
 #include <type_traits>
 
 #include "internal.h"
+#include "tma.cuh"
 
 namespace bcg {
 
@@ -441,7 +442,9 @@ static TileCfg tile_cfg(int N, size_t real_cplx_bytes, int n_tiles, int n_coefs,
 
 // Each thread produces JB consecutive output columns j of one row (site,
 // colour), so every W and P value read from shared memory feeds JB outputs.
-template <class SS, class XS, int JB>
+// DB (FP32 storage): the W, P and X tiles of the next tile are copied with
+// cp.async into a second shared buffer while the current one is computed.
+template <class SS, class XS, int JB, bool DB>
 __global__ void __launch_bounds__(256, 3)
     k_bcg_update(typename SS::elem* __restrict__ Q, typename SS::elem* __restrict__ P,
                  typename XS::elem* __restrict__ X, const double2* __restrict__ Sinv,
@@ -457,27 +460,67 @@ __global__ void __launch_bounds__(256, 3)
   // W and P tiles with a row stride of N + 1 complex numbers, so that the
   // rows read by the lanes of a warp fall into different shared-memory banks
   const int RS = N + 1;
-  cpx<real>* sW = reinterpret_cast<cpx<real>*>(smem_raw);
-  cpx<real>* sP = sW + TS * 3 * RS;
-  cpx<real>* sA = sP + TS * 3 * RS;  // Sinv chunk  [N][JT]
-  cpx<real>* sB = sA + N * JT;      // BC chunk
-  cpx<real>* sC = sB + N * JT;      // SH chunk
+  using XE = typename XS::elem;
+  // tiles: W, P (padded rows) and, with DB, the X tile; two sets with DB
+  const int tile_w = TS * 3 * RS;
+  // one set = [W tile][P tile][X tile (DB only)]; set b starts b * set_bytes in
+  const size_t set_bytes =
+      2 * (size_t)tile_w * sizeof(cpx<real>) + (DB ? (size_t)TS * 3 * N * sizeof(XE) : 0);
+  auto tW = [&](int bsel) { return reinterpret_cast<cpx<real>*>(smem_raw + bsel * set_bytes); };
+  auto tP = [&](int bsel) { return tW(bsel) + tile_w; };
+  auto tX = [&](int bsel) { return reinterpret_cast<XE*>(tP(bsel) + tile_w); };
+  cpx<real>* sW = tW(0);
+  cpx<real>* sP = tP(0);
+  XE* sX = tX(0);
+  cpx<real>* sA = reinterpret_cast<cpx<real>*>(smem_raw + (DB ? 2 : 1) * set_bytes);  // Sinv chunk [N][JT]
+  cpx<real>* sB = sA + N * JT;                         // BC chunk
+  cpx<real>* sC = sB + N * JT;                         // SH chunk
   const bool one_chunk = (JT >= N);
   if (one_chunk) {  // all coefficients fit: stage them once per CTA
     stage_coef<C>(sA, Sinv, N, 0, N, JT);
     stage_coef<C>(sB, BC, N, 0, N, JT);
     if (!keepP) stage_coef<C>(sC, SH, N, 0, N, JT);
   }
-  for (long long tile = blockIdx.x; tile * TS < Vh; tile += gridDim.x) {
+  // asynchronous copy of tile t into buffer set bsel (DB only): the copied
+  // elements are the stored ones, bit-identical to cpx<real> for FP32
+  auto issue = [&](long long t, int bsel) {
+    const long long s0 = t * TS;
+    const int nsi = (int)min((long long)TS, (long long)Vh - s0);
+    const long long bs = s0 * N * 3;
+    for (int idx = threadIdx.x; idx < nsi * N * 3; idx += blockDim.x) {
+      const int rr = idx / N, cc = idx - rr * N;
+      cp_async_bytes(tW(bsel) + rr * RS + cc, Q + bs + idx, sizeof(typename SS::elem));
+      cp_async_bytes(tP(bsel) + rr * RS + cc, P + bs + idx, sizeof(typename SS::elem));
+      cp_async_bytes(tX(bsel) + idx, X + bs + idx, sizeof(XE));
+    }
+    cp_async_commit();
+  };
+  int bcur = 0;
+  if (DB && (long long)blockIdx.x * TS < Vh) issue(blockIdx.x, 0);
+  for (long long tile = blockIdx.x; tile * TS < Vh; tile += gridDim.x, bcur ^= 1) {
     const long long site0 = tile * TS;
     const int ns = (int)min((long long)TS, (long long)Vh - site0);
     const long long base = site0 * N * 3;
     const int nel = ns * N * 3;
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < nel; idx += blockDim.x) {
-      const int rr = idx / N, cc = idx - rr * N;
-      sW[rr * RS + cc] = SS::load_nc(Q + base + idx);
-      sP[rr * RS + cc] = SS::load_nc(P + base + idx);
+    if (DB) {
+      // every thread is done with the previous tile's set before the next
+      // tile is copied into it; then wait for this tile's copies
+      __syncthreads();
+      const long long nxt = tile + gridDim.x;
+      if (nxt * TS < Vh) issue(nxt, bcur ^ 1);
+      else cp_async_commit();
+      cp_async_wait<1>();
+      __syncthreads();
+      sW = tW(bcur);
+      sP = tP(bcur);
+      sX = tX(bcur);
+    } else {
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < nel; idx += blockDim.x) {
+        const int rr = idx / N, cc = idx - rr * N;
+        sW[rr * RS + cc] = SS::load_nc(Q + base + idx);
+        sP[rr * RS + cc] = SS::load_nc(P + base + idx);
+      }
     }
     for (int j0 = 0; j0 < N; j0 += JT) {
       const int jn = min(JT, N - j0);
@@ -578,7 +621,9 @@ __global__ void __launch_bounds__(256, 3)
             const long long gi = gbase + jj;
             cpx<real> qn = cfin<C>(q[u]);
             cpx<real> xs = cfin<C>(x[u]);
-            cpx<typename CX::acc> xa = cacc_from<CX>(XS::load_nc(X + gi));
+            // the old X: from the prefetched tile with DB (plain shared read)
+            cpx<typename CX::acc> xa = cacc_from<CX>(
+                DB ? XS::load_nc(sX + (long long)row * N + j0 + jj) : XS::load_nc(X + gi));
             CX::add(xa.re, conv<CX, C>::f(xs.re));
             CX::add(xa.im, conv<CX, C>::f(xs.im));
             XS::store(X + gi, cfin<CX>(xa));
@@ -605,14 +650,25 @@ static cudaError_t launch_bcg_update(void* Q, void* P, void* X, const double2* S
   // double-float: 2 output columns per thread keep the accumulators within the
   // register budget of four resident blocks (no spills); other kinds use 4
   constexpr int JB = std::is_same<SS, StoreDF>::value ? 2 : 4;
-  // shared memory per block <= ~56 KB so that four blocks fit (up to N = 16)
-  TileCfg t = tile_cfg(N + 1, sizeof(cpx<real>), 2, 3, N <= 16 ? 56 * 1024 : 96 * 1024);
-  size_t sm = ((size_t)2 * t.TS * (N + 1) * 3 + 3 * (size_t)N * t.JT) * sizeof(cpx<real>);
-  cudaFuncSetAttribute(k_bcg_update<SS, XS, JB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  // FP32 storage: double-buffered tiles (W, P, X) filled by cp.async
+  constexpr bool DB = std::is_same<SS, StoreF32>::value;
+  const size_t cb = sizeof(cpx<real>), xb = sizeof(typename XS::elem);
+  const int JT = (N + 1) < 16 ? (N + 1) : 16;
+  const size_t coef = 3ull * N * JT * cb;
+  const size_t budget = N <= 16 ? 56 * 1024 : 96 * 1024;
+  int TS = 32;
+  auto tile_bytes = [&](int ts) {
+    size_t one = 2ull * ts * 3 * (N + 1) * cb + (DB ? (size_t)ts * 3 * N * xb : 0);
+    return (DB ? 2 : 1) * one;
+  };
+  while (TS > 1 && coef + tile_bytes(TS) > budget) TS >>= 1;
+  const size_t sm = coef + tile_bytes(TS);
+  cudaFuncSetAttribute(k_bcg_update<SS, XS, JB, DB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sm);
   // a block size that divides a tile's (row, column group) work units, so no
   // pass over a tile runs with part of the block idle
-  const int jt = t.JT < N ? t.JT : N;
-  const int units = t.TS * 3 * ((jt + JB - 1) / JB);
+  const int jt = JT < N ? JT : N;
+  const int units = TS * 3 * ((jt + JB - 1) / JB);
   int threads = 256;
   if (units <= 256) {
     threads = (units + 31) / 32 * 32;
@@ -625,16 +681,16 @@ static cudaError_t launch_bcg_update(void* Q, void* P, void* X, const double2* S
   }
   // a persistent grid of exactly the resident blocks (no partial last wave)
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bcg_update<SS, XS, JB>, threads, sm) !=
-          cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bcg_update<SS, XS, JB, DB>, threads,
+                                                    sm) != cudaSuccess ||
       per_sm < 1) {
     cudaGetLastError();
     per_sm = 1;
   }
-  unsigned blocks = gcap(Vh, t.TS, num_sms() * per_sm);
-  k_bcg_update<SS, XS, JB><<<blocks, threads, sm, s>>>((typename SS::elem*)Q, (typename SS::elem*)P,
-                                                (typename XS::elem*)X, Sinv, BC, SH, N, Vh, t.TS,
-                                                t.JT, gate);
+  unsigned blocks = gcap(Vh, TS, num_sms() * per_sm);
+  k_bcg_update<SS, XS, JB, DB><<<blocks, threads, sm, s>>>(
+      (typename SS::elem*)Q, (typename SS::elem*)P, (typename XS::elem*)X, Sinv, BC, SH, N, Vh, TS,
+      JT, gate);
   return cudaGetLastError();
 }
 

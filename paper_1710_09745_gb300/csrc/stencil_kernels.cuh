@@ -395,21 +395,6 @@ __global__ void __launch_bounds__(256)
 // the site's nine link elements, each copying every T-th one), so the loads
 // of later hops overlap the arithmetic of the current one without a
 // CTA-wide barrier.  Requires T to divide the block size.
-__device__ __forceinline__ void cp_async_bytes(void* dst, const void* src, int bytes) {
-  const uint32_t d = smem_u32(dst);
-  if (bytes == 16)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
-  else if (bytes == 8)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N_>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N_) : "memory");
-}
-
 static constexpr int ASYNC_TPB = 128;
 
 template <class S, int RV, int V, int EPI, int DEPTH>

@@ -1,6 +1,7 @@
-// Inline-PTX helpers for the Blackwell bulk-copy (TMA) pipeline: mbarrier
-// initialisation, transaction-count arrival, 1-D global -> shared bulk
-// copies, bounded parity waits and the async-proxy fence.
+// Inline-PTX helpers for asynchronous copies: the Blackwell bulk-copy (TMA)
+// pipeline (mbarrier initialisation, transaction-count arrival, 1-D global ->
+// shared bulk copies, bounded parity waits, the async-proxy fence) and
+// per-thread cp.async copies with commit/wait groups.
 #pragma once
 #include <stdint.h>
 
@@ -64,6 +65,23 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase,
     if (mbar_try_wait(bar, phase)) return true;
     if (global_ns() - t0 > limit_ns) return false;
   }
+}
+
+// per-thread asynchronous copy of 4, 8 or 16 bytes global -> shared (both
+// aligned to the size), completed with commit/wait groups
+__device__ __forceinline__ void cp_async_bytes(void* dst, const void* src, int bytes) {
+  const uint32_t d = smem_u32(dst);
+  if (bytes == 16)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+  else if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N_>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N_) : "memory");
 }
 
 // order this thread's earlier generic-proxy shared accesses before later
