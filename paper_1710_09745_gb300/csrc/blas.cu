@@ -442,8 +442,27 @@ static TileCfg tile_cfg(int N, size_t real_cplx_bytes, int n_tiles, int n_coefs,
 
 // Each thread produces JB consecutive output columns j of one row (site,
 // colour), so every W and P value read from shared memory feeds JB outputs.
-// DB (FP32 storage): the W, P and X tiles of the next tile are copied with
-// cp.async into a second shared buffer while the current one is computed.
+// DB: the W, P and X tiles of the next tile are copied with cp.async, as
+// stored, into a second shared buffer while the current one is computed, and
+// converted when read; without DB the tiles hold converted values.
+template <class SS, bool DB>
+struct UpdTile {
+  using T = cpx<typename SS::comp::real>;
+  static __device__ __forceinline__ T get(const T* p) { return *p; }
+};
+template <class SS>
+struct UpdTile<SS, true> {
+  using T = typename SS::elem;
+  static __device__ __forceinline__ cpx<typename SS::comp::real> get(const T* p) {
+    return SS::load_nc(p);  // a plain (generic) read: valid on shared memory
+  }
+};
+
+// bytes of the W and P tiles of one buffer set, rounded up to 16 so that the
+// X tile behind them can take 16-byte asynchronous copies
+__host__ __device__ inline size_t upd_wp_bytes(int TS, int N, size_t tile_elem) {
+  return (2 * (size_t)TS * 3 * (N + 1) * tile_elem + 15) / 16 * 16;
+}
 template <class SS, class XS, int JB, bool DB>
 __global__ void __launch_bounds__(256, 3)
     k_bcg_update(typename SS::elem* __restrict__ Q, typename SS::elem* __restrict__ P,
@@ -462,15 +481,17 @@ __global__ void __launch_bounds__(256, 3)
   const int RS = N + 1;
   using XE = typename XS::elem;
   // tiles: W, P (padded rows) and, with DB, the X tile; two sets with DB
+  using TR = UpdTile<SS, DB>;
+  using TT = typename TR::T;
   const int tile_w = TS * 3 * RS;
   // one set = [W tile][P tile][X tile (DB only)]; set b starts b * set_bytes in
-  const size_t set_bytes =
-      2 * (size_t)tile_w * sizeof(cpx<real>) + (DB ? (size_t)TS * 3 * N * sizeof(XE) : 0);
-  auto tW = [&](int bsel) { return reinterpret_cast<cpx<real>*>(smem_raw + bsel * set_bytes); };
+  const size_t wp_bytes = upd_wp_bytes(TS, N, sizeof(TT));
+  const size_t set_bytes = wp_bytes + (DB ? (size_t)TS * 3 * N * sizeof(XE) : 0);
+  auto tW = [&](int bsel) { return reinterpret_cast<TT*>(smem_raw + bsel * set_bytes); };
   auto tP = [&](int bsel) { return tW(bsel) + tile_w; };
-  auto tX = [&](int bsel) { return reinterpret_cast<XE*>(tP(bsel) + tile_w); };
-  cpx<real>* sW = tW(0);
-  cpx<real>* sP = tP(0);
+  auto tX = [&](int bsel) { return reinterpret_cast<XE*>(smem_raw + bsel * set_bytes + wp_bytes); };
+  TT* sW = tW(0);
+  TT* sP = tP(0);
   XE* sX = tX(0);
   cpx<real>* sA = reinterpret_cast<cpx<real>*>(smem_raw + (DB ? 2 : 1) * set_bytes);  // Sinv chunk [N][JT]
   cpx<real>* sB = sA + N * JT;                         // BC chunk
@@ -516,10 +537,12 @@ __global__ void __launch_bounds__(256, 3)
       sX = tX(bcur);
     } else {
       __syncthreads();
-      for (int idx = threadIdx.x; idx < nel; idx += blockDim.x) {
-        const int rr = idx / N, cc = idx - rr * N;
-        sW[rr * RS + cc] = SS::load_nc(Q + base + idx);
-        sP[rr * RS + cc] = SS::load_nc(P + base + idx);
+      if constexpr (!DB) {
+        for (int idx = threadIdx.x; idx < nel; idx += blockDim.x) {
+          const int rr = idx / N, cc = idx - rr * N;
+          sW[rr * RS + cc] = SS::load_nc(Q + base + idx);
+          sP[rr * RS + cc] = SS::load_nc(P + base + idx);
+        }
       }
     }
     for (int j0 = 0; j0 < N; j0 += JT) {
@@ -540,8 +563,8 @@ __global__ void __launch_bounds__(256, 3)
         const int jg = o / nrows;
         const int row = o - jg * nrows;  // (site, colour)
         const int jj0 = jg * JB;
-        const cpx<real>* w = sW + row * RS;
-        const cpx<real>* p = sP + row * RS;
+        const TT* w = sW + row * RS;
+        const TT* p = sP + row * RS;
         cpx<acc> q[JB], x[JB], pn[JB];
 #pragma unroll
         for (int u = 0; u < JB; ++u) {
@@ -557,8 +580,8 @@ __global__ void __launch_bounds__(256, 3)
         const int i_band_end = min(N, jlo + JB);
         if (full) {
           for (int i = 0; i < jlo; ++i) {
-            const cpx<real> wi = w[i];
-            const cpx<real> pi = p[i];
+            const cpx<real> wi = TR::get(w + i);
+            const cpx<real> pi = TR::get(p + i);
             const cpx<real>* ca = sA + i * JT + jj0;
             const cpx<real>* cb = sB + i * JT + jj0;
 #pragma unroll
@@ -568,8 +591,8 @@ __global__ void __launch_bounds__(256, 3)
             }
           }
           for (int i = jlo; i < i_band_end; ++i) {
-            const cpx<real> wi = w[i];
-            const cpx<real> pi = p[i];
+            const cpx<real> wi = TR::get(w + i);
+            const cpx<real> pi = TR::get(p + i);
 #pragma unroll
             for (int u = 0; u < JB; ++u) {
               const int j = jlo + u;
@@ -580,7 +603,7 @@ __global__ void __launch_bounds__(256, 3)
           }
           if (!keepP) {
             for (int i = i_band_end; i < N; ++i) {
-              const cpx<real> pi = p[i];
+              const cpx<real> pi = TR::get(p + i);
               const cpx<real>* cb = sB + i * JT + jj0;
               const cpx<real>* cc = sC + i * JT + jj0;
 #pragma unroll
@@ -591,7 +614,7 @@ __global__ void __launch_bounds__(256, 3)
             }
           } else {
             for (int i = i_band_end; i < N; ++i) {
-              const cpx<real> pi = p[i];
+              const cpx<real> pi = TR::get(p + i);
               const cpx<real>* cb = sB + i * JT + jj0;
 #pragma unroll
               for (int u = 0; u < JB; ++u) cmac<C>(x[u], pi, cb[u]);
@@ -599,8 +622,8 @@ __global__ void __launch_bounds__(256, 3)
           }
         } else {  // ragged last group
           for (int i = 0; i < N; ++i) {
-            const cpx<real> wi = w[i];
-            const cpx<real> pi = p[i];
+            const cpx<real> wi = TR::get(w + i);
+            const cpx<real> pi = TR::get(p + i);
 #pragma unroll
             for (int u = 0; u < JB; ++u) {
               const int jj = jj0 + u;
@@ -650,15 +673,17 @@ static cudaError_t launch_bcg_update(void* Q, void* P, void* X, const double2* S
   // double-float: 2 output columns per thread keep the accumulators within the
   // register budget of four resident blocks (no spills); other kinds use 4
   constexpr int JB = std::is_same<SS, StoreDF>::value ? 2 : 4;
-  // FP32 storage: double-buffered tiles (W, P, X) filled by cp.async
-  constexpr bool DB = std::is_same<SS, StoreF32>::value;
+  // all kinds but double-float (ALU-bound, and its shared memory is spent on
+  // 4 resident blocks): double-buffered tiles (W, P, X) filled by cp.async
+  constexpr bool DB = !std::is_same<SS, StoreDF>::value;
   const size_t cb = sizeof(cpx<real>), xb = sizeof(typename XS::elem);
+  const size_t tb = DB ? sizeof(typename SS::elem) : cb;  // tile element bytes
   const int JT = (N + 1) < 16 ? (N + 1) : 16;
   const size_t coef = 3ull * N * JT * cb;
   const size_t budget = N <= 16 ? 56 * 1024 : 96 * 1024;
   int TS = 32;
   auto tile_bytes = [&](int ts) {
-    size_t one = 2ull * ts * 3 * (N + 1) * cb + (DB ? (size_t)ts * 3 * N * xb : 0);
+    size_t one = upd_wp_bytes(ts, N, tb) + (DB ? (size_t)ts * 3 * N * xb : 0);
     return (DB ? 2 : 1) * one;
   };
   while (TS > 1 && coef + tile_bytes(TS) > budget) TS >>= 1;
