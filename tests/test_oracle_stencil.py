@@ -177,3 +177,21 @@ def test_sampled_sites_match_full_application():
     pick = ev[[0, 5, 17, len(ev) - 1]]
     part = hisq.apply_A_sites(dims, fat, lng, mass, v, pick)
     assert np.abs(part - full[pick >> 1]).max() < 1e-14
+
+
+def test_batch_problem_set_is_seeded_and_in_range():
+    """The batched workload: 64 problems with L in {8, 12, 16}, m in
+    [0.01, 0.2], N in 2..16, reproducible from its seed, every problem with
+    its own link and source seeds."""
+    import hisq_inputs as hi
+    a = hi.batch_problems(64, seed=4000)
+    b = hi.batch_problems(64, seed=4000)
+    assert a == b
+    assert len(a) == 64
+    assert {p["dims"][0] for p in a} == {8, 12, 16}
+    assert all(p["dims"] == (p["dims"][0],) * 4 for p in a)
+    assert all(0.01 <= p["mass"] <= 0.2 for p in a)
+    assert all(2 <= p["n_rhs"] <= 16 for p in a)
+    seeds = [p["link_seed"] for p in a] + [p["source_seed"] for p in a]
+    assert len(set(seeds)) == len(seeds)
+    assert hi.batch_problems(64, seed=4001) != a
