@@ -43,7 +43,7 @@ SM_COUNT = 152
 FP32_LANES = 128
 SM_MAX_MHZ = 2070.0
 DF_INSTR_PER_FLOP = 6.0   # 12 FP32 instructions per double-float multiply-add (2 flops)
-STENCIL_FLOPS = 1158      # per site per right-hand side (Sec. 5.2)
+STENCIL_FLOPS = 1158      # per site per right-hand side (Sec. 6.2)
 
 
 def parse_args():

@@ -4,9 +4,9 @@
  *
  * Method: Clark, Strelchenko, Vaquero, Wagner, Weinberg, "Pushing memory
  * bandwidth limitations through efficient implementations of Block-Krylov
- * space solvers on GPUs" (arXiv:1710.09745).  Operator: Eq. 1 and Sec. 2.2;
+ * space solvers on GPUs" (arXiv:1710.09745).  Operator: Eq. 1 and Sec. 3.2;
  * solver: Algorithm 1 (blockCGrQ), Algorithm 2 (thin QR), Algorithm 3 (block
- * reliable updates); kernels: Sec. 5.2 (block stencil), 5.3 (streaming
+ * reliable updates); kernels: Sec. 6.2 (block stencil), 5.3 (streaming
  * multi-BLAS), 5.4 (reduction multi-BLAS).
  *
  * Conventions shared by every entry point
@@ -68,7 +68,7 @@ typedef enum {
   BLOCKCG_ERR_TIMEOUT = 7        /* a bounded device-side wait gave up */
 } blockcg_status;
 
-/* Precision of the solve (Sec. 4 storage formats, Algorithm 3).  In every
+/* Precision of the solve (Sec. 5 storage formats, Algorithm 3).  In every
  * form the reliable updates of Algorithm 3 (solution accumulator Y, sources
  * B, true residual R = B - A Y with its own stencil, thin QR of R) and all
  * N x N algebra run in native FP64.
@@ -107,7 +107,7 @@ typedef struct {
   int max_iter;        /* iteration limit (default 100000) */
   double ru_delta;     /* reliable update when the max relative iterated residual
                           fell by this factor since the last one (default 0.1;
-                          0 disables; Sec. 5 and 7.1) */
+                          0 disables; Sec. 6 and 7.1) */
   int ru_every;        /* >0: also a reliable update every ru_every iterations */
   blockcg_prec prec;   /* default BLOCKCG_PREC_F64 */
   int antiperiodic_t;  /* 1: antiperiodic boundary in t (default 0) */
@@ -140,8 +140,8 @@ typedef struct {
   double ms_stencil;       /* their summed device time (params.profile) */
   long long n_stencil_fine;  /* launches of the full-precision stencil (params.profile) */
   double ms_stencil_fine;    /* their summed device time (params.profile) */
-  double ms_gram;          /* params.profile: Gram partials + reductions (Sec. 5.4) */
-  double ms_stream;        /* params.profile: streaming block BLAS (Sec. 5.3) */
+  double ms_gram;          /* params.profile: Gram partials + reductions (Sec. 6.4) */
+  double ms_stream;        /* params.profile: streaming block BLAS (Sec. 6.3) */
   double ms_dense;         /* params.profile: N x N algebra on the device */
   int stencil_variant;     /* the iteration stencil's kernel choice (the
                               params.dslash_variant encoding, plus 1024 for
@@ -151,7 +151,7 @@ typedef struct {
 /* Fill *p with the defaults listed above. */
 void blockcg_default_params(blockcg_params* p);
 
-/* Create a handle for an Lx x Ly x Lz x Lt lattice (Sec. 2.2), quark mass
+/* Create a handle for an Lx x Ly x Lz x Lt lattice (Sec. 3.2), quark mass
  * `mass` (finite), parameters p (NULL: defaults) and stream (cudaStream_t,
  * NULL = legacy default stream).  Allocates host memory for the handle only.
  * Errors: BLOCKCG_ERR_ARG for odd or < 2 extents, V/2 >= 2^31, non-finite
@@ -184,13 +184,13 @@ size_t blockcg_workspace_bytes(blockcg_t h, int n_rhs);
  * largest n_rhs used).  Errors: ERR_ARG, ERR_NOMEM. */
 blockcg_status blockcg_set_workspace(blockcg_t h, void* ws, size_t bytes);
 
-/* out = D_{p,1-p} in: the block stencil of Sec. 5.2 (Eq. 1 hopping term),
+/* out = D_{p,1-p} in: the block stencil of Sec. 6.2 (Eq. 1 hopping term),
  * in on parity 1-out_parity, out on parity out_parity, both user layout
  * [n_rhs][Vh][3] complex128 on the device, computed in the handle's
  * precision.  Errors: ERR_ARG, ERR_NOMEM (no workspace/gauge), ERR_CUDA. */
 blockcg_status blockcg_dslash(blockcg_t h, const void* in, void* out, int n_rhs, int out_parity);
 
-/* out = A in = m^2 in - D_eo D_oe in on even sites (Sec. 2.2), user layout.
+/* out = A in = m^2 in - D_eo D_oe in on even sites (Sec. 3.2), user layout.
  * in and out must not overlap.  Errors as blockcg_dslash. */
 blockcg_status blockcg_apply_MdagM(blockcg_t h, const void* in, void* out, int n_rhs);
 
@@ -198,7 +198,7 @@ blockcg_status blockcg_apply_MdagM(blockcg_t h, const void* in, void* out, int n
  * the fat and long links, in the convention G = dL/dRe(u) + i dL/dIm(u) per
  * link entry u (so dL = Re sum conj(G) du; the convention of complex
  * automatic differentiation).  The paper only solves; this is the link part
- * of the adjoint of a differentiable solve (operator of Sec. 2.2, Eq. 1).
+ * of the adjoint of a differentiable solve (operator of Sec. 3.2, Eq. 1).
  *
  * X: the solution block x; Lam: the adjoint block lam = A^-1 g, g the
  * gradient of L with respect to x (a second solve with the same handle,
@@ -216,11 +216,11 @@ blockcg_status blockcg_apply_MdagM(blockcg_t h, const void* in, void* out, int n
 blockcg_status blockcg_link_grad(blockcg_t h, const void* X, const void* Lam, int n_rhs,
                                  void* grad_fat, void* grad_long);
 
-/* K = X^dag Y (block cDotProduct, Sec. 5.4): X, Y even-site blocks in user
+/* K = X^dag Y (block cDotProduct, Sec. 6.4): X, Y even-site blocks in user
  * layout; K device complex128 [n_rhs][n_rhs] row-major (K[i][j] = X_i^dag Y_j). */
 blockcg_status blockcg_block_cdot(blockcg_t h, const void* X, const void* Y, int n_rhs, void* K);
 
-/* Y = Y + X a (block caxpy, Sec. 5.3): a device complex128 [n_rhs][n_rhs]
+/* Y = Y + X a (block caxpy, Sec. 6.3): a device complex128 [n_rhs][n_rhs]
  * row-major (a[i][j] multiplies column i of X into column j of Y). */
 blockcg_status blockcg_block_caxpy(blockcg_t h, const void* X, const void* a, void* Y, int n_rhs);
 
@@ -246,7 +246,7 @@ blockcg_status blockcg_solve(blockcg_t h, const void* B, void* X, int n_rhs, dou
 blockcg_status blockcg_solve_cg(blockcg_t h, const void* B, void* X, int n_rhs, double tol,
                                 blockcg_stats* st);
 
-/* Time the block stencil of Sec. 5.2 alone (the measurement of Fig. 1):
+/* Time the block stencil of Sec. 6.2 alone (the measurement of Fig. 1):
  * `reps` back-to-back launches of out_parity = D in on n_rhs right-hand sides
  * in the iteration's precision (full precision if fine != 0), on internal
  * workspace buffers (whose contents are overwritten), bracketed by CUDA

@@ -7,10 +7,10 @@ never imports the product path.
 
 Contents:
   hisq_oracle.c   plain FP64 C: staggered stencil D (Eq. 1), the even-odd
-                  normal operator A = m^2 - D_eo D_oe (Sec. 2.2) and textbook
+                  normal operator A = m^2 - D_eo D_oe (Sec. 3.2) and textbook
                   CG per column (the baseline of Sec. 7.1)
   hisq.py         ctypes wrappers of the C functions on NumPy arrays
-  block.py        block cDot / block caxpy (Sec. 5.3, 5.4), thin QR
+  block.py        block cDot / block caxpy (Sec. 6.3, 5.4), thin QR
                   (Algorithm 2), blockCGrQ (Algorithm 1) and block reliable
                   updates (Algorithm 3), in NumPy FP64, step by step
   dense.py        dense matrix of A on tiny lattices, for brute-force checks

@@ -7,8 +7,8 @@ side j, L = 3 * (V/2) complex rows (the paper's X^{L x N}).  `as_columns` and
 `from_columns` convert from and to the [N][V/2][3] spinor-block layout.
 
 Functions follow, in order and notation:
-  block_cdot     K = X^dag Y,  k_ij = sum_k conj(x_ki) y_kj            (Sec. 5.4)
-  block_caxpy    Y + X a,      y_kj += sum_i x_ki a_ij                  (Sec. 5.3)
+  block_cdot     K = X^dag Y,  k_ij = sum_k conj(x_ki) y_kj            (Sec. 6.4)
+  block_caxpy    Y + X a,      y_kj += sum_i x_ki a_ij                  (Sec. 6.3)
   thin_qr        H = M^dag M; R^dag R = H (Cholesky); Q = M R^-1        (Algorithm 2)
   block_cg_rq    Algorithm 1, with the block reliable update of
                  Algorithm 3 (Y += X; X = 0; R = B - A Y; Q C = R;
@@ -34,12 +34,12 @@ def from_columns(cols: np.ndarray, vh: int) -> np.ndarray:
 
 
 def block_cdot(X: np.ndarray, Y: np.ndarray) -> np.ndarray:
-    """K = X^dag Y (block cDotProduct, Sec. 5.4)."""
+    """K = X^dag Y (block cDotProduct, Sec. 6.4)."""
     return X.conj().T @ Y
 
 
 def block_caxpy(Y: np.ndarray, X: np.ndarray, a: np.ndarray) -> np.ndarray:
-    """Y + X a (block caxpy, Sec. 5.3)."""
+    """Y + X a (block caxpy, Sec. 6.3)."""
     return Y + X @ a
 
 

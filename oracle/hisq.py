@@ -73,7 +73,7 @@ def dslash(dims, fat, lng, psi, out_parity: int, antiperiodic_t: bool = False) -
 
 
 def apply_A(dims, fat, lng, mass: float, v, antiperiodic_t: bool = False) -> np.ndarray:
-    """A v = m^2 v - D_eo D_oe v on even sites (Sec. 2.2)."""
+    """A v = m^2 v - D_eo D_oe v on even sites (Sec. 3.2)."""
     fat, lng = _check_links(dims, fat, lng)
     v = _c(v)
     squeeze = v.ndim == 2

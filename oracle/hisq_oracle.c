@@ -8,7 +8,7 @@
  * time, coordinates decoded from the lexicographic index on every access,
  * complex arithmetic through C99 `double complex`.
  *
- * Conventions (paper, Sec. 2.2, Eq. 1, with the readings stated below):
+ * Conventions (paper, Sec. 3.2, Eq. 1, with the readings stated below):
  *   - sites: lexicographic index i = x + Lx*(y + Ly*(z + Lz*t)), x fastest;
  *     parity p(x) = (x+y+z+t) & 1; checkerboard index cb = i >> 1 (Lx even).
  *   - links: fat F and long G, complex [4][V][3][3] (direction mu = x,y,z,t),
@@ -17,7 +17,7 @@
  *     (e.g. -1/24); staggered phases are NOT in the links.
  *   - staggered phases eta_mu(x) = (-1)^(sum_{nu<mu} x_nu).
  *   - hopping term (Eq. 1 with the anti-Hermitian sign reading on backward
- *     hops, so that M^dag M = m^2 - D_eo D_oe on even sites, Sec. 2.2):
+ *     hops, so that M^dag M = m^2 - D_eo D_oe on even sites, Sec. 3.2):
  *       (D psi)(x) = 1/2 sum_mu eta_mu(x) [ F_mu(x) psi(x+mu)
  *                                          - F_mu(x-mu)^dag psi(x-mu)
  *                                          + G_mu(x) psi(x+3mu)
@@ -354,7 +354,7 @@ int oracle_cg_iterates(const int dims[4], const cplx* fat, const cplx* lng, int 
  * Inputs: the even-site solution block x = A^-1 phi and the adjoint block
  * lam = A^-1 g, g being the gradient of L with respect to x.
  *
- * Derivation (Sec. 2.2 operator): dx = -A^-1 dA x, so dL = -Re lam^dag dA x,
+ * Derivation (Sec. 3.2 operator): dx = -A^-1 dA x, so dL = -Re lam^dag dA x,
  * and with dA = -(dD_eo D_oe + D_eo dD_oe), D anti-Hermitian (D_eo^dag =
  * -D_oe, and the same for dD), y = D_oe x and mu = D_oe lam:
  *     dL = Re[lam^dag dD_eo y] + Re[x^dag dD_eo mu].

@@ -3,7 +3,7 @@
 Forward: the block-CGrQ solve of the library (Algorithm 1 with reliable
 updates) for the links U = (fat, long) and the right-hand sides phi.
 Backward, given g = dL/dx: the adjoint block lam = A^-1 g is a second block
-solve with the same handle (A is Hermitian, Sec. 2.2), the gradient with
+solve with the same handle (A is Hermitian, Sec. 3.2), the gradient with
 respect to phi is lam, and the gradient with respect to the links comes from
 the library's outer-product kernel (blockcg_link_grad):
     dL = Re[lam^dag dD_eo y] + Re[x^dag dD_eo mu],  y = D_oe x, mu = D_oe lam.

@@ -5,11 +5,11 @@
 // word, so the host enqueues `check_every` iterations at a time and reads the
 // status only between such chunks:
 //
-//   T  = D_oe P                        stencil            (Sec. 5.2)
-//   AP = m^2 P - D_eo T                stencil + epilogue (Sec. 2.2)
-//   H  = P^dag AP                      Gram               (Sec. 5.4)
+//   T  = D_oe P                        stencil            (Sec. 6.2)
+//   AP = m^2 P - D_eo T                stencil + epilogue (Sec. 3.2)
+//   H  = P^dag AP                      Gram               (Sec. 6.4)
 //   beta = H^-1, BC = beta C           dense              (Algorithm 1)
-//   W  = Q - AP beta                   streaming          (Sec. 5.3)
+//   W  = Q - AP beta                   streaming          (Sec. 6.3)
 //   W^dag W = S^dag S, C = S C, res    Gram + dense       (Algorithm 2)
 //   Q = W S^-1, X += P BC, P = Q + P S^dag       one fused streaming pass
 //   [reliable update, gated]           Algorithm 3:
@@ -210,7 +210,7 @@ int tile_R(int N) { return N >= 8 ? 4 : (N >= 2 ? 2 : 1); }
 
 // Register tile of the stencil for (kind, N): tuned once per handle by timing
 // every candidate R on the handle's own buffers (the register-tile tuning of
-// Sec. 5.2); in is read, out is scratch.  Falls back to tile_R on any error.
+// Sec. 6.2); in is read, out is scratch.  Falls back to tile_R on any error.
 // the stencil flag of a kind's links: two-row storage for the iteration's
 // links when params.link_recon is set (the FP64 links are always complete)
 int recon_flag(const blockcg_ctx* h, FieldKind k) {

@@ -2,17 +2,17 @@
 // sides), stored site-major [site][colour][rhs] (row = (site, colour), the N
 // columns of a row contiguous).
 //
-//  * Reduction multi-BLAS (Sec. 5.4): K = X^dag Y as per-CTA partial sums
+//  * Reduction multi-BLAS (Sec. 6.4): K = X^dag Y as per-CTA partial sums
 //    (gram_partials) followed by a deterministic fixed-order FP64 reduction
 //    over CTAs (gram_reduce).  Hermitian Grams compute only the upper
 //    triangle and the reduction mirrors it (the Hermitian policy of
-//    Sec. 5.4).
-//  * Streaming multi-BLAS (Sec. 5.3): every kernel reads each input row once
+//    Sec. 6.4).
+//  * Streaming multi-BLAS (Sec. 6.3): every kernel reads each input row once
 //    and keeps the N x N work on chip, so traffic is linear in N.  The fused
 //    blockCGrQ update (bcg_update) stages a tile of sites of W and P in shared
 //    memory and produces, in one pass, Q = W S^-1 (S upper triangular: the
-//    zero half is skipped, Sec. 5.3), X += P (beta C) (the X update of
-//    Algorithm 1 using the P of this iteration, Sec. 5.2) and the next search
+//    zero half is skipped, Sec. 6.3), X += P (beta C) (the X update of
+//    Algorithm 1 using the P of this iteration, Sec. 6.2) and the next search
 //    block P = Q + P S^dag (Algorithm 1).  Coefficient columns are staged in
 //    chunks of JT columns so that N = 64 fits in shared memory.
 #include <type_traits>
@@ -160,7 +160,7 @@ int gram_blocks(int N, int rows) {
 // (coalesced 128-bit loads of whole sites), then each thread accumulates a
 // B x B block of entries (i, j) over the rows of its row group, so every
 // value read from shared memory feeds B complex multiply-adds.  Hermitian
-// Grams visit only the blocks on and above the block diagonal (Sec. 5.4).
+// Grams visit only the blocks on and above the block diagonal (Sec. 6.4).
 // The CTA walks the tiles grid-stride and writes one N x N partial (row-major
 // [i][j], only the blocks it computed) for the fixed-order reduction.
 template <class S, int B>

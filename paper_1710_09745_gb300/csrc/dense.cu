@@ -1,6 +1,6 @@
 // Small dense N x N algebra of blockCGrQ in native FP64, on the device, one
 // CTA per call (N <= 64).  The paper does these on the host with Eigen
-// (Sec. 5); keeping them on the device removes every host round trip from the
+// (Sec. 6); keeping them on the device removes every host round trip from the
 // iteration, so a whole iteration is a fixed sequence of launches gated by the
 // status word.
 //
@@ -39,7 +39,7 @@ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_doub
 // BLOCKCG_ERR_BREAKDOWN: d_k / A_kk is the squared sine of the angle between
 // column k and the span of the columns before it, so a value at rounding
 // level means the block is numerically rank deficient (e.g. linearly
-// dependent right-hand sides, Sec. 3).  Returns 0 or the error (uniform over
+// dependent right-hand sides, Sec. 4).  Returns 0 or the error (uniform over
 // the CTA).
 static constexpr double CHOL_REL_TOL = 1e-13;
 

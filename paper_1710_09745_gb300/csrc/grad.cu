@@ -1,5 +1,5 @@
 // Gradient of a real loss with respect to the fat and long links, for loss
-// functions of the solution x = A^-1 phi of the Sec. 2.2 normal operator.
+// functions of the solution x = A^-1 phi of the Sec. 3.2 normal operator.
 // (The paper solves and does not differentiate; this is the adjoint step of
 // a differentiable solve.)
 //

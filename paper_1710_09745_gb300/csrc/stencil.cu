@@ -1,4 +1,4 @@
-// Multi-RHS improved-staggered stencil (Sec. 5.2, Eq. 1).
+// Multi-RHS improved-staggered stencil (Sec. 6.2, Eq. 1).
 //
 // Links are repacked once per gauge field (pack_links) into, for each output
 // parity p and each of the 16 hops d = 4*mu + q (q: +1, -1, +3, -3 along mu),
@@ -11,9 +11,9 @@
 // one LW * 144-element block instead of 144 streams a parity apart.
 //
 // One thread owns one output site and a register tile of R right-hand sides
-// (the register tiling of Sec. 5.2); the T = ceil(N/R) threads of a site sit
+// (the register tiling of Sec. 6.2); the T = ceil(N/R) threads of a site sit
 // next to each other in a warp, so each link element is fetched once per
-// warp and broadcast (the cache tiling of Sec. 5.2 maps onto the broadcast of
+// warp and broadcast (the cache tiling of Sec. 6.2 maps onto the broadcast of
 // a warp-wide load).  Spinor blocks are site-major [site][colour][rhs] and
 // thread k of a site owns the right-hand sides k, k + T, k + 2T, ...: for one
 // (colour, r) the T threads of a site read T consecutive elements, so every

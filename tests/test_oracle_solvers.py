@@ -86,7 +86,7 @@ def test_thin_qr_against_householder():
 
 
 def test_block_cg_rq_n1_equals_cg_iterates():
-    """For N=1 blockCGrQ reduces to CG (Sec. 3): same iterates."""
+    """For N=1 blockCGrQ reduces to CG (Sec. 4): same iterates."""
     dims = (4, 4, 4, 4)
     mass = 0.1
     fat, lng, b = _setup(dims, mass, 1, seed=4)
@@ -137,7 +137,7 @@ def test_block_cg_rq_fewer_iterations_than_cg():
 
 
 def test_block_cg_rq_finite_termination_tiny():
-    """Exact arithmetic ends in at most L/N iterations (Sec. 3); L = 24 on 2^4."""
+    """Exact arithmetic ends in at most L/N iterations (Sec. 4); L = 24 on 2^4."""
     dims = (2, 2, 2, 2)
     mass = 0.1
     N = 4
