@@ -4,7 +4,7 @@
  *
  * Method: Clark, Strelchenko, Vaquero, Wagner, Weinberg, "Pushing memory
  * bandwidth limitations through efficient implementations of Block-Krylov
- * space solvers on GPUs" (arXiv:1710.09745).  Operator: Eq. 1 and Sec. 3.2;
+ * space solvers on GPUs" (arXiv:1710.09745).  Operator: Eq. 2 and Sec. 3.2;
  * solver: Algorithm 1 (blockCGrQ), Algorithm 2 (thin QR), Algorithm 3 (block
  * reliable updates); kernels: Sec. 6.2 (block stencil), 5.3 (streaming
  * multi-BLAS), 5.4 (reduction multi-BLAS).
@@ -26,7 +26,7 @@
  *      - F_mu(x-mu)^dag psi(x-mu) + G_mu(x) psi(x+3mu) - G_mu(x-3mu)^dag psi(x-3mu) ],
  *  periodic (optionally antiperiodic in t), and A = m^2 - D_eo D_oe on even
  *  sites, the Hermitian positive-definite Schur normal operator of
- *  M = m + D (Eq. 1 with the anti-Hermitian sign on backward hops).
+ *  M = m + D (Eq. 2 with the anti-Hermitian sign on backward hops).
  *
  *  Spinor blocks (user layout): complex128 [n_rhs][Vh][3], one parity,
  *  checkerboard-indexed; column j is right-hand side j.  1 <= n_rhs <= 64.
@@ -164,7 +164,7 @@ size_t blockcg_gauge_bytes(blockcg_t h);
 
 /* Reorder the caller's links (device complex128 [4][V][3][3] each, layout
  * above) into `storage` (device, >= blockcg_gauge_bytes): per output parity
- * the 16 hop matrices of Eq. 1 with staggered phases, the factor 1/2, the
+ * the 16 hop matrices of Eq. 2 with staggered phases, the factor 1/2, the
  * boundary sign and the backward-hop dagger and minus sign folded in, in
  * the storage formats the precision needs.  The caller may free fat/lng once
  * the stream has passed this call.  With params.link_recon = 12 it first
@@ -184,7 +184,7 @@ size_t blockcg_workspace_bytes(blockcg_t h, int n_rhs);
  * largest n_rhs used).  Errors: ERR_ARG, ERR_NOMEM. */
 blockcg_status blockcg_set_workspace(blockcg_t h, void* ws, size_t bytes);
 
-/* out = D_{p,1-p} in: the block stencil of Sec. 6.2 (Eq. 1 hopping term),
+/* out = D_{p,1-p} in: the block stencil of Sec. 6.2 (Eq. 2 hopping term),
  * in on parity 1-out_parity, out on parity out_parity, both user layout
  * [n_rhs][Vh][3] complex128 on the device, computed in the handle's
  * precision.  Errors: ERR_ARG, ERR_NOMEM (no workspace/gauge), ERR_CUDA. */
@@ -198,7 +198,7 @@ blockcg_status blockcg_apply_MdagM(blockcg_t h, const void* in, void* out, int n
  * the fat and long links, in the convention G = dL/dRe(u) + i dL/dIm(u) per
  * link entry u (so dL = Re sum conj(G) du; the convention of complex
  * automatic differentiation).  The paper only solves; this is the link part
- * of the adjoint of a differentiable solve (operator of Sec. 3.2, Eq. 1).
+ * of the adjoint of a differentiable solve (operator of Sec. 3.2, Eq. 2).
  *
  * X: the solution block x; Lam: the adjoint block lam = A^-1 g, g the
  * gradient of L with respect to x (a second solve with the same handle,
@@ -216,11 +216,11 @@ blockcg_status blockcg_apply_MdagM(blockcg_t h, const void* in, void* out, int n
 blockcg_status blockcg_link_grad(blockcg_t h, const void* X, const void* Lam, int n_rhs,
                                  void* grad_fat, void* grad_long);
 
-/* K = X^dag Y (block cDotProduct, Sec. 6.4): X, Y even-site blocks in user
+/* K = X^dag Y (block cDotProduct, Sec. 6.4, Eq. 4): X, Y even-site blocks in user
  * layout; K device complex128 [n_rhs][n_rhs] row-major (K[i][j] = X_i^dag Y_j). */
 blockcg_status blockcg_block_cdot(blockcg_t h, const void* X, const void* Y, int n_rhs, void* K);
 
-/* Y = Y + X a (block caxpy, Sec. 6.3): a device complex128 [n_rhs][n_rhs]
+/* Y = Y + X a (block caxpy, Sec. 6.3, Eq. 3): a device complex128 [n_rhs][n_rhs]
  * row-major (a[i][j] multiplies column i of X into column j of Y). */
 blockcg_status blockcg_block_caxpy(blockcg_t h, const void* X, const void* a, void* Y, int n_rhs);
 

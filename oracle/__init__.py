@@ -6,7 +6,7 @@ baseline leg may import or run anything in this package.  The product path
 never imports the product path.
 
 Contents:
-  hisq_oracle.c   plain FP64 C: staggered stencil D (Eq. 1), the even-odd
+  hisq_oracle.c   plain FP64 C: staggered stencil D (Eq. 2), the even-odd
                   normal operator A = m^2 - D_eo D_oe (Sec. 3.2) and textbook
                   CG per column (the baseline of Sec. 7.1)
   hisq.py         ctypes wrappers of the C functions on NumPy arrays

@@ -58,7 +58,7 @@ def _check_links(dims, fat, lng):
 
 
 def dslash(dims, fat, lng, psi, out_parity: int, antiperiodic_t: bool = False) -> np.ndarray:
-    """D restricted to out_parity <- 1-out_parity, on a block [N][V/2][3] (Eq. 1)."""
+    """D restricted to out_parity <- 1-out_parity, on a block [N][V/2][3] (Eq. 2)."""
     fat, lng = _check_links(dims, fat, lng)
     psi = _c(psi)
     squeeze = psi.ndim == 2

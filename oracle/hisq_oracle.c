@@ -8,7 +8,7 @@
  * time, coordinates decoded from the lexicographic index on every access,
  * complex arithmetic through C99 `double complex`.
  *
- * Conventions (paper, Sec. 3.2, Eq. 1, with the readings stated below):
+ * Conventions (paper, Sec. 3.2, Eq. 2, with the readings stated below):
  *   - sites: lexicographic index i = x + Lx*(y + Ly*(z + Lz*t)), x fastest;
  *     parity p(x) = (x+y+z+t) & 1; checkerboard index cb = i >> 1 (Lx even).
  *   - links: fat F and long G, complex [4][V][3][3] (direction mu = x,y,z,t),
@@ -16,7 +16,7 @@
  *     G_mu(x) connects x to x+3mu.  Long links carry their own coefficient
  *     (e.g. -1/24); staggered phases are NOT in the links.
  *   - staggered phases eta_mu(x) = (-1)^(sum_{nu<mu} x_nu).
- *   - hopping term (Eq. 1 with the anti-Hermitian sign reading on backward
+ *   - hopping term (Eq. 2 with the anti-Hermitian sign reading on backward
  *     hops, so that M^dag M = m^2 - D_eo D_oe on even sites, Sec. 3.2):
  *       (D psi)(x) = 1/2 sum_mu eta_mu(x) [ F_mu(x) psi(x+mu)
  *                                          - F_mu(x-mu)^dag psi(x-mu)

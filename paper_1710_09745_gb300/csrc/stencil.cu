@@ -1,8 +1,8 @@
-// Multi-RHS improved-staggered stencil (Sec. 6.2, Eq. 1).
+// Multi-RHS improved-staggered stencil (Sec. 6.2, Eq. 2).
 //
 // Links are repacked once per gauge field (pack_links) into, for each output
 // parity p and each of the 16 hops d = 4*mu + q (q: +1, -1, +3, -3 along mu),
-// the matrix that multiplies psi(x + k_q mu) in Eq. 1 with everything folded
+// the matrix that multiplies psi(x + k_q mu) in Eq. 2 with everything folded
 // in: 1/2, the staggered phase eta_mu(x), the boundary sign, and for the
 // backward hops the dagger and the minus sign of the anti-Hermitian reading.
 // Layout [p][site / LW][d * 9 + e][site % LW] (e = 0..8 matrix element,

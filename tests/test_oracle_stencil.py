@@ -1,5 +1,5 @@
 """Pins of the CPU oracle's stencil and normal operator against the
-mathematics of Sec. 3.2 / Eq. 1 (not against the oracle itself)."""
+mathematics of Sec. 3.2 / Eq. 2 (not against the oracle itself)."""
 import itertools
 
 import numpy as np
