@@ -491,7 +491,9 @@ def main():
                                     "ms_dense", "ms_total")}},
     }
 
-    if rank == 0 and not a.no_extras:
+    def extras():
+        """Context legs beside the headline line (not part of the timed
+        region); a failure in one is recorded in the line instead of losing it."""
         # N independent CG solves on the same sources (Sec. 7.1 baseline)
         _, ic = s.solve_cg(B, tol=a.tol)
         out["cg_baseline"] = {"ms_per_rhs": ic["ms_total"] / N, "iters_per_rhs": ic["iters"] / N,
@@ -575,6 +577,13 @@ def main():
                 "one_core": {"value": sec_it1 * iters * 1e3, "unit": UNIT, "cores": 1,
                              "sample": f"{k1} iterations ({sec_it1 * 1e3:.1f} ms each)"},
                 "apply_A_ms_per_rhs": apply_ms}
+
+    if rank == 0 and not a.no_extras:
+        try:
+            extras()
+        except Exception as exc:  # keep the headline line
+            out["extras_error"] = f"{type(exc).__name__}: {exc}"
+
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
