@@ -180,6 +180,23 @@ def oracle_sample(dims, mass, fat, lng, b0, budget_s=12.0):
     return (time.time() - t) / k, k
 
 
+def oracle_full_solves():
+    """Whole oracle solves (textbook CG to 1e-10, host cores) on the small
+    workloads: 4^4, m = 0.1, N = 4 and 16^4, m = 0.01, N = 1."""
+    import hisq_inputs as hi
+    from oracle import hisq
+    res = {}
+    for name, dims, mass, n in (("4^4 m=0.1 N=4", (4, 4, 4, 4), 0.1, 4),
+                                ("16^4 m=0.01 N=1", (16, 16, 16, 16), 0.01, 1)):
+        fat, lng = hi.random_links(dims, 1001)
+        b = hi.gaussian_sources(dims, n, 2001)
+        t = time.time()
+        _, iters, rr = hisq.cg(dims, fat, lng, mass, b, tol=1e-10, max_iter=20000)
+        res[name] = {"s": time.time() - t, "iters": [int(i) for i in iters],
+                     "true_rel_res_max": float(max(rr))}
+    return res
+
+
 def golden_cg_iterations(a):
     p = os.path.join(ROOT, "tests", "golden", "cg_iters_32x4.json")
     if not os.path.exists(p):
@@ -576,7 +593,8 @@ def main():
                           f"(the GPU CG baseline's count to {a.tol:g})",
                 "one_core": {"value": sec_it1 * iters * 1e3, "unit": UNIT, "cores": 1,
                              "sample": f"{k1} iterations ({sec_it1 * 1e3:.1f} ms each)"},
-                "apply_A_ms_per_rhs": apply_ms}
+                "apply_A_ms_per_rhs": apply_ms,
+                "full_solves": oracle_full_solves()}
 
     if rank == 0 and not a.no_extras:
         try:
