@@ -370,3 +370,23 @@ def test_solve_in_place_out_matches_allocating_solve():
     assert X3.data_ptr() == out2.data_ptr() and i3["iters"] == 0
     with pytest.raises(ValueError):
         s.solve(b, out=torch.zeros((2, b.shape[1], 3), dtype=b.dtype, device=b.device))
+
+
+@pytest.mark.parametrize("prec,N,dims", [("mixed_f32", 64, (4, 4, 4, 8)),
+                                          ("mixed_f32", 24, (4, 4, 4, 8)),
+                                          ("f64_native", 40, (8, 8, 4, 8))])
+def test_solve_wide_blocks_double_buffered_update(prec, N, dims):
+    """Wide blocks in the storage kinds whose fused update double-buffers its
+    tiles: small tiles (4 sites at N = 64) and several coefficient chunks.
+    The native-FP64 case runs on 8x8x4x8 (L = 3072 rows): on 4x4x4x8 (L = 768)
+    forty columns exhaust the space after L/N ~ 19 iterations and the block
+    breaks down in exact arithmetic too (the oracle's block CG reaches a
+    relative Cholesky pivot of 2e-14 there), which the solver reports as
+    BLOCKCG_ERR_BREAKDOWN."""
+    s, fat, lng = gh.make_solver(dims, 0.2, prec=prec, seed=1011, max_rhs=N)
+    b = hi.gaussian_sources(dims, N, seed=2011)
+    X, info = s.solve(b, tol=1e-10)
+    assert info["status"] == 0, info
+    r = b - hisq.apply_A(dims, fat, lng, 0.2, gh.to_np(X))
+    rel = np.linalg.norm(r.reshape(N, -1), axis=1) / np.linalg.norm(b.reshape(N, -1), axis=1)
+    assert rel.max() <= 1.05e-10
