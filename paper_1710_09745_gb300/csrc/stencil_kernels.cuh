@@ -1,5 +1,9 @@
 // Stencil kernels and their launch helpers, included once per storage kind
-// by stencil_<kind>.cu so that the kinds compile in parallel.
+// by stencil_<kind>.cu so that the kinds compile in parallel: the block
+// stencil of Sec. 6.2 (the hopping term of Eq. 2 applied to N right-hand
+// sides with every link loaded once per site), in three variants (plain,
+// per-thread cp.async prefetch, bulk-copy pipelined) and with the fused
+// epilogues of the normal operator (Sec. 3.2).
 #pragma once
 #include <type_traits>
 
