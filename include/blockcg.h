@@ -128,6 +128,11 @@ typedef struct {
                           blockcg_load_gauge checks (BLOCKCG_ERR_ARG otherwise);
                           only with MIXED_F32 / MIXED_F16 / MIXED_BF16 (the
                           FP64 links of the reliable updates stay complete) */
+  long long wait_limit_ns; /* bounded device-side waits (the bulk-copy stencil's
+                          mbarrier waits) give up after this many nanoseconds
+                          and the call reports BLOCKCG_ERR_TIMEOUT; 0 = 4 s
+                          (default).  Copies already issued are always waited
+                          for (up to 4 s) before a kernel returns. */
 } blockcg_params;
 
 typedef struct {
@@ -146,6 +151,13 @@ typedef struct {
   int stencil_variant;     /* the iteration stencil's kernel choice (the
                               params.dslash_variant encoding, plus 1024 for
                               two-row links) */
+  double* true_rel_res;    /* set by the caller: a host array of n_rhs doubles
+                              that receives |b_i - A x_i| / |b_i| per right-hand
+                              side at exit (the true residual of each column,
+                              computed in native FP64), or NULL to skip.  The
+                              library writes through it and leaves the pointer
+                              itself unchanged.  Entries are NaN if the solve
+                              failed before its first true-residual check. */
 } blockcg_stats;
 
 /* Fill *p with the defaults listed above. */
@@ -256,6 +268,16 @@ blockcg_status blockcg_solve_cg(blockcg_t h, const void* B, void* X, int n_rhs, 
 blockcg_status blockcg_bench_dslash(blockcg_t h, int n_rhs, int fine, int reps,
                                     double* ms_per_launch);
 
+/* Run the stencil autotuner for block width n_rhs now (the register-tile and
+ * kernel choice of Sec. 6.2, each candidate timed on the normal operator's
+ * pair of stencil launches), for the iteration's storage kind and for the
+ * native-FP64 kind of the reliable updates, so that a following solve of
+ * that width does not spend its first call tuning.  A no-op for a width
+ * already tuned on this handle or when params.dslash_variant fixes the
+ * kernel.  Zeroes and uses the workspace's block fields.  Synchronises the
+ * stream.  Errors: ERR_ARG, ERR_NOMEM, ERR_CUDA. */
+blockcg_status blockcg_tune(blockcg_t h, int n_rhs);
+
 /* K = X^dag Y, the same block inner product as blockcg_block_cdot, for
  * callers that cannot allocate device memory: code running inside a memory
  * pool it does not own, plug-ins that receive only the host application's
@@ -272,7 +294,10 @@ blockcg_status blockcg_bench_dslash(blockcg_t h, int n_rhs, int fine, int reps,
  * process exits.  The entry point calls no cudaMalloc, cudaFree or any other
  * allocating routine.  On its first call on a device (with that device
  * current) it looks up the array's device address once, so make that first
- * call before any stream capture.  Every call overwrites the whole region it
+ * call before any stream capture.  The looked-up address is kept for the life
+ * of the process: after cudaDeviceReset on a device it no longer refers to
+ * live memory, so do not call this entry point on a device that was reset.
+ * Every call overwrites the whole region it
  * uses, so no state carries over from one call to the next, but all calls
  * share the one array: calls whose kernels overlap on the GPU (e.g. on two
  * streams at once) race and must be serialised by the caller.

@@ -30,7 +30,7 @@ ABI_SYMBOLS = [
     "blockcg_solve_cg", "blockcg_bench_dslash", "blockcg_destroy", "blockcg_status_string",
     "blockcg_last_error", "blockcg_block_cdot_noalloc", "blockcg_batch_create",
     "blockcg_batch_solve", "blockcg_batch_destroy", "blockcg_batch_last_error",
-    "blockcg_link_grad",
+    "blockcg_link_grad", "blockcg_tune",
 ]
 
 BATCH_GRAPH = 1
@@ -39,7 +39,8 @@ BATCH_GRAPH = 1
 class Params(ct.Structure):
     _fields_ = [("max_iter", ct.c_int), ("ru_delta", ct.c_double), ("ru_every", ct.c_int),
                 ("prec", ct.c_int), ("antiperiodic_t", ct.c_int), ("check_every", ct.c_int),
-                ("profile", ct.c_int), ("dslash_variant", ct.c_int), ("link_recon", ct.c_int)]
+                ("profile", ct.c_int), ("dslash_variant", ct.c_int), ("link_recon", ct.c_int),
+                ("wait_limit_ns", ct.c_longlong)]
 
 
 class Stats(ct.Structure):
@@ -49,7 +50,7 @@ class Stats(ct.Structure):
                 ("ms_stencil", ct.c_double), ("n_stencil_fine", ct.c_longlong),
                 ("ms_stencil_fine", ct.c_double), ("ms_gram", ct.c_double),
                 ("ms_stream", ct.c_double), ("ms_dense", ct.c_double),
-                ("stencil_variant", ct.c_int)]
+                ("stencil_variant", ct.c_int), ("true_rel_res", ct.POINTER(ct.c_double))]
 
 
 class BatchStats(ct.Structure):
@@ -101,6 +102,7 @@ def load_library(path: str = LIB_PATH):
                                     ct.POINTER(Stats), ct.POINTER(I), ct.POINTER(BatchStats)]),
         "blockcg_batch_destroy": (None, [P]),
         "blockcg_link_grad": (I, [P, P, P, I, P, P]),
+        "blockcg_tune": (I, [P, I]),
         "blockcg_batch_last_error": (ct.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
@@ -129,7 +131,8 @@ class BlockCG:
     def __init__(self, dims, fat, lng, mass: float, prec: str = "f64", max_rhs: int = 16,
                  max_iter: int = 100000, ru_delta: float = 0.1, ru_every: int = 0,
                  antiperiodic_t: bool = False, check_every: int = 0, profile: bool = False,
-                 dslash_variant: int = 0, link_recon: int = 0, device=None):
+                 dslash_variant: int = 0, link_recon: int = 0, wait_limit_ns: int = 0,
+                 device=None):
         torch = _torch()
         L = load_library()
         self.lib = L
@@ -147,6 +150,7 @@ class BlockCG:
         p.profile = int(bool(profile))
         p.dslash_variant = int(dslash_variant)
         p.link_recon = int(link_recon)
+        p.wait_limit_ns = int(wait_limit_ns)
         self.params = p
         self.prec = prec
         h = ct.c_void_p()
@@ -293,6 +297,8 @@ class BlockCG:
         else:
             X = torch.zeros_like(B) if X0 is None else self._block(X0).clone()
         st = Stats()
+        per_rhs = (ct.c_double * B.shape[0])()
+        st.true_rel_res = ct.cast(per_rhs, ct.POINTER(ct.c_double))
         rc = fn(self.h, ct.c_void_p(B.data_ptr()), ct.c_void_p(X.data_ptr()), B.shape[0], float(tol),
                 ct.byref(st))
         info = {"iters": st.iters, "reliable_updates": st.reliable_updates,
@@ -300,7 +306,7 @@ class BlockCG:
                 "launches": st.launches, "n_stencil": st.n_stencil, "ms_stencil": st.ms_stencil,
                 "n_stencil_fine": st.n_stencil_fine, "ms_stencil_fine": st.ms_stencil_fine,
                 "ms_gram": st.ms_gram, "ms_stream": st.ms_stream, "ms_dense": st.ms_dense,
-                "stencil_variant": st.stencil_variant}
+                "stencil_variant": st.stencil_variant, "true_rel_res": list(per_rhs)}
         if rc not in (0, 6):
             self._check(rc)
         return X, info
@@ -315,6 +321,10 @@ class BlockCG:
     def solve_cg(self, B, X0=None, tol: float = 1e-10, out=None):
         """N sequential CG solves (baseline); returns (X, info); out as in solve."""
         return self._solve(self.lib.blockcg_solve_cg, B, X0, tol, out)
+
+    def tune(self, n_rhs: int):
+        """Run the stencil autotuner for block width n_rhs now (blockcg_tune)."""
+        self._check(self.lib.blockcg_tune(self.h, int(n_rhs)))
 
     def bench_dslash(self, n_rhs: int, reps: int = 20, fine: bool = False) -> float:
         """Mean device time (ms) of one block-stencil launch on n_rhs columns."""
@@ -379,13 +389,17 @@ class BlockCGBatch:
         Xp = (ct.c_void_p * n)(*[X.data_ptr() for X in Xd])
         Np = (ct.c_int * n)(*[B.shape[0] for B in Bd])
         st = (Stats * n)()
+        per_rhs = [(ct.c_double * B.shape[0])() for B in Bd]
+        for p in range(n):
+            st[p].true_rel_res = ct.cast(per_rhs[p], ct.POINTER(ct.c_double))
         status = (ct.c_int * n)()
         bst = BatchStats()
         flags = (BATCH_GRAPH if graph else 0) | ((int(trip) & 0xff) << 8)
         rc = self.lib.blockcg_batch_solve(self.b, Bp, Xp, Np, float(tol), flags,
                                           st, status, ct.byref(bst))
         infos = [{"iters": st[p].iters, "reliable_updates": st[p].reliable_updates,
-                  "true_rel_res_max": st[p].true_rel_res_max, "status": status[p]} for p in range(n)]
+                  "true_rel_res_max": st[p].true_rel_res_max, "status": status[p],
+                  "true_rel_res": list(per_rhs[p])} for p in range(n)]
         binfo = {"ms_total": bst.ms_total, "chunk": bst.chunk, "graph_replays": bst.graph_replays,
                  "graph_captures": bst.graph_captures, "graph_nodes": bst.graph_nodes,
                  "launches": bst.launches, "status": rc}

@@ -80,6 +80,7 @@ struct Ws {
   double2* partials;
   double2* mats;
   double* bnorm;
+  double* tres;  // per-column true relative residual of the last check
   SolverStatus* st;
   double* scal;  // CG scalars: rr, alpha, beta, gamma, alpha / gamma
   int* ierr;
@@ -112,6 +113,7 @@ Ws carve(const blockcg_ctx* h, int N, char* base) {
   w.partials = (double2*)take(np * sizeof(double2));
   w.mats = (double2*)take((size_t)M_COUNT * N * N * sizeof(double2));
   w.bnorm = (double*)take(N * sizeof(double));
+  w.tres = (double*)take(N * sizeof(double));
   w.st = (SolverStatus*)take(sizeof(SolverStatus));
   w.scal = (double*)take(8 * sizeof(double));
   w.ierr = (int*)take(sizeof(int));
@@ -142,6 +144,19 @@ blockcg_status cuda_fail(blockcg_ctx* h, cudaError_t e, const char* where) {
     ++h->launches;   \
     CK(call);        \
   } while (0)
+
+// two timing events destroyed on every return path
+struct EventPair {
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t create() {
+    cudaError_t e = cudaEventCreate(&a);
+    return e != cudaSuccess ? e : cudaEventCreate(&b);
+  }
+  ~EventPair() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+};
 
 cudaEvent_t pool_event(blockcg_ctx* h) {
   if (!h->ev_pool.empty()) {
@@ -339,7 +354,7 @@ blockcg_status restart_block(blockcg_ctx* h, const Ws& w, int N, double tol, int
   TL(TC_GRAM, gram_partials(h->fine, w.R, w.R, N, h->g.Vh, 1, w.partials, w.nblocks, gate, s));
   TL(TC_GRAM, gram_reduce(w.partials, w.nblocks, N, 1, mat(w, M_G, N), gate, s));
   TL(TC_DENSE, dense_restart(mat(w, M_G, N), mat(w, M_C, N), mat(w, M_CPREV, N), mat(w, M_CINV, N),
-                   mat(w, M_SHRU, N), w.bnorm, tol, init, N, w.st, gate, s));
+                   mat(w, M_SHRU, N), w.bnorm, w.tres, tol, init, N, w.st, gate, s));
   TL(TC_STREAM, restart_update(h->fine, h->sloppy, w.R, w.Q, w.P, mat(w, M_CINV, N), mat(w, M_SHRU, N), init,
                     N, h->g.Vh, gate, s));
   return BLOCKCG_OK;
@@ -402,6 +417,7 @@ blockcg_status solve_begin(blockcg_ctx* h, const Ws& w, const void* B, const voi
   Gate g0{nullptr, GATE_ALWAYS};
   Gate ga{w.st, GATE_ACTIVE};
   CK(cudaMemsetAsync(w.st, 0, sizeof(SolverStatus), s));
+  CK(cudaMemsetAsync(w.tres, 0xff, N * sizeof(double), s));  // NaN until a true residual exists
   KL(to_internal(h->fine, (const double2*)B, w.B, N, h->g.Vh, s));
   KL(to_internal(h->fine, (const double2*)X, w.Y, N, h->g.Vh, s));
   CK(zero_field(h->upd, w.X, nel, s));
@@ -446,6 +462,7 @@ void blockcg_default_params(blockcg_params* p) {
   p->profile = 0;
   p->dslash_variant = 0;
   p->link_recon = 0;
+  p->wait_limit_ns = 0;
 }
 
 const char* blockcg_status_string(blockcg_status s) {
@@ -486,6 +503,7 @@ blockcg_status blockcg_create(blockcg_t* out, const int dims[4], double mass,
     if (prm.dslash_variant != 0 && r != 1 && r != 2 && r != 4 && r != 8) return BLOCKCG_ERR_ARG;
   }
   if (prm.link_recon != 0 && prm.link_recon != 12) return BLOCKCG_ERR_ARG;
+  if (prm.wait_limit_ns < 0) return BLOCKCG_ERR_ARG;
   if (prm.link_recon == 12 && prm.prec != BLOCKCG_PREC_MIXED_F32 &&
       prm.prec != BLOCKCG_PREC_MIXED_F16 && prm.prec != BLOCKCG_PREC_MIXED_BF16)
     return BLOCKCG_ERR_ARG;
@@ -498,6 +516,7 @@ blockcg_status blockcg_create(blockcg_t* out, const int dims[4], double mass,
   h->g.Vh = (int)(V / 2);
   h->g.antiperiodic = prm.antiperiodic_t ? 1 : 0;
   h->g.inv_c[0] = h->g.inv_c[1] = 0.f;
+  h->g.wait_ns = (unsigned long long)prm.wait_limit_ns;
   h->mass = mass;
   h->p = prm;
   h->stream = (cudaStream_t)stream;
@@ -703,9 +722,9 @@ blockcg_status blockcg_solve(blockcg_t h, const void* B, void* X, int n_rhs, dou
   Ws w = carve(h, N, h->ws);
   cudaStream_t s = h->stream;
   reset_instrumentation(h);
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
+  EventPair ev;
+  CK(ev.create());
+  cudaEvent_t e0 = ev.a, e1 = ev.b;
   CK(cudaEventRecord(e0, s));
   rc = solve_begin(h, w, B, X, N, tol);
   if (rc) return rc;
@@ -735,8 +754,6 @@ blockcg_status blockcg_solve(blockcg_t h, const void* B, void* X, int n_rhs, dou
   drain_events(h);
   float ms = 0;
   cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   if (stats) {
     stats->iters = hs.iters;
     stats->reliable_updates = hs.reliable_updates;
@@ -744,6 +761,10 @@ blockcg_status blockcg_solve(blockcg_t h, const void* B, void* X, int n_rhs, dou
     stats->ms_total = ms;
     fill_stats(h, stats);
     stats->stencil_variant = cached_R(h, h->sloppy, N);
+    if (stats->true_rel_res) {
+      CK(cudaMemcpyAsync(stats->true_rel_res, w.tres, N * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+    }
   }
   return result;
 }
@@ -776,9 +797,9 @@ blockcg_status blockcg_solve_cg(blockcg_t h, const void* B, void* X, int n_rhs, 
   Gate ga{w.st, GATE_ACTIVE};
   Gate gi{w.st, GATE_ITER};
   reset_instrumentation(h);
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
+  EventPair ev;
+  CK(ev.create());
+  cudaEvent_t e0 = ev.a, e1 = ev.b;
   CK(cudaEventRecord(e0, s));
   int total_iters = 0, total_ru = 0;
   double worst = 0.0;
@@ -850,6 +871,7 @@ blockcg_status blockcg_solve_cg(blockcg_t h, const void* B, void* X, int n_rhs, 
       result = fail(h, BLOCKCG_ERR_NOT_CONVERGED, "max_iter reached");
     }
     if (hs.true_res_max > worst) worst = hs.true_res_max;
+    if (stats && stats->true_rel_res) stats->true_rel_res[j] = hs.true_res_max;
     KL(from_internal(fk, y, (double2*)X + j * col, 1, Vh, s));
   }
   CK(cudaEventRecord(e1, s));
@@ -857,8 +879,6 @@ blockcg_status blockcg_solve_cg(blockcg_t h, const void* B, void* X, int n_rhs, 
   drain_events(h);
   float ms = 0;
   cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   if (stats) {
     stats->iters = total_iters;
     stats->reliable_updates = total_ru;
@@ -867,6 +887,19 @@ blockcg_status blockcg_solve_cg(blockcg_t h, const void* B, void* X, int n_rhs, 
     fill_stats(h, stats);
   }
   return result;
+}
+
+blockcg_status blockcg_tune(blockcg_t h, int n_rhs) {
+  blockcg_status rc = check_ready(h, n_rhs);
+  if (rc) return rc;
+  const int N = n_rhs;
+  Ws w = carve(h, N, h->ws);
+  const size_t nel = (size_t)h->g.Vh * N * 3;
+  CK(cudaMemsetAsync(w.P, 0, nel * elem_bytes(h->sloppy), h->stream));
+  CK(cudaMemsetAsync(w.Y, 0, nel * elem_bytes(h->fine), h->stream));
+  tune_block(h, w, N);
+  CK(cudaStreamSynchronize(h->stream));
+  return BLOCKCG_OK;
 }
 
 blockcg_status blockcg_bench_dslash(blockcg_t h, int n_rhs, int fine, int reps,
@@ -887,18 +920,15 @@ blockcg_status blockcg_bench_dslash(blockcg_t h, int n_rhs, int fine, int reps,
   int R = stencil_R(h, k, N, links, in, out);
   // one untimed launch, then the timed ones
   KL(dslash(k, R, EPI_NONE, links, in, out, nullptr, nullptr, 0.0, h->g, 1, N, g0, s));
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
-  CK(cudaEventRecord(e0, s));
+  EventPair ev;
+  CK(ev.create());
+  CK(cudaEventRecord(ev.a, s));
   for (int i = 0; i < reps; ++i)
     KL(dslash(k, R, EPI_NONE, links, in, out, nullptr, nullptr, 0.0, h->g, 1, N, g0, s));
-  CK(cudaEventRecord(e1, s));
-  CK(cudaEventSynchronize(e1));
+  CK(cudaEventRecord(ev.b, s));
+  CK(cudaEventSynchronize(ev.b));
   float ms = 0;
-  cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  cudaEventElapsedTime(&ms, ev.a, ev.b);
   *ms_per_launch = ms / reps;
   return BLOCKCG_OK;
 }
@@ -1190,9 +1220,9 @@ blockcg_status blockcg_batch_solve(blockcg_batch_t b, const void* const* B, void
   }
   const bool use_graph = (flags & BLOCKCG_BATCH_GRAPH) != 0;
   BatchGuard guard(b);
-  cudaEvent_t e0, e1;
-  BK(cudaEventCreate(&e0));
-  BK(cudaEventCreate(&e1));
+  EventPair ev;
+  BK(ev.create());
+  cudaEvent_t e0 = ev.a, e1 = ev.b;
   // the batch runs after the caller's earlier work on its stream
   BK(cudaEventRecord(b->fork_ev, b->user));
   BK(cudaStreamWaitEvent(b->origin, b->fork_ev, 0));
@@ -1276,10 +1306,15 @@ blockcg_status blockcg_batch_solve(blockcg_batch_t b, const void* const* B, void
       b->err = "problem " + std::to_string(p) + ": " + h->err;
     }
     if (stats) {
+      double* per_rhs = stats[p].true_rel_res;  // the caller's array (or NULL)
       memset(&stats[p], 0, sizeof(blockcg_stats));
+      stats[p].true_rel_res = per_rhs;
       stats[p].iters = hs.iters;
       stats[p].reliable_updates = hs.reliable_updates;
       stats[p].true_rel_res_max = hs.true_res_max;
+      if (per_rhs)
+        BK(cudaMemcpyAsync(per_rhs, w.tres, N[p] * sizeof(double), cudaMemcpyDeviceToHost,
+                           b->streams[p]));
     }
     BK(cudaEventRecord(b->done_ev[p], b->streams[p]));
     BK(cudaStreamWaitEvent(b->origin, b->done_ev[p], 0));
@@ -1289,8 +1324,6 @@ blockcg_status blockcg_batch_solve(blockcg_batch_t b, const void* const* B, void
   BK(cudaEventSynchronize(e1));
   float ms = 0;
   cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   if (stats)
     for (int p = 0; p < n; ++p) stats[p].ms_total = ms;
   if (bstats) {

@@ -328,6 +328,8 @@ struct Geom {
   // inv_c[kind], inv_c = 1 / (c / 2) for the fat (0) and long (1) link scale c
   int antiperiodic;
   float inv_c[2];
+  // bounded device waits (bulk-copy stencil) give up after this many ns
+  unsigned long long wait_ns;
 };
 
 // coordinates of the site with checkerboard index cb on parity p
@@ -382,7 +384,9 @@ __device__ __forceinline__ int neighbour_cb_s(const Geom& g, int lex, int x, int
 // hop table: direction d = 4*mu + q, q = 0..3 -> k = +1, -1, +3, -3
 __device__ __forceinline__ int hop_k(int q) { return (q == 0) ? 1 : (q == 1) ? -1 : (q == 2) ? 3 : -3; }
 
-// Solver status word shared by the device-driven iteration (see solver.cu).
+// Solver status word of the device-driven iteration: written by the N x N
+// kernels of dense.cu (convergence, reliable-update trigger, breakdown) and by
+// bounded waits (time-out), read by the gated kernels and polled by api.cu.
 struct SolverStatus {
   int converged_iter;  // iteration at which the iterated residual met tol (or INT_MAX)
   int done;            // 1: true residual verified <= tol

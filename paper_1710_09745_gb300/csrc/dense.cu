@@ -250,8 +250,9 @@ cudaError_t dense_qr_step(const double2* G, double2* C, double2* C_prev, double2
 __global__ void __launch_bounds__(DENSE_THREADS)
     k_dense_restart(const double2* __restrict__ G, double2* __restrict__ C,
                     double2* __restrict__ C_prev, double2* __restrict__ Cinv,
-                    double2* __restrict__ SH, const double* __restrict__ bnorm, double tol,
-                    int init, int N, SolverStatus* st, int gmode) {
+                    double2* __restrict__ SH, const double* __restrict__ bnorm,
+                    double* __restrict__ tres_out, double tol, int init, int N, SolverStatus* st,
+                    int gmode) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int flag;
   __shared__ double tres[64];
@@ -260,7 +261,10 @@ __global__ void __launch_bounds__(DENSE_THREADS)
   double2* Wk = A + N * N;                            // L^-1, then C_prev^dag (lower)
   double2* Pi = Wk + N * N;                           // (C_prev^dag)^-1
   load_mat(A, G, N);
-  for (int i = threadIdx.x; i < N; i += blockDim.x) tres[i] = sqrt(fmax(A[i * N + i].x, 0.0)) / bnorm[i];
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    tres[i] = sqrt(fmax(A[i * N + i].x, 0.0)) / bnorm[i];
+    tres_out[i] = tres[i];
+  }
   __syncthreads();
   int f = chol_lower(A, N, &flag);
   if (f) {
@@ -306,12 +310,12 @@ __global__ void __launch_bounds__(DENSE_THREADS)
 }
 
 cudaError_t dense_restart(const double2* G, double2* C, double2* C_prev, double2* Cinv,
-                          double2* SH, const double* bnorm, double tol, int init, int N,
-                          SolverStatus* st, Gate gate, cudaStream_t s) {
+                          double2* SH, const double* bnorm, double* tres, double tol, int init,
+                          int N, SolverStatus* st, Gate gate, cudaStream_t s) {
   size_t sm = 3ull * N * N * sizeof(double2);
   cudaFuncSetAttribute(k_dense_restart, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_dense_restart<<<1, DENSE_THREADS, sm, s>>>(G, C, C_prev, Cinv, SH, bnorm, tol, init, N, st,
-                                               gate.mode);
+  k_dense_restart<<<1, DENSE_THREADS, sm, s>>>(G, C, C_prev, Cinv, SH, bnorm, tres, tol, init, N,
+                                               st, gate.mode);
   return cudaGetLastError();
 }
 

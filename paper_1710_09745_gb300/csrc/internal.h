@@ -136,9 +136,10 @@ cudaError_t dense_qr_step(const double2* G, double2* C, double2* C_prev, double2
                           SolverStatus* st, Gate gate, cudaStream_t s);
 // Cholesky of the true-residual Gram -> C_new, Cinv; convergence on the true
 // residual; S = C_new C_prev^-1 -> SH = S^dag (unless init).
+// tres (N doubles) receives the per-column true relative residuals.
 cudaError_t dense_restart(const double2* G, double2* C, double2* C_prev, double2* Cinv,
-                          double2* SH, const double* bnorm, double tol, int init, int N,
-                          SolverStatus* st, Gate gate, cudaStream_t s);
+                          double2* SH, const double* bnorm, double* tres, double tol, int init,
+                          int N, SolverStatus* st, Gate gate, cudaStream_t s);
 // bnorm_i = sqrt(Gb_ii); error if any is zero or not finite
 cudaError_t dense_bnorm(const double2* Gb, double* bnorm, int N, SolverStatus* st,
                         cudaStream_t s);

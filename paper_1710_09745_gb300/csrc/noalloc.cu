@@ -12,7 +12,10 @@
 // Host code must not hand the kernels the array's name: on the host it is a
 // stand-in symbol, not a device address.  The device address is looked up
 // once per device with cudaGetSymbolAddress, with that device current, on the
-// first call made while it is current.
+// first call made while it is current, and cached with the device's SM count.
+// The cache is not invalidated: after cudaDeviceReset the cached address
+// belongs to a context that no longer exists, so a process that resets a
+// device must not call this entry point on it again.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -82,9 +85,11 @@ __global__ void __launch_bounds__(NOALLOC_THREADS)
 
 static std::mutex g_noalloc_mutex;
 static void* g_noalloc_addr[NOALLOC_MAX_DEVICES];
+static int g_noalloc_sms[NOALLOC_MAX_DEVICES];
 
-// Device address of the scratch array on the current device (looked up once).
-static cudaError_t noalloc_scratch_address(void** out) {
+// Device address of the scratch array and SM count of the current device
+// (looked up once per device).
+static cudaError_t noalloc_scratch_address(void** out, int* sms) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -94,9 +99,14 @@ static cudaError_t noalloc_scratch_address(void** out) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
+    int n = 0;
+    e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    g_noalloc_sms[dev] = n > 0 ? n : 1;
     g_noalloc_addr[dev] = p;
   }
   *out = g_noalloc_addr[dev];
+  *sms = g_noalloc_sms[dev];
   return cudaSuccess;
 }
 
@@ -110,10 +120,11 @@ extern "C" blockcg_status blockcg_block_cdot_noalloc(const void* X, const void* 
   const int N = n_rhs;
   const long long rows = 3LL * vh;
   void* scratch = nullptr;
-  if (noalloc_scratch_address(&scratch) != cudaSuccess) return BLOCKCG_ERR_CUDA;
+  int sms = 1;
+  if (noalloc_scratch_address(&scratch, &sms) != cudaSuccess) return BLOCKCG_ERR_CUDA;
   // as many CTAs as the scratch holds partial matrices for, up to 4 per SM
   int nblocks = NOALLOC_SCRATCH_ELEMS / (N * N);
-  if (nblocks > 4 * 152) nblocks = 4 * 152;
+  if (nblocks > 4 * sms) nblocks = 4 * sms;
   long long by_rows = (rows + 63) / 64;
   if (nblocks > by_rows) nblocks = (int)by_rows;
   if (nblocks < 1) nblocks = 1;

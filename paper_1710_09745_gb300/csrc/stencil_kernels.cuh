@@ -233,9 +233,14 @@ __global__ void __launch_bounds__(BCG_DSLASH_TPB, BCG_DSLASH_MINB)
 // multiply from shared memory and accumulate in registers; after hop 15 they
 // write their outputs.  Loads for later hops are in flight while a hop is
 // computed, so the kernel no longer waits on one hop's loads at a time.
-// Every wait is bounded: on time-out the CTA records BLOCKCG_ERR_TIMEOUT in
-// the status word, waits (bounded) for copies it issued and returns.
-static constexpr uint64_t TMA_WAIT_LIMIT = 4000000000ull;  // 4 s of wall-clock time
+// Every wait is bounded (Geom::wait_ns, default 4 s): on time-out the CTA
+// records BLOCKCG_ERR_TIMEOUT in the status word and, before it returns,
+// waits for every stage it has issued, the stage that timed out included, so
+// that no bulk copy is still writing into its shared memory when it exits.
+// That drain has its own limit of TMA_DRAIN_LIMIT (copies of a few KB land in
+// microseconds; the limit only keeps a broken copy from hanging the kernel).
+static constexpr uint64_t TMA_WAIT_LIMIT = 4000000000ull;   // 4 s of wall-clock time
+static constexpr uint64_t TMA_DRAIN_LIMIT = 4000000000ull;  // 4 s
 
 template <class S, int RV, int V, int EPI, int STAGES>
 __global__ void __launch_bounds__(256)
@@ -269,6 +274,7 @@ __global__ void __launch_bounds__(256)
   }
   __syncthreads();
   const uint32_t spin_bytes = 3u * N * sizeof(E);
+  const uint64_t wait_ns = g.wait_ns ? (uint64_t)g.wait_ns : TMA_WAIT_LIMIT;
 
   auto issue = [&](long long task) {  // warp 0
     const long long unit = blockIdx.x + (task >> 4) * (long long)gridDim.x;
@@ -320,7 +326,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
           for (int i = 0; i < 3; ++i) a[r][w][i] = czero<C>();
     }
-    if (!mbar_wait_bounded(&full[st], (uint32_t)((tau / STAGES) & 1), TMA_WAIT_LIMIT)) {
+    if (!mbar_wait_bounded(&full[st], (uint32_t)((tau / STAGES) & 1), wait_ns)) {
       abort_flag = 1;
     } else if (valid) {
       const E* base = sbase + (size_t)st * stage_elems;
@@ -382,11 +388,13 @@ __global__ void __launch_bounds__(256)
     if (abort_flag) break;
   }
   if (abort_flag) {
-    // record the failure, then wait (bounded) for the copies still in flight
+    // record the failure, then wait for every stage issued and not yet
+    // consumed: tau (the one whose wait gave up) up to issued - 1.  Each of
+    // these STAGES at most distinct stages has exactly one phase pending.
     if (tid == 0) {
       if (errst) atomicExch(&errst->error, (int)7 /* BLOCKCG_ERR_TIMEOUT */);
-      for (long long q = tau + 1; q < issued; ++q)
-        mbar_wait_bounded(&full[q % STAGES], (uint32_t)((q / STAGES) & 1), TMA_WAIT_LIMIT);
+      for (long long q = tau; q < issued; ++q)
+        mbar_wait_bounded(&full[q % STAGES], (uint32_t)((q / STAGES) & 1), TMA_DRAIN_LIMIT);
     }
     __syncthreads();
   }

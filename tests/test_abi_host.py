@@ -169,3 +169,54 @@ def test_link_recon_parameter_checks(lib):
     f32_two = 2 * (V // 2 // 32) * 16 * 6 * 32 * 8
     assert sizes[("mixed_f32", 0)] == fine + f32_full
     assert sizes[("mixed_f32", 12)] == fine + f32_two + 256
+
+
+def _c_layout(struct, fields):
+    """offsetof/sizeof of a struct of include/blockcg.h, from a C program
+    compiled against the header (gcc, host only)."""
+    import subprocess
+    import tempfile
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "blockcg.h"', "int main(void) {",
+             f'  printf("%zu\\n", sizeof({struct}));']
+    lines += [f'  printf("%zu\\n", offsetof({struct}, {f}));' for f in fields]
+    lines += ["  return 0;", "}"]
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "layout.c"), os.path.join(d, "layout")
+        with open(src, "w") as f:
+            f.write("\n".join(lines))
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), src, "-o", exe], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split()
+    return [int(v) for v in out]
+
+
+@pytest.mark.parametrize("struct,cls", [("blockcg_params", "Params"), ("blockcg_stats", "Stats"),
+                                        ("blockcg_batch_stats", "BatchStats")])
+def test_binding_structs_match_the_header_layout(struct, cls):
+    """The ctypes mirrors of the ABI structs have the C compiler's field
+    offsets and sizes, including the per-right-hand-side residual pointer of
+    blockcg_stats and the wait limit of blockcg_params."""
+    from paper_1710_09745_gb300 import binding
+    C = getattr(binding, cls)
+    names = [f[0] for f in C._fields_]
+    got = _c_layout(struct, names)
+    assert got[0] == ct.sizeof(C)
+    for name, off in zip(names, got[1:]):
+        assert getattr(C, name).offset == off, name
+    if struct == "blockcg_stats":
+        assert "true_rel_res" in names
+    if struct == "blockcg_params":
+        assert "wait_limit_ns" in names
+
+
+def test_wait_limit_must_not_be_negative(lib):
+    from paper_1710_09745_gb300.binding import Params
+    h = ct.c_void_p()
+    d = (ct.c_int * 4)(4, 4, 4, 4)
+    p = Params()
+    lib.blockcg_default_params(ct.byref(p))
+    assert p.wait_limit_ns == 0
+    p.wait_limit_ns = -1
+    assert lib.blockcg_create(ct.byref(h), d, 0.1, ct.byref(p), None) == 1
+    p.wait_limit_ns = 1000
+    assert lib.blockcg_create(ct.byref(h), d, 0.1, ct.byref(p), None) == 0
+    lib.blockcg_destroy(h)

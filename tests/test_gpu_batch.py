@@ -67,6 +67,9 @@ def test_batch_equals_individual_solves(prec, graph):
         assert ii["iters"] == info["iters"]
         assert ii["reliable_updates"] == info["reliable_updates"]
         assert torch.equal(Xi, X)
+        # per-right-hand-side true residuals: the same as the single solve's
+        assert info["true_rel_res"] == ii["true_rel_res"]
+        assert max(info["true_rel_res"]) == info["true_rel_res_max"]
         assert _true_res(sp, fat, lng, b, to_np(X)).max() <= TOL * RES_SLACK
     batch.close()
 

@@ -390,3 +390,63 @@ def test_solve_wide_blocks_double_buffered_update(prec, N, dims):
     r = b - hisq.apply_A(dims, fat, lng, 0.2, gh.to_np(X))
     rel = np.linalg.norm(r.reshape(N, -1), axis=1) / np.linalg.norm(b.reshape(N, -1), axis=1)
     assert rel.max() <= 1.05e-10
+
+
+def _oracle_rel_res(dims, fat, lng, mass, b, X):
+    r = b - hisq.apply_A(dims, fat, lng, mass, X)
+    n = b.shape[0]
+    return np.linalg.norm(r.reshape(n, -1), axis=1) / np.linalg.norm(b.reshape(n, -1), axis=1)
+
+
+@pytest.mark.parametrize("prec", ["f64", "mixed_f32", "mixed_f16"])
+def test_per_rhs_true_residuals_match_oracle(prec):
+    """blockcg_stats.true_rel_res: the library's per-column true relative
+    residual |b_i - A x_i| / |b_i| at exit against the oracle's, recomputed in
+    FP64 on the CPU from the returned X.  Both are FP64 computations of a
+    residual ~1e-10 |b|, so they agree to ~1e-15 |b| (absolute, relative to
+    |b_i|), not to a relative 1e-15."""
+    dims, mass, N = (8, 8, 8, 8), 0.05, 6
+    s, fat, lng = gh.make_solver(dims, mass, prec=prec, seed=1021, max_rhs=8)
+    b = hi.gaussian_sources(dims, N, seed=2021)
+    X, info = s.solve(b, tol=1e-10)
+    assert info["status"] == 0
+    ref = _oracle_rel_res(dims, fat, lng, mass, b, gh.to_np(X))
+    got = np.array(info["true_rel_res"])
+    assert got.shape == (N,) and np.isfinite(got).all()
+    assert np.abs(got - ref).max() < 1e-13
+    assert abs(got.max() - info["true_rel_res_max"]) < 1e-15
+    assert got.max() <= 1e-10
+    # the CG baseline fills the same array, column by column
+    Xc, ic = s.solve_cg(b[:3], tol=1e-10)
+    refc = _oracle_rel_res(dims, fat, lng, mass, b[:3], gh.to_np(Xc))
+    assert np.abs(np.array(ic["true_rel_res"]) - refc).max() < 1e-13
+
+
+def test_bulk_copy_wait_limit_reports_timeout_and_context_survives():
+    """A bounded device wait that runs out: the bulk-copy stencil with a
+    1 ns wait limit gives up on its first stage, waits for every copy it has
+    issued, records BLOCKCG_ERR_TIMEOUT and returns; the solve reports it and
+    the context stays usable (a normal solve follows)."""
+    dims, mass, N = (8, 8, 8, 8), 0.05, 4
+    s, fat, lng = gh.make_solver(dims, mass, seed=1022, max_rhs=4, dslash_variant=TMA + 2,
+                                 wait_limit_ns=1)
+    b = hi.gaussian_sources(dims, N, seed=2022)
+    _, info = s.solve(b, tol=1e-10)
+    assert info["status"] == 7
+    s.close()
+    s2, fat, lng = gh.make_solver(dims, mass, seed=1022, max_rhs=4, dslash_variant=TMA + 2)
+    X, info2 = s2.solve(b, tol=1e-10)
+    assert info2["status"] == 0
+    assert _oracle_rel_res(dims, fat, lng, mass, b, gh.to_np(X)).max() <= 1e-10
+
+
+def test_tune_then_solve_uses_the_tuned_kernel():
+    """blockcg_tune runs the autotuner ahead of the solve; the solve then
+    reports the tuned kernel and converges as usual."""
+    dims, mass, N = (8, 8, 8, 8), 0.05, 8
+    s, fat, lng = gh.make_solver(dims, mass, seed=1023, max_rhs=8)
+    s.tune(N)
+    b = hi.gaussian_sources(dims, N, seed=2023)
+    X, info = s.solve(b, tol=1e-10)
+    assert info["status"] == 0 and info["stencil_variant"] != 0
+    assert _oracle_rel_res(dims, fat, lng, mass, b, gh.to_np(X)).max() <= 1e-10
