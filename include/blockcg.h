@@ -128,11 +128,13 @@ typedef struct {
                           blockcg_load_gauge checks (BLOCKCG_ERR_ARG otherwise);
                           only with MIXED_F32 / MIXED_F16 / MIXED_BF16 (the
                           FP64 links of the reliable updates stay complete) */
-  long long wait_limit_ns; /* bounded device-side waits (the bulk-copy stencil's
-                          mbarrier waits) give up after this many nanoseconds
-                          and the call reports BLOCKCG_ERR_TIMEOUT; 0 = 4 s
-                          (default).  Copies already issued are always waited
-                          for (up to 4 s) before a kernel returns. */
+  long long wait_limit_ns; /* watchdog of bounded device-side waits (the
+                          bulk-copy stencil's mbarrier waits): a thread block
+                          gives up waiting once this many nanoseconds have
+                          passed since it started, and the call reports
+                          BLOCKCG_ERR_TIMEOUT; 0 = 4 s (default).  Copies
+                          already issued are always waited for (up to 4 s)
+                          before a kernel returns. */
 } blockcg_params;
 
 typedef struct {

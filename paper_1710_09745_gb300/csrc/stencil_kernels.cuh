@@ -233,11 +233,12 @@ __global__ void __launch_bounds__(BCG_DSLASH_TPB, BCG_DSLASH_MINB)
 // multiply from shared memory and accumulate in registers; after hop 15 they
 // write their outputs.  Loads for later hops are in flight while a hop is
 // computed, so the kernel no longer waits on one hop's loads at a time.
-// Every wait is bounded (Geom::wait_ns, default 4 s): on time-out the CTA
-// records BLOCKCG_ERR_TIMEOUT in the status word and, before it returns,
-// waits for every stage it has issued, the stage that timed out included, so
-// that no bulk copy is still writing into its shared memory when it exits.
-// That drain has its own limit of TMA_DRAIN_LIMIT (copies of a few KB land in
+// Every wait is bounded by a watchdog deadline: Geom::wait_ns (default 4 s)
+// after the CTA started.  Once it has passed, the CTA records
+// BLOCKCG_ERR_TIMEOUT in the status word and, before it returns, waits for
+// every stage it has issued, the stage that timed out included, so that no
+// bulk copy is still writing into its shared memory when it exits.  That
+// drain has its own limit of TMA_DRAIN_LIMIT (copies of a few KB land in
 // microseconds; the limit only keeps a broken copy from hanging the kernel).
 static constexpr uint64_t TMA_WAIT_LIMIT = 4000000000ull;   // 4 s of wall-clock time
 static constexpr uint64_t TMA_DRAIN_LIMIT = 4000000000ull;  // 4 s
@@ -274,7 +275,8 @@ __global__ void __launch_bounds__(256)
   }
   __syncthreads();
   const uint32_t spin_bytes = 3u * N * sizeof(E);
-  const uint64_t wait_ns = g.wait_ns ? (uint64_t)g.wait_ns : TMA_WAIT_LIMIT;
+  const uint64_t deadline =
+      global_ns() + (g.wait_ns ? (uint64_t)g.wait_ns : TMA_WAIT_LIMIT);
 
   auto issue = [&](long long task) {  // warp 0
     const long long unit = blockIdx.x + (task >> 4) * (long long)gridDim.x;
@@ -326,7 +328,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
           for (int i = 0; i < 3; ++i) a[r][w][i] = czero<C>();
     }
-    if (!mbar_wait_bounded(&full[st], (uint32_t)((tau / STAGES) & 1), wait_ns)) {
+    if (!mbar_wait_until(&full[st], (uint32_t)((tau / STAGES) & 1), deadline)) {
       abort_flag = 1;
     } else if (valid) {
       const E* base = sbase + (size_t)st * stage_elems;

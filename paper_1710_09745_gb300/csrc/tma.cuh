@@ -55,6 +55,17 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
+// wait for the phase with the given parity to complete, giving up once the
+// wall clock passes deadline_ns (checked before every attempt, so a deadline
+// already passed fails at once); returns false on timeout
+__device__ __forceinline__ bool mbar_wait_until(uint64_t* bar, uint32_t phase,
+                                                uint64_t deadline_ns) {
+  for (;;) {
+    if (global_ns() > deadline_ns) return false;
+    if (mbar_try_wait(bar, phase)) return true;
+  }
+}
+
 // wait for the phase with the given parity to complete, giving up after
 // limit_ns nanoseconds of wall-clock time; returns false on timeout
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase,
