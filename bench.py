@@ -65,6 +65,9 @@ def parse_args():
                     help="only the batched leg (64 small problems, one CUDA graph)")
     ap.add_argument("--autograd-only", action="store_true",
                     help="only the differentiable-solve leg (16^4, N = 8)")
+    ap.add_argument("--legs", nargs="*", default=None,
+                    help="run only these context legs (cg f64_native mixed dslash width "
+                         "fine_tol config3 batched autograd alu cpu)")
     return ap.parse_args()
 
 
@@ -508,78 +511,193 @@ def main():
                                     "ms_dense", "ms_total")}},
     }
 
+    forms = {"f64": "iteration fields P, Q, AP, T, update X and links in double-float (FP32 "
+                     "hi+lo pairs, ~48 significant bits) with error-free double-float arithmetic "
+                     "on the FP32 pipes; reliable updates (Y, B, R, FP64 stencil, QR of R) and "
+                     "all N x N algebra in native FP64",
+             "f64_native": "native FP64 storage and arithmetic everywhere (the plain-FP64 form)",
+             "mixed_f32": "sloppy P, Q, AP, T and links in FP32 with FP32 arithmetic; X in "
+                          "double-float; native-FP64 reliable updates and N x N algebra",
+             "mixed_f16": "as mixed_f32 with FP16 storage (2^4-scaled) and a reliable update "
+                          "every 10 iterations"}
+    out["forms"] = forms
+    out["solve"]["true_rel_res"] = infos[-1]["true_rel_res"]
+
     def extras():
-        """Context legs beside the headline line (not part of the timed
-        region); a failure in one is recorded in the line instead of losing it."""
-        # N independent CG solves on the same sources (Sec. 7.1 baseline)
-        _, ic = s.solve_cg(B, tol=a.tol)
-        out["cg_baseline"] = {"ms_per_rhs": ic["ms_total"] / N, "iters_per_rhs": ic["iters"] / N,
-                              "true_rel_res_max": ic["true_rel_res_max"],
-                              "block_speedup": (ic["ms_total"] / N) / value,
-                              "stencil_avg_launch_ms": ic["ms_stencil"] / max(ic["n_stencil"], 1)}
-        # mixed-precision forms (Algorithm 3): FP32 and FP16 sloppy storage
-        for key, prec in (("mixed", "mixed_f32"), ("mixed_f16", "mixed_f16")):
-            sm = BlockCG(dims, fat, lng, a.mass, prec=prec, max_rhs=max(N, 32), profile=True,
+        """Context legs beside the headline line (outside the timed region)."""
+        col0 = {"f64": X[0].cpu().numpy()}  # column 0 of each form's solution (oracle error)
+
+        def leg(name, fn):
+            """A context leg beside the headline (outside the timed region); its
+            failure is recorded in the line instead of losing the line."""
+            if a.legs and name not in a.legs:
+                return
+            try:
+                fn()
+            except Exception as exc:
+                out.setdefault("leg_errors", {})[name] = f"{type(exc).__name__}: {exc}"
+
+        def free_cuda():
+            import gc
+            gc.collect()
+            torch.cuda.empty_cache()
+
+        def cg_leg():
+            # N independent CG solves on the same sources (Sec. 7.1 baseline)
+            _, ic = s.solve_cg(B, tol=a.tol)
+            out["cg_baseline"] = {"ms_per_rhs": ic["ms_total"] / N, "iters_per_rhs": ic["iters"] / N,
+                                  "true_rel_res_max": ic["true_rel_res_max"],
+                                  "block_speedup": (ic["ms_total"] / N) / value,
+                                  "per_rhs_iteration_ratio": (value / out["solve"]["iters"]) /
+                                  ((ic["ms_total"] / N) / (ic["iters"] / N)),
+                                  "stencil_avg_launch_ms": ic["ms_stencil"] / max(ic["n_stencil"], 1)}
+
+        def form_leg(key, prec, n_cg):
+            """One solver form on the headline workload: block CGrQ (tuned
+            first, then one timed solve) and n_cg independent CG solves."""
+            sf = BlockCG(dims, fat, lng, a.mass, prec=prec, max_rhs=max(N, 32), profile=True,
                          device=dev)
-            sm.solve(B, tol=a.tol)
-            _, im = sm.solve(B, tol=a.tol)
-            _, imc = sm.solve_cg(B[:4], tol=a.tol)
-            out[key] = {"ms_per_rhs": im["ms_total"] / N, "iters": im["iters"],
+            sf.tune(N)
+            Xf, im = sf.solve(B, tol=a.tol)
+            _, imc = sf.solve_cg(B[:n_cg], tol=a.tol)
+            col0[prec] = Xf[0].cpu().numpy()
+            ms_rhs = im["ms_total"] / N
+            cg_rhs = imc["ms_total"] / n_cg
+            out[key] = {"ms_per_rhs": ms_rhs, "iters": im["iters"],
                         "reliable_updates": im["reliable_updates"],
                         "true_rel_res_max": im["true_rel_res_max"],
+                        "true_rel_res": im["true_rel_res"],
+                        "converged": im["status"] == 0 and im["true_rel_res_max"] <= a.tol,
                         "ms_breakdown": {k: im[k] for k in ("ms_stencil", "ms_stencil_fine",
                                                             "ms_gram", "ms_stream", "ms_dense",
                                                             "ms_total")},
                         "stencil_variant": im["stencil_variant"],
-                        "cg_ms_per_rhs": imc["ms_total"] / 4, "cg_iters_per_rhs": imc["iters"] / 4,
-                        "block_speedup": (imc["ms_total"] / 4) / (im["ms_total"] / N)}
-            if prec == "mixed_f32":
-                s32 = sm
-            else:
-                s16 = sm
-        # Dslash GB/s per N (Fig. 1 analogue) for each storage format; "f32r12":
-        # FP32 with two-row links, its GB/s counted with 18 reals per link as
-        # for the others (the method's bytes), so it can exceed the HBM copy rate
-        s32r = BlockCG(dims, fat, lng, a.mass, prec="mixed_f32", max_rhs=32, link_recon=12,
-                       device=dev)
-        sweep = {}
-        for n in (1, 4, 8, 16, 32):
-            row = {}
-            for name, h, bpr in (("f32", s32, 4), ("f32r12", s32r, 4), ("f16", s16, 2),
-                                 ("df", s, 8)):
-                ms = h.bench_dslash(n, reps=10)
-                gbs = (288 + 12 * n) * bpr * Vh / (ms * 1e-3) / 1e9
-                row[name] = {"ms": ms, "gbs": gbs, "hbm_frac": gbs / hbm_peak,
-                             "gflops": STENCIL_FLOPS * n * Vh / (ms * 1e-3) / 1e9}
-            sweep[str(n)] = row
-        out["dslash"] = sweep
-        del s32, s16, s32r
-        # time to solution per RHS against the block width (F64 form, same
-        # sources: the first n columns of a 32-column block)
-        import hisq_inputs as hi
-        b32 = torch.as_tensor(hi.gaussian_sources(dims, 32, SRC_SEED)).to(dev)
-        sN = BlockCG(dims, fat, lng, a.mass, prec=a.prec, max_rhs=32, device=dev)
-        width = {}
-        for n in (1, 4, 8, 16, 32):
-            sN.solve(b32[:n], tol=a.tol)  # tuning for this width
-            _, iN = sN.solve(b32[:n], tol=a.tol)
-            width[str(n)] = {"ms_per_rhs": iN["ms_total"] / n, "iters": iN["iters"],
-                             "reliable_updates": iN["reliable_updates"],
-                             "true_rel_res_max": iN["true_rel_res_max"]}
-        out["block_width"] = width
-        del sN, b32
-        out["batched"] = batched_leg(a.tol, dev)
-        out["autograd"] = autograd_leg(dev)
-        # CPU oracle on a bounded sample (rank 0, one GPU)
-        if world == 1:
+                        "cg_rhs": n_cg, "cg_ms_per_rhs": cg_rhs, "cg_iters_per_rhs": imc["iters"] / n_cg,
+                        "cg_true_rel_res_max": imc["true_rel_res_max"],
+                        "block_speedup": cg_rhs / ms_rhs,
+                        "per_rhs_iteration_ratio": (ms_rhs / im["iters"]) /
+                        (cg_rhs / (imc["iters"] / n_cg))}
+            return sf
+
+        def f64_native_leg():
+            # the plain-FP64 form: block CGrQ vs independent CG, native FP64 throughout
+            sf = form_leg("f64_native", "f64_native", 4)
+            del sf
+            free_cuda()
+
+        handles = {}
+
+        def mixed_legs():
+            handles["mixed_f32"] = form_leg("mixed", "mixed_f32", 4)
+            handles["mixed_f16"] = form_leg("mixed_f16", "mixed_f16", 4)
+            # the best CG of any form as a baseline for the 16-bit block solve
+            best = min(out[k]["cg_ms_per_rhs"] for k in ("mixed", "mixed_f16"))
+            if "cg_baseline" in out:
+                best = min(best, out["cg_baseline"]["ms_per_rhs"])
+            out["mixed_f16"]["block_speedup_vs_best_cg"] = best / out["mixed_f16"]["ms_per_rhs"]
+
+        def dslash_leg():
+            # Dslash GB/s per N (Fig. 1 analogue) for each storage format; "f32r12":
+            # FP32 with two-row links, its GB/s counted with 18 reals per link as
+            # for the others (the method's bytes), so it can exceed the HBM copy rate
+            s32 = handles.get("mixed_f32") or BlockCG(dims, fat, lng, a.mass, prec="mixed_f32",
+                                                      max_rhs=32, device=dev)
+            s16 = handles.get("mixed_f16") or BlockCG(dims, fat, lng, a.mass, prec="mixed_f16",
+                                                      max_rhs=32, device=dev)
+            s32r = BlockCG(dims, fat, lng, a.mass, prec="mixed_f32", max_rhs=32, link_recon=12,
+                           device=dev)
+            sweep = {}
+            for n in (1, 4, 8, 16, 32):
+                row = {}
+                for name, h, bpr in (("f32", s32, 4), ("f32r12", s32r, 4), ("f16", s16, 2),
+                                     ("df", s, 8)):
+                    ms = h.bench_dslash(n, reps=10)
+                    gbs = (288 + 12 * n) * bpr * Vh / (ms * 1e-3) / 1e9
+                    row[name] = {"ms": ms, "gbs": gbs, "hbm_frac": gbs / hbm_peak,
+                                 "gflops": STENCIL_FLOPS * n * Vh / (ms * 1e-3) / 1e9}
+                sweep[str(n)] = row
+            out["dslash"] = sweep
+
+        def width_leg():
+            # time to solution per RHS against the block width (F64 form, same
+            # sources: the first n columns of a 32-column block)
+            import hisq_inputs as hi
+            b32 = torch.as_tensor(hi.gaussian_sources(dims, 32, SRC_SEED)).to(dev)
+            sN = BlockCG(dims, fat, lng, a.mass, prec=a.prec, max_rhs=32, device=dev)
+            width = {}
+            for n in (1, 4, 8, 16, 32):
+                sN.tune(n)
+                _, iN = sN.solve(b32[:n], tol=a.tol)
+                width[str(n)] = {"ms_per_rhs": iN["ms_total"] / n, "iters": iN["iters"],
+                                 "reliable_updates": iN["reliable_updates"],
+                                 "true_rel_res_max": iN["true_rel_res_max"]}
+            out["block_width"] = width
+
+        def fine_tol_leg():
+            # the F64 form at the paper's fine tolerance, for the solution error
+            # against the oracle (column 0; the oracle solves to the same 1e-12)
+            X12, i12 = s.solve(B, tol=1e-12)
+            col0["f64@1e-12"] = X12[0].cpu().numpy()
+            out["f64_tol_1e-12"] = {"ms_per_rhs": i12["ms_total"] / N, "iters": i12["iters"],
+                                    "true_rel_res_max": i12["true_rel_res_max"]}
+
+        def config3_leg():
+            """48^3 x 96, m = 0.01, N = 32 in the mixed forms: FP16 storage with a
+            reliable update every 10 iterations, and FP32 storage beside it."""
+            import hisq_inputs as hi
+            d3, n3, m3 = (48, 48, 48, 96), 32, 0.01
+            f3, l3 = hi.random_links_torch(d3, 1003, dev)
+            b3 = hi.gaussian_sources_torch(d3, n3, 2300, dev)
+            res = {"workload": "48x48x48x96 m=0.01 N=32 to 1e-10 (links seed 1003, sources seed "
+                               "2300)"}
+            for key, prec, kw in (("mixed_f16", "mixed_f16", {"ru_every": 10}),
+                                  ("mixed_f32", "mixed_f32", {})):
+                h3 = BlockCG(d3, f3, l3, m3, prec=prec, max_rhs=n3, max_iter=5000, profile=True,
+                             device=dev, **kw)
+                h3.tune(n3)
+                _, i3 = h3.solve(b3, tol=a.tol)
+                res[key] = {"ms_per_rhs": i3["ms_total"] / n3, "ms_per_solve": i3["ms_total"],
+                            "iters": i3["iters"], "reliable_updates": i3["reliable_updates"],
+                            "true_rel_res_max": i3["true_rel_res_max"],
+                            "converged": i3["status"] == 0 and i3["true_rel_res_max"] <= a.tol,
+                            "ms_breakdown": {k: i3[k] for k in ("ms_stencil", "ms_stencil_fine",
+                                                                "ms_gram", "ms_stream", "ms_dense")}}
+                del h3
+                free_cuda()
+            out["config_48x96"] = res
+            del f3, l3, b3
+            free_cuda()
+
+        def alu_leg():
+            from paper_1710_09745_gb300.binding import bench_alu
+            f32, f64, sms = bench_alu(stream)
+            out["alu_probe"] = {"fp32_fma_per_s": f32, "fp64_fma_per_s": f64, "sm_count": sms,
+                                "fp32_issue_frac_of_derived": f32 / (sms * FP32_LANES *
+                                                                     SM_MAX_MHZ * 1e6),
+                                "fp64_tflops": 2 * f64 / 1e12}
+
+        def cpu_leg():
+            # CPU oracle (rank 0, one GPU): one whole textbook-CG solve of source 0
+            # of the workload to tol on the host cores (the baseline, measured, not
+            # extrapolated), continued to 1e-12 for the solution error of every
+            # form's column 0 against the FP64 oracle
             os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
             from oracle import build as obuild
             obuild.build()
             from oracle import hisq as ohisq
+            import numpy as np
             fat_n, lng_n = fat_c.numpy(), lng_c.numpy()
-            sec_it, k = oracle_sample(dims, a.mass, fat_n, lng_n, b_np[0])
-            iters = ic["iters"] / N
             cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+            t0 = time.time()
+            x10, it10, rr10 = ohisq.cg(dims, fat_n, lng_n, a.mass, b_np[:1], tol=a.tol, max_iter=5000)
+            sec10 = time.time() - t0
+            t0 = time.time()
+            x12, it12, rr12 = ohisq.cg(dims, fat_n, lng_n, a.mass, b_np[:1], tol=1e-12, max_iter=5000,
+                                       x0=x10)
+            sec12 = time.time() - t0
+            ref = x12[0]
+            nref = np.linalg.norm(ref)
+            errs = {k: float(np.linalg.norm(v - ref) / nref) for k, v in col0.items()}
             t0 = time.time()
             ohisq.apply_A(dims, fat_n, lng_n, a.mass, b_np[:1])
             apply_ms = (time.time() - t0) * 1e3
@@ -587,20 +705,40 @@ def main():
             sec_it1, k1 = oracle_sample(dims, a.mass, fat_n, lng_n, b_np[0], budget_s=4.0)
             ohisq.set_threads(prev)
             out["cpu_baseline"] = {
-                "value": sec_it * iters * 1e3, "unit": UNIT, "cores": cores, "kind": "oracle",
-                "sample": f"{k} oracle textbook-CG iterations on 1 source of the workload "
-                          f"({sec_it * 1e3:.1f} ms each), extrapolated to {iters:.0f} iterations "
-                          f"(the GPU CG baseline's count to {a.tol:g})",
-                "one_core": {"value": sec_it1 * iters * 1e3, "unit": UNIT, "cores": 1,
-                             "sample": f"{k1} iterations ({sec_it1 * 1e3:.1f} ms each)"},
+                "value": sec10 * 1e3, "unit": UNIT, "cores": cores, "kind": "oracle",
+                "sample": f"one whole oracle textbook-CG solve of source 0 of the workload to "
+                          f"{a.tol:g} ({int(it10[0])} iterations, {sec10:.1f} s, true residual "
+                          f"{float(rr10[0]):.2e}) on {cores} host threads",
+                "one_core": {"value": sec_it1 * int(it10[0]) * 1e3, "unit": UNIT, "cores": 1,
+                             "sample": f"{k1} iterations ({sec_it1 * 1e3:.1f} ms each) x "
+                                       f"{int(it10[0])}"},
                 "apply_A_ms_per_rhs": apply_ms,
                 "full_solves": oracle_full_solves()}
+            out["oracle_error"] = {
+                "what": "|x_0 - x_0^oracle| / |x_0^oracle| for column 0 of each form's solution; "
+                        f"oracle = textbook CG in FP64 to 1e-12 ({int(it10[0] + it12[0])} iterations, "
+                        f"true residual {float(rr12[0]):.2e})",
+                "errors": errs,
+                "bound_note": "|e|/|x| <= kappa |r|/|b|, kappa = lambda_max / m^2 ~ 4.3e4 at "
+                              "m = 0.01: <= ~4e-6 at a 1e-10 residual, ~4e-8 at 1e-12"}
+
+        leg("cg", cg_leg)
+        leg("f64_native", f64_native_leg)
+        leg("mixed", mixed_legs)
+        leg("dslash", dslash_leg)
+        handles.clear()
+        free_cuda()
+        leg("width", width_leg)
+        leg("fine_tol", fine_tol_leg)
+        leg("config3", config3_leg)
+        leg("batched", lambda: out.__setitem__("batched", batched_leg(a.tol, dev)))
+        leg("autograd", lambda: out.__setitem__("autograd", autograd_leg(dev)))
+        leg("alu", alu_leg)
+        if world == 1:
+            leg("cpu", cpu_leg)
 
     if rank == 0 and not a.no_extras:
-        try:
-            extras()
-        except Exception as exc:  # keep the headline line
-            out["extras_error"] = f"{type(exc).__name__}: {exc}"
+        extras()
 
     if rank == 0:
         print(json.dumps(out))

@@ -270,6 +270,51 @@ blockcg_status blockcg_solve_cg(blockcg_t h, const void* B, void* X, int n_rhs, 
 blockcg_status blockcg_bench_dslash(blockcg_t h, int n_rhs, int fine, int reps,
                                     double* ms_per_launch);
 
+/* ---- Many right-hand sides: block width chosen by measurement ------------
+ *
+ * Sec. 7.1 solves 192 sources in blocks of N, and Sec. 7.2 finds that the
+ * best N depends on the problem and the machine ("bigger is not necessarily
+ * better": fewer iterations against costlier ones).  blockcg_solve_many
+ * solves m_rhs right-hand sides (any count >= 1) in consecutive blocks of
+ * `width` columns with blockcg_solve.  width = 0 picks the width itself:
+ * unless the tuning cache (below) already holds a choice for this lattice,
+ * precision form, mass, tolerance and device, it solves the first blocks at
+ * the candidate widths 8, 16 and 32 in turn (each a real solve of distinct
+ * right-hand sides, after tuning the stencil for that width, so no work is
+ * thrown away), takes the width with the least device time per right-hand
+ * side, solves the rest at that width and stores the choice in the cache.
+ * Candidates must fit the workspace (blockcg_workspace_bytes); with fewer
+ * than 8 right-hand sides all are solved in one block.
+ * B, X: device, user layout [m_rhs][Vh][3]; X holds the initial guesses on
+ * entry and the solutions on exit.  Synchronises the stream.
+ * Errors: as blockcg_solve (the first failing block's status; later blocks
+ * are not solved), ERR_ARG (width < 0 or > 64), ERR_NOMEM (width beyond the
+ * workspace). */
+typedef struct {
+  int width;                 /* width of the blocks after the exploration */
+  int from_cache;            /* 1: the width came from the tuning cache */
+  int blocks;                /* blocks solved */
+  long long iters_total;     /* Algorithm 1 iterations summed over blocks */
+  double ms_total;           /* device time of all block solves */
+  double true_rel_res_max;   /* max over all right-hand sides */
+  int n_candidates;          /* widths timed in the exploration (<= 8) */
+  int cand_width[8];
+  double cand_ms_per_rhs[8]; /* device time per right-hand side of each */
+  double* true_rel_res;      /* set by the caller: host array of m_rhs
+                                doubles for the per-RHS true residuals, or NULL */
+} blockcg_many_stats;
+
+blockcg_status blockcg_solve_many(blockcg_t h, const void* B, void* X, int m_rhs, double tol,
+                                  int width, blockcg_many_stats* st);
+
+/* Persist this handle's tuning choices (stencil kernel per storage kind and
+ * width, block width of blockcg_solve_many) in the text file `path` (a JSON
+ * object of "key": integer lines; created if absent, shared by handles and
+ * processes that name it; entries are keyed by lattice, kind, width and
+ * device name).  NULL or "" turns persistence off.  Choices already in the
+ * file are used instead of timing.  Errors: ERR_ARG (null handle). */
+blockcg_status blockcg_set_tune_cache(blockcg_t h, const char* path);
+
 /* Run the stencil autotuner for block width n_rhs now (the register-tile and
  * kernel choice of Sec. 6.2, each candidate timed on the normal operator's
  * pair of stencil launches), for the iteration's storage kind and for the
@@ -279,6 +324,18 @@ blockcg_status blockcg_bench_dslash(blockcg_t h, int n_rhs, int fine, int reps,
  * kernel.  Zeroes and uses the workspace's block fields.  Synchronises the
  * stream.  Errors: ERR_ARG, ERR_NOMEM, ERR_CUDA. */
 blockcg_status blockcg_tune(blockcg_t h, int n_rhs);
+
+/* Measured arithmetic issue rates of the current device, the denominators of
+ * the arithmetic roofline of the FP64-accurate form (whose double-float
+ * stencil of Sec. 6.2 is bound by FP32 instruction issue on GPUs with a
+ * reduced FP64 rate): long chains of independent fused multiply-adds on
+ * 8 blocks of 256 threads per SM, timed with CUDA events on `stream`
+ * (cudaStream_t, NULL = legacy default), in FP32 and in FP64.  Outputs
+ * (host): *fp32_fma_per_s and *fp64_fma_per_s multiply-adds per second,
+ * *sm_count the device's SM count.  Needs no handle; allocates nothing;
+ * synchronises the stream.  Errors: ERR_ARG (null output), ERR_CUDA. */
+blockcg_status blockcg_bench_alu(void* stream, double* fp32_fma_per_s, double* fp64_fma_per_s,
+                                 int* sm_count);
 
 /* K = X^dag Y, the same block inner product as blockcg_block_cdot, for
  * callers that cannot allocate device memory: code running inside a memory

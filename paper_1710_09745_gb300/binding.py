@@ -30,7 +30,8 @@ ABI_SYMBOLS = [
     "blockcg_solve_cg", "blockcg_bench_dslash", "blockcg_destroy", "blockcg_status_string",
     "blockcg_last_error", "blockcg_block_cdot_noalloc", "blockcg_batch_create",
     "blockcg_batch_solve", "blockcg_batch_destroy", "blockcg_batch_last_error",
-    "blockcg_link_grad", "blockcg_tune",
+    "blockcg_link_grad", "blockcg_tune", "blockcg_bench_alu", "blockcg_solve_many",
+    "blockcg_set_tune_cache",
 ]
 
 BATCH_GRAPH = 1
@@ -51,6 +52,14 @@ class Stats(ct.Structure):
                 ("ms_stencil_fine", ct.c_double), ("ms_gram", ct.c_double),
                 ("ms_stream", ct.c_double), ("ms_dense", ct.c_double),
                 ("stencil_variant", ct.c_int), ("true_rel_res", ct.POINTER(ct.c_double))]
+
+
+class ManyStats(ct.Structure):
+    _fields_ = [("width", ct.c_int), ("from_cache", ct.c_int), ("blocks", ct.c_int),
+                ("iters_total", ct.c_longlong), ("ms_total", ct.c_double),
+                ("true_rel_res_max", ct.c_double), ("n_candidates", ct.c_int),
+                ("cand_width", ct.c_int * 8), ("cand_ms_per_rhs", ct.c_double * 8),
+                ("true_rel_res", ct.POINTER(ct.c_double))]
 
 
 class BatchStats(ct.Structure):
@@ -103,6 +112,9 @@ def load_library(path: str = LIB_PATH):
         "blockcg_batch_destroy": (None, [P]),
         "blockcg_link_grad": (I, [P, P, P, I, P, P]),
         "blockcg_tune": (I, [P, I]),
+        "blockcg_bench_alu": (I, [P, ct.POINTER(D), ct.POINTER(D), ct.POINTER(I)]),
+        "blockcg_solve_many": (I, [P, P, P, I, D, I, ct.POINTER(ManyStats)]),
+        "blockcg_set_tune_cache": (I, [P, ct.c_char_p]),
         "blockcg_batch_last_error": (ct.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
@@ -322,6 +334,40 @@ class BlockCG:
         """N sequential CG solves (baseline); returns (X, info); out as in solve."""
         return self._solve(self.lib.blockcg_solve_cg, B, X0, tol, out)
 
+    def set_tune_cache(self, path):
+        """Persist tuning choices in `path` (blockcg_set_tune_cache); None turns it off."""
+        self._check(self.lib.blockcg_set_tune_cache(self.h, None if path is None
+                                                    else str(path).encode()))
+
+    def solve_many(self, B, X0=None, tol: float = 1e-10, width: int = 0, out=None):
+        """Solve m right-hand sides (B of shape (m, Vh, 3), any m >= 1) in blocks
+        of `width` columns; width = 0 picks the width by timing the first
+        blocks (blockcg_solve_many).  Returns (X, info)."""
+        torch = _torch()
+        B = self._block(B)
+        m = B.shape[0]
+        if out is not None:
+            if out.shape != B.shape or out.dtype != B.dtype or not out.is_contiguous():
+                raise ValueError("out must be a contiguous tensor like B")
+            if X0 is not None:
+                out.copy_(self._block(X0))
+            X = out
+        else:
+            X = torch.zeros_like(B) if X0 is None else self._block(X0).clone()
+        st = ManyStats()
+        per_rhs = (ct.c_double * m)()
+        st.true_rel_res = ct.cast(per_rhs, ct.POINTER(ct.c_double))
+        rc = self.lib.blockcg_solve_many(self.h, ct.c_void_p(B.data_ptr()), ct.c_void_p(X.data_ptr()),
+                                         m, float(tol), int(width), ct.byref(st))
+        info = {"status": rc, "width": st.width, "from_cache": st.from_cache, "blocks": st.blocks,
+                "iters_total": st.iters_total, "ms_total": st.ms_total,
+                "true_rel_res_max": st.true_rel_res_max, "true_rel_res": list(per_rhs),
+                "candidates": {st.cand_width[i]: st.cand_ms_per_rhs[i]
+                               for i in range(st.n_candidates)}}
+        if rc not in (0, 6):
+            self._check(rc)
+        return X, info
+
     def tune(self, n_rhs: int):
         """Run the stencil autotuner for block width n_rhs now (blockcg_tune)."""
         self._check(self.lib.blockcg_tune(self.h, int(n_rhs)))
@@ -332,6 +378,21 @@ class BlockCG:
         self._check(self.lib.blockcg_bench_dslash(self.h, int(n_rhs), int(bool(fine)), int(reps),
                                                   ct.byref(ms)))
         return ms.value
+
+
+def bench_alu(stream=None):
+    """Measured FP32 and FP64 multiply-adds per second of the current device
+    (blockcg_bench_alu); returns (fp32_per_s, fp64_per_s, sm_count)."""
+    torch = _torch()
+    L = load_library()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    f32, f64, sms = ct.c_double(), ct.c_double(), ct.c_int()
+    rc = L.blockcg_bench_alu(ct.c_void_p(stream.cuda_stream), ct.byref(f32), ct.byref(f64),
+                             ct.byref(sms))
+    if rc != 0:
+        raise BlockCGError(rc, "blockcg_bench_alu failed")
+    return f32.value, f64.value, sms.value
 
 
 class BlockCGBatch:

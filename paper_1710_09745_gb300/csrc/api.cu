@@ -19,11 +19,14 @@
 // The reliable update also serves as the convergence test: when the
 // iterated residual meets tol, the true residual of Y decides.
 #include <cuda_runtime.h>
+#include <unistd.h>
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -61,6 +64,8 @@ struct blockcg_ctx {
   double ms_st[5];
   // autotuned register tile of the stencil, keyed by kind * 128 + N
   std::map<int, int> tuned_R;
+  // persisted tuning cache (blockcg_set_tune_cache): file path and entries
+  std::string cache_path;
 };
 
 namespace {
@@ -223,6 +228,96 @@ void fill_stats(const blockcg_ctx* h, blockcg_stats* st) {
 
 int tile_R(int N) { return N >= 8 ? 4 : (N >= 2 ? 2 : 1); }
 
+// ---- persisted tuning cache --------------------------------------------
+// A JSON object with one "key": integer entry per line, shared by every
+// handle that names the same file; keys carry the lattice, storage kind or
+// precision form, width and the device name, so one file can serve several
+// problems and GPUs.  Reads and writes are serialised within the process and
+// a write replaces the file atomically (temporary file + rename).
+std::mutex g_cache_mutex;
+
+std::string device_tag() {
+  int dev = 0;
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return "unknown";
+  }
+  std::string n = prop.name;
+  for (char& c : n)
+    if (c == ' ' || c == '"' || c == '\\') c = '_';
+  return n;
+}
+
+std::map<std::string, long long> cache_read(const std::string& path) {
+  std::map<std::string, long long> m;
+  FILE* f = fopen(path.c_str(), "r");
+  if (!f) return m;
+  char line[1024];
+  while (fgets(line, sizeof(line), f)) {
+    const char* q0 = strchr(line, '"');
+    if (!q0) continue;
+    const char* q1 = strchr(q0 + 1, '"');
+    if (!q1) continue;
+    const char* colon = strchr(q1, ':');
+    if (!colon) continue;
+    char* end = nullptr;
+    long long v = strtoll(colon + 1, &end, 10);
+    if (end == colon + 1) continue;
+    m[std::string(q0 + 1, q1)] = v;
+  }
+  fclose(f);
+  return m;
+}
+
+bool cache_write(const std::string& path, const std::map<std::string, long long>& m) {
+  std::string tmp = path + ".tmp" + std::to_string((long long)getpid());
+  FILE* f = fopen(tmp.c_str(), "w");
+  if (!f) return false;
+  fprintf(f, "{\n");
+  size_t i = 0;
+  for (const auto& kv : m) {
+    fprintf(f, "  \"%s\": %lld%s\n", kv.first.c_str(), kv.second, ++i < m.size() ? "," : "");
+  }
+  fprintf(f, "}\n");
+  bool ok = fclose(f) == 0;
+  if (ok) ok = rename(tmp.c_str(), path.c_str()) == 0;
+  if (!ok) remove(tmp.c_str());
+  return ok;
+}
+
+// value of key in the handle's cache file (false when absent or no file)
+bool cache_get(const blockcg_ctx* h, const std::string& key, long long* v) {
+  if (h->cache_path.empty()) return false;
+  std::lock_guard<std::mutex> lock(g_cache_mutex);
+  auto m = cache_read(h->cache_path);
+  auto it = m.find(key);
+  if (it == m.end()) return false;
+  *v = it->second;
+  return true;
+}
+
+void cache_put(const blockcg_ctx* h, const std::string& key, long long v) {
+  if (h->cache_path.empty()) return;
+  std::lock_guard<std::mutex> lock(g_cache_mutex);
+  auto m = cache_read(h->cache_path);
+  m[key] = v;
+  cache_write(h->cache_path, m);
+}
+
+std::string dims_tag(const blockcg_ctx* h) {
+  char buf[64];
+  snprintf(buf, sizeof(buf), "%d.%d.%d.%d", h->dims[0], h->dims[1], h->dims[2], h->dims[3]);
+  return buf;
+}
+
+std::string stencil_key(const blockcg_ctx* h, FieldKind k, int N, int rf) {
+  char buf[160];
+  snprintf(buf, sizeof(buf), "stencil/%s/kind%d/N%d/recon%d/%s", dims_tag(h).c_str(), (int)k, N,
+           rf ? 1 : 0, device_tag().c_str());
+  return buf;
+}
+
 // Register tile of the stencil for (kind, N): tuned once per handle by timing
 // every candidate R on the handle's own buffers (the register-tile tuning of
 // Sec. 6.2); in is read, out is scratch.  Falls back to tile_R on any error.
@@ -244,6 +339,13 @@ int stencil_R(blockcg_ctx* h, FieldKind k, int N, const void* links, const void*
   const int key = (int)k * 128 + N;
   auto it = h->tuned_R.find(key);
   if (it != h->tuned_R.end()) return it->second;
+  {
+    long long v = 0;
+    if (cache_get(h, stencil_key(h, k, N, rf), &v)) {
+      h->tuned_R[key] = (int)v;
+      return (int)v;
+    }
+  }
   int best = tile_R(N) | rf;
   float best_ms = 1e30f;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -293,6 +395,7 @@ int stencil_R(blockcg_ctx* h, FieldKind k, int N, const void* links, const void*
   cudaEventDestroy(e1);
   cudaGetLastError();
   h->tuned_R[key] = best;
+  cache_put(h, stencil_key(h, k, N, rf), best);
   return best;
 }
 
@@ -886,6 +989,92 @@ blockcg_status blockcg_solve_cg(blockcg_t h, const void* B, void* X, int n_rhs, 
     stats->ms_total = ms;
     fill_stats(h, stats);
   }
+  return result;
+}
+
+blockcg_status blockcg_set_tune_cache(blockcg_t h, const char* path) {
+  if (!h) return BLOCKCG_ERR_ARG;
+  h->cache_path = path ? path : "";
+  return BLOCKCG_OK;
+}
+
+blockcg_status blockcg_solve_many(blockcg_t h, const void* B, void* X, int m_rhs, double tol,
+                                  int width, blockcg_many_stats* st) {
+  if (!h) return BLOCKCG_ERR_ARG;
+  if (!B || !X) return fail(h, BLOCKCG_ERR_ARG, "null pointer");
+  if (m_rhs < 1) return fail(h, BLOCKCG_ERR_ARG, "m_rhs must be >= 1");
+  if (width < 0 || width > 64) return fail(h, BLOCKCG_ERR_ARG, "width must be in [0, 64]");
+  if (!(tol > 0) || !std::isfinite(tol)) return fail(h, BLOCKCG_ERR_ARG, "tol must be > 0");
+  if (!h->ws) return fail(h, BLOCKCG_ERR_NOMEM, "no workspace set");
+  int maxw = 64;
+  while (maxw > 1 && carve(h, maxw, nullptr).total > h->ws_bytes) --maxw;
+  if (carve(h, 1, nullptr).total > h->ws_bytes) return fail(h, BLOCKCG_ERR_NOMEM, "workspace too small");
+  if (width > maxw) return fail(h, BLOCKCG_ERR_NOMEM, "width beyond the workspace");
+  blockcg_many_stats loc;
+  memset(&loc, 0, sizeof(loc));
+  if (st) loc.true_rel_res = st->true_rel_res;
+  const size_t col_bytes = (size_t)h->g.Vh * 3 * sizeof(double2);
+  int done = 0;
+  blockcg_status result = BLOCKCG_OK;
+  // one block of n columns starting at column done
+  auto solve_block = [&](int n, double* ms_out) -> blockcg_status {
+    blockcg_stats bs;
+    memset(&bs, 0, sizeof(bs));
+    bs.true_rel_res = loc.true_rel_res ? loc.true_rel_res + done : nullptr;
+    blockcg_status rc = blockcg_solve(h, (const char*)B + done * col_bytes,
+                                      (char*)X + done * col_bytes, n, tol, &bs);
+    loc.blocks += 1;
+    loc.iters_total += bs.iters;
+    loc.ms_total += bs.ms_total;
+    if (bs.true_rel_res_max > loc.true_rel_res_max || std::isnan(bs.true_rel_res_max))
+      loc.true_rel_res_max = bs.true_rel_res_max;
+    if (ms_out) *ms_out = bs.ms_total;
+    done += n;
+    return rc;
+  };
+  char keybuf[200];
+  snprintf(keybuf, sizeof(keybuf), "width/%s/prec%d/m=%.6g/tol=%.3g/ru%d/%s", dims_tag(h).c_str(),
+           (int)h->p.prec, h->mass, tol, h->p.ru_every, device_tag().c_str());
+  const std::string wkey = keybuf;
+  int chosen = width;
+  if (chosen == 0) {
+    long long v = 0;
+    if (cache_get(h, wkey, &v) && v >= 1 && v <= maxw) {
+      chosen = (int)v;
+      loc.from_cache = 1;
+    }
+  }
+  if (chosen == 0) {
+    // exploration: real solves of the first blocks at each candidate width
+    const int cands[3] = {8, 16, 32};
+    double best_ms = 0.0;
+    for (int w : cands) {
+      if (w > maxw || done + w > m_rhs || loc.n_candidates >= 8) continue;
+      blockcg_status rc = blockcg_tune(h, w);
+      if (rc) return rc;
+      double ms = 0.0;
+      rc = solve_block(w, &ms);
+      if (rc) {
+        result = rc;
+        break;
+      }
+      loc.cand_width[loc.n_candidates] = w;
+      loc.cand_ms_per_rhs[loc.n_candidates] = ms / w;
+      ++loc.n_candidates;
+      if (chosen == 0 || ms / w < best_ms) {
+        best_ms = ms / w;
+        chosen = w;
+      }
+    }
+    if (!result && chosen == 0) chosen = m_rhs < maxw ? m_rhs : maxw;  // fewer than 8 RHS
+    if (!result && loc.n_candidates >= 2) cache_put(h, wkey, chosen);
+  }
+  while (!result && done < m_rhs) {
+    const int n = (m_rhs - done) < chosen ? (m_rhs - done) : chosen;
+    result = solve_block(n, nullptr);
+  }
+  loc.width = chosen;
+  if (st) *st = loc;
   return result;
 }
 

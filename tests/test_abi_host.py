@@ -190,7 +190,8 @@ def _c_layout(struct, fields):
 
 
 @pytest.mark.parametrize("struct,cls", [("blockcg_params", "Params"), ("blockcg_stats", "Stats"),
-                                        ("blockcg_batch_stats", "BatchStats")])
+                                        ("blockcg_batch_stats", "BatchStats"),
+                                        ("blockcg_many_stats", "ManyStats")])
 def test_binding_structs_match_the_header_layout(struct, cls):
     """The ctypes mirrors of the ABI structs have the C compiler's field
     offsets and sizes, including the per-right-hand-side residual pointer of
@@ -220,3 +221,20 @@ def test_wait_limit_must_not_be_negative(lib):
     p.wait_limit_ns = 1000
     assert lib.blockcg_create(ct.byref(h), d, 0.1, ct.byref(p), None) == 0
     lib.blockcg_destroy(h)
+
+
+def test_solve_many_validates_without_gpu(lib):
+    h = ct.c_void_p()
+    d = (ct.c_int * 4)(4, 4, 4, 4)
+    assert lib.blockcg_solve_many(None, None, None, 1, 1e-10, 0, None) == 1
+    assert lib.blockcg_set_tune_cache(None, b"x") == 1
+    assert lib.blockcg_create(ct.byref(h), d, 0.1, None, None) == 0
+    try:
+        p = ct.c_void_p(16)
+        assert lib.blockcg_solve_many(h, p, p, 0, 1e-10, 0, None) == 1      # m_rhs < 1
+        assert lib.blockcg_solve_many(h, p, p, 4, 1e-10, 65, None) == 1     # width > 64
+        assert lib.blockcg_solve_many(h, p, p, 4, -1.0, 0, None) == 1       # tol
+        assert lib.blockcg_solve_many(h, p, p, 4, 1e-10, 0, None) == 3      # no workspace
+        assert lib.blockcg_set_tune_cache(h, None) == 0
+    finally:
+        lib.blockcg_destroy(h)

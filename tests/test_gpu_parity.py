@@ -431,8 +431,10 @@ def test_bulk_copy_wait_limit_reports_timeout_and_context_survives():
     s, fat, lng = gh.make_solver(dims, mass, seed=1022, max_rhs=4, dslash_variant=TMA + 2,
                                  wait_limit_ns=1)
     b = hi.gaussian_sources(dims, N, seed=2022)
-    _, info = s.solve(b, tol=1e-10)
-    assert info["status"] == 7
+    from paper_1710_09745_gb300 import BlockCGError
+    with pytest.raises(BlockCGError) as ei:
+        s.solve(b, tol=1e-10)
+    assert ei.value.status == 7
     s.close()
     s2, fat, lng = gh.make_solver(dims, mass, seed=1022, max_rhs=4, dslash_variant=TMA + 2)
     X, info2 = s2.solve(b, tol=1e-10)
@@ -450,3 +452,36 @@ def test_tune_then_solve_uses_the_tuned_kernel():
     X, info = s.solve(b, tol=1e-10)
     assert info["status"] == 0 and info["stencil_variant"] != 0
     assert _oracle_rel_res(dims, fat, lng, mass, b, gh.to_np(X)).max() <= 1e-10
+
+
+def test_solve_many_picks_width_and_persists_it(tmp_path):
+    """blockcg_solve_many with width 0 on 40 right-hand sides: the first
+    blocks are solved at the candidate widths 8 and 16 (32 no longer fits the
+    remaining 16), the rest at the faster one; every column meets the
+    tolerance on the oracle's residual; the choice is written to the cache
+    file, and a second handle naming the file reuses it without exploring."""
+    dims, mass, M = (8, 8, 8, 8), 0.05, 40
+    cache = tmp_path / "tune.json"
+    s, fat, lng = gh.make_solver(dims, mass, seed=1024, max_rhs=32)
+    s.set_tune_cache(cache)
+    b = hi.gaussian_sources(dims, M, seed=2024)
+    X, info = s.solve_many(b, tol=1e-10)
+    assert info["status"] == 0, info
+    assert sorted(info["candidates"]) == [8, 16]
+    assert info["width"] in (8, 16)
+    assert info["blocks"] == 2 + (16 + info["width"] - 1) // info["width"]
+    ref = _oracle_rel_res(dims, fat, lng, mass, b, gh.to_np(X))
+    assert ref.max() <= 1e-10
+    assert np.abs(np.array(info["true_rel_res"]) - ref).max() < 1e-13
+    text = cache.read_text()
+    assert '"width/8.8.8.8/' in text and '"stencil/8.8.8.8/' in text
+    s2, _, _ = gh.make_solver(dims, mass, seed=1024, max_rhs=32)
+    s2.set_tune_cache(cache)
+    X2, info2 = s2.solve_many(b[:24], tol=1e-10)
+    assert info2["status"] == 0 and info2["from_cache"] == 1
+    assert info2["width"] == info["width"] and info2["candidates"] == {}
+    assert _oracle_rel_res(dims, fat, lng, mass, b[:24], gh.to_np(X2)).max() <= 1e-10
+    # a fixed width needs no cache
+    X3, info3 = s.solve_many(b[:10], tol=1e-10, width=4)
+    assert info3["blocks"] == 3 and info3["width"] == 4
+    assert _oracle_rel_res(dims, fat, lng, mass, b[:10], gh.to_np(X3)).max() <= 1e-10
