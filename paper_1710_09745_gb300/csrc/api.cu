@@ -41,12 +41,15 @@ struct blockcg_ctx {
   double mass;
   blockcg_params p;
   cudaStream_t stream;
-  FieldKind fine;    // Y, B, R and the true-residual operator: native FP64
+  FieldKind fine;    // B and the final true-residual check: native FP64
+  FieldKind ru;      // Y, R and the operator of the reliable updates (Algorithm 3):
+                     // double-float, or native FP64 in the F64_NATIVE form
   FieldKind sloppy;  // P, Q, AP, T and the iteration's operator
   FieldKind upd;     // X, the iterated solution update between reliable updates
   void* gauge;
   size_t gauge_bytes;
   void* links_fine;
+  void* links_ru;
   void* links_sloppy;
   bool gauge_loaded;
   char* ws;
@@ -76,8 +79,9 @@ inline size_t up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 enum MatId { M_H = 0, M_G, M_C, M_CPREV, M_BETA, M_BC, M_SINV, M_SH, M_CINV, M_SHRU, M_K, M_RINV, M_COUNT };
 
 struct Ws {
-  // fine-kind fields
-  void *B, *Y, *R, *Tf;
+  // B: native FP64; Bru, Y, R, Tf: the reliable-update kind (Bru aliases B
+  // when that kind is FP64)
+  void *B, *Bru, *Y, *R, *Tf;
   // update-kind field
   void* X;
   // sloppy-kind fields
@@ -102,16 +106,18 @@ Ws carve(const blockcg_ctx* h, int N, char* base) {
     return p;
   };
   size_t nel = (size_t)h->g.Vh * N * 3;
-  size_t fb = nel * elem_bytes(h->fine), sb = nel * elem_bytes(h->sloppy);
+  size_t fb = nel * elem_bytes(h->fine), rb = nel * elem_bytes(h->ru),
+         sb = nel * elem_bytes(h->sloppy);
   w.B = take(fb);
-  w.Y = take(fb);
+  w.Bru = (h->ru == h->fine) ? w.B : take(rb);
+  w.Y = take(rb);
   w.X = take(nel * elem_bytes(h->upd));
-  w.R = take(fb);
-  w.Tf = take(fb);
+  w.R = take(rb);
+  w.Tf = take(rb);
   w.Q = take(sb);
   w.P = take(sb);
   w.AP = take(sb);
-  w.Ts = (h->sloppy == h->fine) ? w.Tf : take(sb);
+  w.Ts = (h->sloppy == h->ru) ? w.Tf : take(sb);
   w.nblocks = gram_blocks(N, 3 * h->g.Vh);
   int nb_cg = 2 * 152;
   size_t np = (size_t)(w.nblocks > nb_cg ? w.nblocks : nb_cg) * N * N;
@@ -324,7 +330,9 @@ std::string stencil_key(const blockcg_ctx* h, FieldKind k, int N, int rf) {
 // the stencil flag of a kind's links: two-row storage for the iteration's
 // links when params.link_recon is set (the FP64 links are always complete)
 int recon_flag(const blockcg_ctx* h, FieldKind k) {
-  return (h->p.link_recon && k == h->sloppy && h->sloppy != h->fine) ? DSLASH_RECON : 0;
+  return (h->p.link_recon && k == h->sloppy && h->sloppy != h->fine && h->sloppy != h->ru)
+             ? DSLASH_RECON
+             : 0;
 }
 
 // Autotuned stencil choice for (kind, N), cached.  Each candidate is timed
@@ -446,20 +454,47 @@ int default_check_every(const blockcg_ctx* h, int N) {
 }
 
 // R = B - A Y, thin QR, restart of Q and P (Algorithm 3; init: Algorithm 1 set-up)
+// (R = B - A Y in the reliable-update kind: double-float, or native FP64 in
+// the F64_NATIVE form; a convergence it reports is confirmed in native FP64
+// by verify_fp64 before the solve ends)
 blockcg_status restart_block(blockcg_ctx* h, const Ws& w, int N, double tol, int init, Gate gate) {
-  int R = cached_R(h, h->fine, N);
+  const FieldKind rk = h->ru;
+  int R = cached_R(h, rk, N);
   double m2 = h->mass * h->mass;
   size_t nel = (size_t)h->g.Vh * N * 3;
   cudaStream_t s = h->stream;
-  TL(TC_STREAM, accumulate(h->fine, h->upd, w.Y, w.X, nel, gate, s));
-  SL(1, dslash(h->fine, R, EPI_NONE, h->links_fine, w.Y, w.Tf, nullptr, nullptr, 0.0, h->g, 1, N, gate, s));
-  SL(1, dslash(h->fine, R, EPI_RESIDUAL, h->links_fine, w.Tf, w.R, w.Y, w.B, m2, h->g, 0, N, gate, s));
-  TL(TC_GRAM, gram_partials(h->fine, w.R, w.R, N, h->g.Vh, 1, w.partials, w.nblocks, gate, s));
+  TL(TC_STREAM, accumulate(rk, h->upd, w.Y, w.X, nel, gate, s));
+  SL(1, dslash(rk, R, EPI_NONE, h->links_ru, w.Y, w.Tf, nullptr, nullptr, 0.0, h->g, 1, N, gate, s));
+  SL(1, dslash(rk, R, EPI_RESIDUAL, h->links_ru, w.Tf, w.R, w.Y, w.Bru, m2, h->g, 0, N, gate, s));
+  TL(TC_GRAM, gram_partials(rk, w.R, w.R, N, h->g.Vh, 1, w.partials, w.nblocks, gate, s));
   TL(TC_GRAM, gram_reduce(w.partials, w.nblocks, N, 1, mat(w, M_G, N), gate, s));
   TL(TC_DENSE, dense_restart(mat(w, M_G, N), mat(w, M_C, N), mat(w, M_CPREV, N), mat(w, M_CINV, N),
                    mat(w, M_SHRU, N), w.bnorm, w.tres, tol, init, N, w.st, gate, s));
-  TL(TC_STREAM, restart_update(h->fine, h->sloppy, w.R, w.Q, w.P, mat(w, M_CINV, N), mat(w, M_SHRU, N), init,
+  TL(TC_STREAM, restart_update(rk, h->sloppy, w.R, w.Q, w.P, mat(w, M_CINV, N), mat(w, M_SHRU, N), init,
                     N, h->g.Vh, gate, s));
+  return BLOCKCG_OK;
+}
+
+// The true residual of the current Y in native FP64: Y (reliable-update kind)
+// converted exactly to FP64, R = B - A Y with the FP64 links and the original
+// FP64 B, per-column norms against tol.  Confirms a convergence that a
+// double-float reliable update reported (done stays set, verified = 1), or
+// clears done and tightens the double-float threshold tenfold so that the
+// iteration goes on (dense_verify).  Buffers: R holds Y in FP64, Tf the odd
+// half, X the residual (X is zero at this point and zeroed again after).
+blockcg_status verify_fp64(blockcg_ctx* h, const Ws& w, int N, double tol) {
+  const int R = cached_R(h, FK_F64, N);
+  const double m2 = h->mass * h->mass;
+  const size_t nel = (size_t)h->g.Vh * N * 3;
+  cudaStream_t s = h->stream;
+  Gate g0{nullptr, GATE_ALWAYS};
+  TL(TC_STREAM, convert_field(h->ru, FK_F64, w.Y, w.R, nel, nullptr, g0, s));
+  SL(1, dslash(FK_F64, R, EPI_NONE, h->links_fine, w.R, w.Tf, nullptr, nullptr, 0.0, h->g, 1, N, g0, s));
+  SL(1, dslash(FK_F64, R, EPI_RESIDUAL, h->links_fine, w.Tf, w.X, w.R, w.B, m2, h->g, 0, N, g0, s));
+  TL(TC_GRAM, gram_partials(FK_F64, w.X, w.X, N, h->g.Vh, 1, w.partials, w.nblocks, g0, s));
+  TL(TC_GRAM, gram_reduce(w.partials, w.nblocks, N, 1, mat(w, M_K, N), g0, s));
+  TL(TC_DENSE, dense_verify(mat(w, M_K, N), w.bnorm, w.tres, tol, N, w.st, s));
+  CK(zero_field(h->upd, w.X, nel, s));
   return BLOCKCG_OK;
 }
 
@@ -508,7 +543,7 @@ blockcg_status check_solve_args(blockcg_ctx* h, const void* B, const void* X, in
 // first iteration and the next reliable update rewrite them)
 void tune_block(blockcg_ctx* h, const Ws& w, int N) {
   stencil_R(h, h->sloppy, N, h->links_sloppy, w.P, w.Ts, w.AP);
-  stencil_R(h, h->fine, N, h->links_fine, w.Y, w.Tf, w.R);
+  stencil_R(h, h->ru, N, h->links_ru, w.Y, w.Tf, w.R);
 }
 
 // Algorithm 1 set-up: B and X in internal layout, |b_i|, X = 0 (update),
@@ -522,7 +557,8 @@ blockcg_status solve_begin(blockcg_ctx* h, const Ws& w, const void* B, const voi
   CK(cudaMemsetAsync(w.st, 0, sizeof(SolverStatus), s));
   CK(cudaMemsetAsync(w.tres, 0xff, N * sizeof(double), s));  // NaN until a true residual exists
   KL(to_internal(h->fine, (const double2*)B, w.B, N, h->g.Vh, s));
-  KL(to_internal(h->fine, (const double2*)X, w.Y, N, h->g.Vh, s));
+  if (w.Bru != w.B) KL(to_internal(h->ru, (const double2*)B, w.Bru, N, h->g.Vh, s));
+  KL(to_internal(h->ru, (const double2*)X, w.Y, N, h->g.Vh, s));
   CK(zero_field(h->upd, w.X, nel, s));
   CK(zero_field(h->sloppy, w.P, nel, s));
   KL(gram_partials(h->fine, w.B, w.B, N, h->g.Vh, 1, w.partials, w.nblocks, g0, s));
@@ -531,20 +567,59 @@ blockcg_status solve_begin(blockcg_ctx* h, const Ws& w, const void* B, const voi
   return restart_block(h, w, N, tol, 1, ga);
 }
 
+// a convergence the solve may report: done in the reliable-update kind and,
+// unless that kind is FP64, confirmed by the native-FP64 true residual
+bool converged(const blockcg_ctx* h, const SolverStatus& hs) {
+  return hs.done && (h->ru == FK_F64 || hs.verified);
+}
+
+// Host-driven iteration from the current device state: enqueue chunks of
+// gated iterations and poll the status word between them; a convergence
+// reported by a double-float reliable update is checked in native FP64
+// (verify_fp64), and if that check fails the iteration goes on.  Returns
+// with *hs the last status (converged, error, or the iteration budget spent).
+blockcg_status host_loop(blockcg_ctx* h, const Ws& w, int N, double tol, SolverStatus* hs) {
+  const int chunk = default_check_every(h, N);
+  for (;;) {
+    blockcg_status rc = read_status(h, w, hs);
+    if (rc) return rc;
+    if (hs->error || converged(h, *hs)) return BLOCKCG_OK;
+    if (hs->done) {
+      rc = verify_fp64(h, w, N, tol);
+      if (rc) return rc;
+      continue;
+    }
+    if (hs->iters >= h->p.max_iter || hs->stopped) return BLOCKCG_OK;
+    int n = chunk;
+    if (hs->iters + n > h->p.max_iter) n = h->p.max_iter - hs->iters;
+    if (n <= 0) n = 1;
+    for (int i = 0; i < n; ++i) {
+      rc = iterate_block(h, w, N, tol);
+      if (rc) return rc;
+    }
+  }
+}
+
 // after the iterations: at max_iter fold the last update into Y and take the
-// true residual; write Y to the caller's X.  *result = the solve's outcome.
+// true residual (in native FP64); write Y to the caller's X.  *result = the
+// solve's outcome.
 blockcg_status solve_end(blockcg_ctx* h, const Ws& w, void* X, int N, double tol,
                          SolverStatus* hs, blockcg_status* result) {
   Gate g0{nullptr, GATE_ALWAYS};
   *result = status_to_result(h, *hs);
-  if (!*result && !hs->done) {
-    blockcg_status rc = restart_block(h, w, N, tol, 1, g0);
+  if (!*result && !converged(h, *hs)) {
+    blockcg_status rc = BLOCKCG_OK;
+    if (!hs->done) rc = restart_block(h, w, N, tol, 1, g0);
+    if (rc) return rc;
+    if (h->ru != FK_F64) rc = verify_fp64(h, w, N, tol);
     if (rc) return rc;
     rc = read_status(h, w, hs);
     if (rc) return rc;
-    *result = hs->done ? BLOCKCG_OK : fail(h, BLOCKCG_ERR_NOT_CONVERGED, "max_iter reached");
+    *result = status_to_result(h, *hs);
+    if (!*result && !converged(h, *hs))
+      *result = fail(h, BLOCKCG_ERR_NOT_CONVERGED, "max_iter reached");
   }
-  KL(from_internal(h->fine, w.Y, (double2*)X, N, h->g.Vh, h->stream));
+  KL(from_internal(h->ru, w.Y, (double2*)X, N, h->g.Vh, h->stream));
   return BLOCKCG_OK;
 }
 
@@ -631,6 +706,7 @@ blockcg_status blockcg_create(blockcg_t* out, const int dims[4], double mass,
     case BLOCKCG_PREC_MIXED_F16: h->sloppy = FK_H16; h->upd = FK_DF; break;
     case BLOCKCG_PREC_MIXED_BF16: h->sloppy = FK_BF16; h->upd = FK_DF; break;
   }
+  h->ru = (prm.prec == BLOCKCG_PREC_F64_NATIVE) ? FK_F64 : FK_DF;
   // with 16-bit storage the sloppy recursion can stagnate (bfloat16's 8-bit
   // significand) or drift (FP16 on ill-conditioned problems) before the
   // residual falls by ru_delta; a periodic reliable update keeps it on track
@@ -639,7 +715,7 @@ blockcg_status blockcg_create(blockcg_t* out, const int dims[4], double mass,
     h->p.ru_every = 10;
   h->gauge = nullptr;
   h->gauge_bytes = 0;
-  h->links_fine = h->links_sloppy = nullptr;
+  h->links_fine = h->links_ru = h->links_sloppy = nullptr;
   h->gauge_loaded = false;
   h->ws = nullptr;
   h->ws_bytes = 0;
@@ -662,6 +738,7 @@ size_t blockcg_gauge_bytes(blockcg_t h) {
   if (!h) return 0;
   size_t b = up(links_bytes(h->fine, h->g));
   if (h->sloppy != h->fine) b += up(links_bytes(h->sloppy, h->g, h->p.link_recon));
+  if (h->ru != h->fine && h->ru != h->sloppy) b += up(links_bytes(h->ru, h->g));
   if (h->p.link_recon) b += ALIGN;  // scratch of the link check
   return b;
 }
@@ -695,13 +772,24 @@ blockcg_status blockcg_load_gauge(blockcg_t h, const void* fat, const void* lng,
   }
   h->gauge = storage;
   h->gauge_bytes = storage_bytes;
+  // [FP64 links][iteration links, if another kind][reliable-update links, if
+  // a third kind]
+  char* next = (char*)storage + up(links_bytes(h->fine, h->g));
   h->links_fine = storage;
-  h->links_sloppy = (h->sloppy != h->fine) ? (char*)storage + up(links_bytes(h->fine, h->g)) : storage;
+  h->links_sloppy = storage;
+  if (h->sloppy != h->fine) {
+    h->links_sloppy = next;
+    next += up(links_bytes(h->sloppy, h->g, recon));
+  }
+  h->links_ru = (h->ru == h->fine) ? h->links_fine : (h->ru == h->sloppy) ? h->links_sloppy : next;
   CK(pack_links(h->fine, (const double2*)fat, (const double2*)lng, h->links_fine, h->g,
                 h->p.antiperiodic_t, 0, h->stream));
   if (h->sloppy != h->fine)
     CK(pack_links(h->sloppy, (const double2*)fat, (const double2*)lng, h->links_sloppy, h->g,
                   h->p.antiperiodic_t, recon, h->stream));
+  if (h->links_ru != h->links_fine && h->links_ru != h->links_sloppy)
+    CK(pack_links(h->ru, (const double2*)fat, (const double2*)lng, h->links_ru, h->g,
+                  h->p.antiperiodic_t, 0, h->stream));
   h->gauge_loaded = true;
   return BLOCKCG_OK;
 }
@@ -832,23 +920,10 @@ blockcg_status blockcg_solve(blockcg_t h, const void* B, void* X, int n_rhs, dou
   rc = solve_begin(h, w, B, X, N, tol);
   if (rc) return rc;
   tune_block(h, w, N);
-  const int chunk = default_check_every(h, N);
   SolverStatus hs;
   memset(&hs, 0, sizeof(hs));
-  int launched = 0;
-  for (;;) {
-    rc = read_status(h, w, &hs);
-    if (rc) return rc;
-    if (hs.done || hs.error || hs.iters >= h->p.max_iter) break;
-    int n = chunk;
-    if (launched + n > h->p.max_iter) n = h->p.max_iter - launched;
-    if (n <= 0) n = 1;
-    for (int i = 0; i < n; ++i) {
-      rc = iterate_block(h, w, N, tol);
-      if (rc) return rc;
-    }
-    launched += n;
-  }
+  rc = host_loop(h, w, N, tol, &hs);
+  if (rc) return rc;
   blockcg_status result = BLOCKCG_OK;
   rc = solve_end(h, w, X, N, tol, &hs, &result);
   if (rc) return rc;
@@ -1478,7 +1553,26 @@ blockcg_status blockcg_batch_solve(blockcg_batch_t b, const void* const* B, void
       }
     }
   }
-  // results: max_iter handling and the copy-out, each problem on its stream
+  // native-FP64 confirmation of every convergence a double-float reliable
+  // update reported: enqueued for all such problems, then one wait
+  bool verifying = false;
+  for (int p = 0; p < n; ++p) {
+    blockcg_ctx* h = b->probs[p];
+    const SolverStatus& hs = b->host_st[p];
+    if (hs.error || !hs.done || converged(h, hs)) continue;
+    Ws w = carve(h, N[p], h->ws);
+    long long l0 = h->launches;
+    blockcg_status rc = verify_fp64(h, w, N[p], tol);
+    if (rc) return pfail(b, p, rc);
+    launches += h->launches - l0;
+    BK(cudaMemcpyAsync(&b->host_st[p], w.st, sizeof(SolverStatus), cudaMemcpyDeviceToHost,
+                       b->streams[p]));
+    verifying = true;
+  }
+  if (verifying)
+    for (int p = 0; p < n; ++p) BK(cudaStreamSynchronize(b->streams[p]));
+  // results: a failed confirmation continues on the host (rare), max_iter
+  // handling and the copy-out, each problem on its stream
   blockcg_status first = BLOCKCG_OK;
   for (int p = 0; p < n; ++p) {
     blockcg_ctx* h = b->probs[p];
@@ -1486,6 +1580,10 @@ blockcg_status blockcg_batch_solve(blockcg_batch_t b, const void* const* B, void
     SolverStatus hs = b->host_st[p];
     blockcg_status result = BLOCKCG_OK;
     long long l0 = h->launches;
+    if (!hs.error && !converged(h, hs) && hs.iters < h->p.max_iter && !hs.stopped) {
+      blockcg_status rc = host_loop(h, w, N[p], tol, &hs);
+      if (rc) return pfail(b, p, rc);
+    }
     blockcg_status rc = solve_end(h, w, X[p], N[p], tol, &hs, &result);
     if (rc) return pfail(b, p, rc);
     launches += h->launches - l0;

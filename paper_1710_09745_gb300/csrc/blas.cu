@@ -826,6 +826,14 @@ cudaError_t restart_update(FieldKind rk, FieldKind sk, const void* R, void* Q, v
     return launch_restart<StoreF64, StoreH16>(R, Q, P, Cinv, SH, init, N, Vh, gate, s);
   if (rk == FK_F64 && sk == FK_BF16)
     return launch_restart<StoreF64, StoreBF16>(R, Q, P, Cinv, SH, init, N, Vh, gate, s);
+  if (rk == FK_DF && sk == FK_DF)
+    return launch_restart<StoreDF, StoreDF>(R, Q, P, Cinv, SH, init, N, Vh, gate, s);
+  if (rk == FK_DF && sk == FK_F32)
+    return launch_restart<StoreDF, StoreF32>(R, Q, P, Cinv, SH, init, N, Vh, gate, s);
+  if (rk == FK_DF && sk == FK_H16)
+    return launch_restart<StoreDF, StoreH16>(R, Q, P, Cinv, SH, init, N, Vh, gate, s);
+  if (rk == FK_DF && sk == FK_BF16)
+    return launch_restart<StoreDF, StoreBF16>(R, Q, P, Cinv, SH, init, N, Vh, gate, s);
   return cudaErrorInvalidValue;
 }
 
@@ -889,6 +897,8 @@ cudaError_t convert_field(FieldKind from, FieldKind to, const void* in, void* ou
     k_convert<StoreBF16, StoreF64><<<gcap(n, 256), 256, 0, s>>>((const double2*)in, (__nv_bfloat162*)out, n, scale, gate);
   else if (from == FK_F64 && to == FK_F64)
     k_convert<StoreF64, StoreF64><<<gcap(n, 256), 256, 0, s>>>((const double2*)in, (double2*)out, n, scale, gate);
+  else if (from == FK_DF && to == FK_F64)
+    k_convert<StoreF64, StoreDF><<<gcap(n, 256), 256, 0, s>>>((const float4*)in, (double2*)out, n, scale, gate);
   else if (from == to && !scale)
     return cudaMemcpyAsync(out, in, n * elem_bytes(to), cudaMemcpyDeviceToDevice, s);
   else

@@ -224,8 +224,9 @@ __global__ void __launch_bounds__(DENSE_THREADS)
     st->iters = it;
     st->res_max = rmax;
     int ru = 0;
-    if (!(rmax <= p.tol) && !isfinite(rmax)) st->error = BLOCKCG_ERR_NONFINITE;
-    if (rmax <= p.tol) ru = 1;
+    const double tol = shifted_tol(p.tol, st->tol_shift);
+    if (!(rmax <= tol) && !isfinite(rmax)) st->error = BLOCKCG_ERR_NONFINITE;
+    if (rmax <= tol) ru = 1;
     else if (p.delta > 0.0 && rmax < p.delta * st->res_at_ru) ru = 1;
     else if (p.ru_every > 0 && (it % p.ru_every) == 0) ru = 1;
     // the iterated residual has grown far above the last true one: the
@@ -304,9 +305,49 @@ __global__ void __launch_bounds__(DENSE_THREADS)
     st->res_max = tmax;
     st->res_at_ru = tmax;
     if (!isfinite(tmax)) st->error = BLOCKCG_ERR_NONFINITE;
-    if (tmax <= tol) st->done = 1;
+    if (tmax <= shifted_tol(tol, st->tol_shift)) st->done = 1;
     if (!init) st->reliable_updates += 1;
   }
+}
+
+// Native-FP64 confirmation of a convergence (see verify_fp64 in api.cu): G is
+// the Gram of R = B - A Y computed in FP64; the per-column true residuals
+// replace those of the double-float update.  All within tol: verified.
+// Otherwise the solve goes on with a double-float threshold ten times
+// tighter, so that the next convergence it reports leaves room for the
+// difference between the two residuals.
+__global__ void k_dense_verify(const double2* __restrict__ G, const double* __restrict__ bnorm,
+                               double* __restrict__ tres, double tol, int N, SolverStatus* st) {
+  __shared__ double r[64];
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    r[i] = sqrt(fmax(G[i * N + i].x, 0.0)) / bnorm[i];
+    tres[i] = r[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tmax = 0.0;
+    bool finite = true;
+    for (int i = 0; i < N; ++i) {
+      tmax = fmax(tmax, r[i]);
+      finite = finite && isfinite(r[i]);
+    }
+    st->true_res_max = tmax;
+    if (!finite) {
+      st->error = BLOCKCG_ERR_NONFINITE;
+    } else if (tmax <= tol) {
+      st->verified = 1;
+    } else {
+      st->done = 0;
+      st->verified = 0;
+      st->tol_shift += 1;
+    }
+  }
+}
+
+cudaError_t dense_verify(const double2* G, const double* bnorm, double* tres, double tol, int N,
+                         SolverStatus* st, cudaStream_t s) {
+  k_dense_verify<<<1, 64, 0, s>>>(G, bnorm, tres, tol, N, st);
+  return cudaGetLastError();
 }
 
 cudaError_t dense_restart(const double2* G, double2* C, double2* C_prev, double2* Cinv,

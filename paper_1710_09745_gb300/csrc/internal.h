@@ -140,6 +140,11 @@ cudaError_t dense_qr_step(const double2* G, double2* C, double2* C_prev, double2
 cudaError_t dense_restart(const double2* G, double2* C, double2* C_prev, double2* Cinv,
                           double2* SH, const double* bnorm, double* tres, double tol, int init,
                           int N, SolverStatus* st, Gate gate, cudaStream_t s);
+// native-FP64 confirmation of a convergence: true residuals from the FP64
+// Gram G of R = B - A Y into tres; verified, or done cleared and the
+// double-float threshold tightened
+cudaError_t dense_verify(const double2* G, const double* bnorm, double* tres, double tol, int N,
+                         SolverStatus* st, cudaStream_t s);
 // bnorm_i = sqrt(Gb_ii); error if any is zero or not finite
 cudaError_t dense_bnorm(const double2* Gb, double* bnorm, int N, SolverStatus* st,
                         cudaStream_t s);
