@@ -67,7 +67,7 @@ def parse_args():
                     help="only the differentiable-solve leg (16^4, N = 8)")
     ap.add_argument("--legs", nargs="*", default=None,
                     help="run only these context legs (cg f64_native mixed dslash width "
-                         "fine_tol config3 batched autograd alu cpu)")
+                         "fine_tol config3 batched autograd cpu)")
     return ap.parse_args()
 
 
@@ -413,6 +413,9 @@ def main():
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
 
+    # measured FP32 / FP64 multiply-add rates of this GPU (the double-float roofline's basis)
+    from paper_1710_09745_gb300.binding import bench_alu
+    alu_f32, alu_f64, alu_sms = bench_alu(stream)
     for _ in range(a.warmup):
         X, info = s.solve(B, tol=a.tol)
     barrier()
@@ -449,13 +452,25 @@ def main():
         # tuned double-float stencil (k_dslash_async<StoreDF, 2, 1, 0, 3>), 2.0x the
         # algorithmic bytes; only that workload and kernel version
         full = tuple(dims) == (32, 32, 32, 32) and N == 16
+        measured_peak = alu_f32 / DF_INSTR_PER_FLOP / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": 4.04e9 if full else None,
                 "traffic_note": "ncu DRAM read+write of one k_dslash_async<StoreDF,2,1,0,3> "
-                                "launch at 32^4 N=16 (algorithmic 2.013e9)" if full else None,
+                                "launch at 32^4 N=16 (algorithmic 2.013e9; "
+                                "profiles/k_dslash_df_traffic_32x4_N16.md)" if full else None,
                 "kernel": "k_dslash<StoreDF> (double-float stencil)",
                 "peak_note": "FP32 issue rate 152 SM x 128 lanes x 2070 MHz / 6 instr per "
-                             "FP64-equivalent flop (double-float); derived, not measured",
+                             "FP64-equivalent flop (double-float: 12 FP32 instructions per "
+                             "multiply-add); derived from unit counts and the maximum clock",
+                "peak_measured": measured_peak,
+                "frac_of_measured": achieved / measured_peak,
+                "alu_probe": {"fp32_fma_per_s": alu_f32, "fp64_fma_per_s": alu_f64,
+                              "sm_count": alu_sms,
+                              "note": "blockcg_bench_alu in this run (FMA chains, 8 blocks of "
+                                      "256 threads per SM); profiles/alu_issue_rates.md"},
+                "ncu": {"profile": "profiles/k_dslash_df_24x4_N16.md (24^4, N = 16, same kernel)",
+                        "issue_slots_active": 0.809, "fma_pipe_active": 0.681,
+                        "dram_throughput": 0.195, "achieved_occupancy": 0.287},
                 "hbm_view": {"achieved_gbs": alg_bytes / (avg_launch_ms * 1e-3) / 1e9,
                              "peak_gbs": hbm_peak,
                              "frac": alg_bytes / (avg_launch_ms * 1e-3) / 1e9 / hbm_peak},
@@ -668,14 +683,6 @@ def main():
             del f3, l3, b3
             free_cuda()
 
-        def alu_leg():
-            from paper_1710_09745_gb300.binding import bench_alu
-            f32, f64, sms = bench_alu(stream)
-            out["alu_probe"] = {"fp32_fma_per_s": f32, "fp64_fma_per_s": f64, "sm_count": sms,
-                                "fp32_issue_frac_of_derived": f32 / (sms * FP32_LANES *
-                                                                     SM_MAX_MHZ * 1e6),
-                                "fp64_tflops": 2 * f64 / 1e12}
-
         def cpu_leg():
             # CPU oracle (rank 0, one GPU): one whole textbook-CG solve of source 0
             # of the workload to tol on the host cores (the baseline, measured, not
@@ -733,7 +740,6 @@ def main():
         leg("config3", config3_leg)
         leg("batched", lambda: out.__setitem__("batched", batched_leg(a.tol, dev)))
         leg("autograd", lambda: out.__setitem__("autograd", autograd_leg(dev)))
-        leg("alu", alu_leg)
         if world == 1:
             leg("cpu", cpu_leg)
 

@@ -9,15 +9,17 @@
 //   AP = m^2 P - D_eo T                stencil + epilogue (Sec. 3.2)
 //   H  = P^dag AP                      Gram               (Sec. 6.4)
 //   beta = H^-1, BC = beta C           dense              (Algorithm 1)
-//   W  = Q - AP beta                   streaming          (Sec. 6.3)
-//   W^dag W = S^dag S, C = S C, res    Gram + dense       (Algorithm 2)
+//   W  = Q - AP beta and W^dag W       streaming + Gram in one pass (6.3, 6.4)
+//   W^dag W = S^dag S, C = S C, res    dense              (Algorithm 2)
 //   Q = W S^-1, X += P BC, P = Q + P S^dag       one fused streaming pass
 //   [reliable update, gated]           Algorithm 3:
 //      Y += X, X = 0; R = B - A Y; R = Q C (thin QR); S = C C_old^-1;
 //      P = Q + P S^dag
 //
 // The reliable update also serves as the convergence test: when the
-// iterated residual meets tol, the true residual of Y decides.
+// iterated residual meets tol, the true residual of Y decides.  Updates run
+// in double-float (native FP64 in the F64_NATIVE form); a convergence they
+// report is confirmed once in native FP64 before the solve ends.
 #include <cuda_runtime.h>
 #include <unistd.h>
 
@@ -41,9 +43,9 @@ struct blockcg_ctx {
   double mass;
   blockcg_params p;
   cudaStream_t stream;
-  FieldKind fine;    // B and the final true-residual check: native FP64
-  FieldKind ru;      // Y, R and the operator of the reliable updates (Algorithm 3):
-                     // double-float, or native FP64 in the F64_NATIVE form
+  FieldKind fine;    // Y, B, R and the true-residual operator: native FP64
+  FieldKind ru;      // a cheaper kind for the early reliable updates (Algorithm 3)
+                     // of a single solve: double-float, or FP64 (= fine: none)
   FieldKind sloppy;  // P, Q, AP, T and the iteration's operator
   FieldKind upd;     // X, the iterated solution update between reliable updates
   void* gauge;
@@ -79,9 +81,9 @@ inline size_t up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 enum MatId { M_H = 0, M_G, M_C, M_CPREV, M_BETA, M_BC, M_SINV, M_SH, M_CINV, M_SHRU, M_K, M_RINV, M_COUNT };
 
 struct Ws {
-  // B: native FP64; Bru, Y, R, Tf: the reliable-update kind (Bru aliases B
-  // when that kind is FP64)
-  void *B, *Bru, *Y, *R, *Tf;
+  // fine-kind fields (native FP64); Bru, Yru, Rru: copies in the kind of the
+  // early reliable updates (alias B, Y, R when that kind is FP64)
+  void *B, *Y, *R, *Tf, *Bru, *Yru, *Rru;
   // update-kind field
   void* X;
   // sloppy-kind fields
@@ -109,15 +111,18 @@ Ws carve(const blockcg_ctx* h, int N, char* base) {
   size_t fb = nel * elem_bytes(h->fine), rb = nel * elem_bytes(h->ru),
          sb = nel * elem_bytes(h->sloppy);
   w.B = take(fb);
-  w.Bru = (h->ru == h->fine) ? w.B : take(rb);
-  w.Y = take(rb);
+  w.Y = take(fb);
   w.X = take(nel * elem_bytes(h->upd));
-  w.R = take(rb);
-  w.Tf = take(rb);
+  w.R = take(fb);
+  w.Tf = take(fb);  // odd-site temporary of both reliable-update kinds (16-byte elements)
+  const bool cheap = h->ru != h->fine;
+  w.Bru = cheap ? take(rb) : w.B;
+  w.Yru = cheap ? take(rb) : w.Y;
+  w.Rru = cheap ? take(rb) : w.R;
   w.Q = take(sb);
   w.P = take(sb);
   w.AP = take(sb);
-  w.Ts = (h->sloppy == h->ru) ? w.Tf : take(sb);
+  w.Ts = (h->sloppy == h->fine) ? w.Tf : take(sb);
   w.nblocks = gram_blocks(N, 3 * h->g.Vh);
   int nb_cg = 2 * 152;
   size_t np = (size_t)(w.nblocks > nb_cg ? w.nblocks : nb_cg) * N * N;
@@ -454,51 +459,53 @@ int default_check_every(const blockcg_ctx* h, int N) {
 }
 
 // R = B - A Y, thin QR, restart of Q and P (Algorithm 3; init: Algorithm 1 set-up)
-// (R = B - A Y in the reliable-update kind: double-float, or native FP64 in
-// the F64_NATIVE form; a convergence it reports is confirmed in native FP64
-// by verify_fp64 before the solve ends)
-blockcg_status restart_block(blockcg_ctx* h, const Ws& w, int N, double tol, int init, Gate gate) {
-  const FieldKind rk = h->ru;
+// cheap = true: the residual R = B - A Y of the restart in the early-update
+// kind (double-float, from a rounded copy of Y; accurate to ~2^-48 |A| |Y|,
+// far below residuals well above tol); otherwise in native FP64, and a
+// convergence it reports is confirmed.  Y itself is always FP64.
+blockcg_status restart_block(blockcg_ctx* h, const Ws& w, int N, double tol, int init, Gate gate,
+                             bool cheap = false) {
+  const FieldKind rk = cheap ? h->ru : h->fine;
+  const void* links = cheap ? h->links_ru : h->links_fine;
+  void* Yk = cheap ? w.Yru : w.Y;
+  void* Rk = cheap ? w.Rru : w.R;
+  void* Bk = cheap ? w.Bru : w.B;
   int R = cached_R(h, rk, N);
   double m2 = h->mass * h->mass;
   size_t nel = (size_t)h->g.Vh * N * 3;
   cudaStream_t s = h->stream;
-  TL(TC_STREAM, accumulate(rk, h->upd, w.Y, w.X, nel, gate, s));
-  SL(1, dslash(rk, R, EPI_NONE, h->links_ru, w.Y, w.Tf, nullptr, nullptr, 0.0, h->g, 1, N, gate, s));
-  SL(1, dslash(rk, R, EPI_RESIDUAL, h->links_ru, w.Tf, w.R, w.Y, w.Bru, m2, h->g, 0, N, gate, s));
-  TL(TC_GRAM, gram_partials(rk, w.R, w.R, N, h->g.Vh, 1, w.partials, w.nblocks, gate, s));
+  TL(TC_STREAM, accumulate(h->fine, h->upd, w.Y, w.X, nel, gate, s));
+  if (cheap) TL(TC_STREAM, convert_field(h->fine, rk, w.Y, Yk, nel, nullptr, gate, s));
+  SL(1, dslash(rk, R, EPI_NONE, links, Yk, w.Tf, nullptr, nullptr, 0.0, h->g, 1, N, gate, s));
+  SL(1, dslash(rk, R, EPI_RESIDUAL, links, w.Tf, Rk, Yk, Bk, m2, h->g, 0, N, gate, s));
+  TL(TC_GRAM, gram_partials(rk, Rk, Rk, N, h->g.Vh, 1, w.partials, w.nblocks, gate, s));
   TL(TC_GRAM, gram_reduce(w.partials, w.nblocks, N, 1, mat(w, M_G, N), gate, s));
   TL(TC_DENSE, dense_restart(mat(w, M_G, N), mat(w, M_C, N), mat(w, M_CPREV, N), mat(w, M_CINV, N),
-                   mat(w, M_SHRU, N), w.bnorm, w.tres, tol, init, N, w.st, gate, s));
-  TL(TC_STREAM, restart_update(rk, h->sloppy, w.R, w.Q, w.P, mat(w, M_CINV, N), mat(w, M_SHRU, N), init,
+                   mat(w, M_SHRU, N), w.bnorm, w.tres, tol, init, cheap ? 0 : 1, N, w.st, gate, s));
+  TL(TC_STREAM, restart_update(rk, h->sloppy, Rk, w.Q, w.P, mat(w, M_CINV, N), mat(w, M_SHRU, N), init,
                     N, h->g.Vh, gate, s));
   return BLOCKCG_OK;
 }
 
-// The true residual of the current Y in native FP64: Y (reliable-update kind)
-// converted exactly to FP64, R = B - A Y with the FP64 links and the original
-// FP64 B, per-column norms against tol.  Confirms a convergence that a
-// double-float reliable update reported (done stays set, verified = 1), or
-// clears done and tightens the double-float threshold tenfold so that the
-// iteration goes on (dense_verify).  Buffers: R holds Y in FP64, Tf the odd
-// half, X the residual (X is zero at this point and zeroed again after).
+// The true residual of the current Y in native FP64 (R = B - A Y with the
+// FP64 links and B), per-column norms against tol.  Confirms a convergence
+// that a double-float reliable update reported (done stays set, verified =
+// 1), or clears done and sets fp64_only, after which the solve's reliable
+// updates are all native FP64 (dense_verify).  Buffers: Tf (odd half) and R.
 blockcg_status verify_fp64(blockcg_ctx* h, const Ws& w, int N, double tol) {
   const int R = cached_R(h, FK_F64, N);
   const double m2 = h->mass * h->mass;
-  const size_t nel = (size_t)h->g.Vh * N * 3;
   cudaStream_t s = h->stream;
   Gate g0{nullptr, GATE_ALWAYS};
-  TL(TC_STREAM, convert_field(h->ru, FK_F64, w.Y, w.R, nel, nullptr, g0, s));
-  SL(1, dslash(FK_F64, R, EPI_NONE, h->links_fine, w.R, w.Tf, nullptr, nullptr, 0.0, h->g, 1, N, g0, s));
-  SL(1, dslash(FK_F64, R, EPI_RESIDUAL, h->links_fine, w.Tf, w.X, w.R, w.B, m2, h->g, 0, N, g0, s));
-  TL(TC_GRAM, gram_partials(FK_F64, w.X, w.X, N, h->g.Vh, 1, w.partials, w.nblocks, g0, s));
+  SL(1, dslash(FK_F64, R, EPI_NONE, h->links_fine, w.Y, w.Tf, nullptr, nullptr, 0.0, h->g, 1, N, g0, s));
+  SL(1, dslash(FK_F64, R, EPI_RESIDUAL, h->links_fine, w.Tf, w.R, w.Y, w.B, m2, h->g, 0, N, g0, s));
+  TL(TC_GRAM, gram_partials(FK_F64, w.R, w.R, N, h->g.Vh, 1, w.partials, w.nblocks, g0, s));
   TL(TC_GRAM, gram_reduce(w.partials, w.nblocks, N, 1, mat(w, M_K, N), g0, s));
   TL(TC_DENSE, dense_verify(mat(w, M_K, N), w.bnorm, w.tres, tol, N, w.st, s));
-  CK(zero_field(h->upd, w.X, nel, s));
   return BLOCKCG_OK;
 }
 
-blockcg_status iterate_block(blockcg_ctx* h, const Ws& w, int N, double tol) {
+blockcg_status iterate_block(blockcg_ctx* h, const Ws& w, int N, double tol, bool cheap_ru = false) {
   Gate ga{w.st, GATE_ACTIVE};
   Gate gr{w.st, GATE_RU};
   int R = cached_R(h, h->sloppy, N);
@@ -510,15 +517,16 @@ blockcg_status iterate_block(blockcg_ctx* h, const Ws& w, int N, double tol) {
   TL(TC_GRAM, gram_partials(k, w.P, w.AP, N, h->g.Vh, 1, w.partials, w.nblocks, ga, s));
   TL(TC_GRAM, gram_reduce(w.partials, w.nblocks, N, 1, mat(w, M_H, N), ga, s));
   TL(TC_DENSE, dense_beta(mat(w, M_H, N), mat(w, M_C, N), mat(w, M_BETA, N), mat(w, M_BC, N), N, w.st, ga, s));
-  TL(TC_STREAM, w_update(k, w.Q, w.AP, mat(w, M_BETA, N), N, h->g.Vh, ga, s));
-  TL(TC_GRAM, gram_partials(k, w.Q, w.Q, N, h->g.Vh, 1, w.partials, w.nblocks, ga, s));
+  // W = Q - AP beta (over Q) with the partials of W^dag W in the same pass
+  TL(TC_STREAM, w_update_gram(k, w.Q, w.AP, mat(w, M_BETA, N), N, h->g.Vh, w.partials, w.nblocks,
+                              ga, s));
   TL(TC_GRAM, gram_reduce(w.partials, w.nblocks, N, 1, mat(w, M_G, N), ga, s));
   QrStepParams qp{tol, h->p.ru_delta, h->p.ru_every, h->p.max_iter};
   TL(TC_DENSE, dense_qr_step(mat(w, M_G, N), mat(w, M_C, N), mat(w, M_CPREV, N), mat(w, M_SINV, N),
                    mat(w, M_SH, N), w.bnorm, qp, N, w.st, ga, s));
   TL(TC_STREAM, bcg_update(k, h->upd, w.Q, w.P, w.X, mat(w, M_SINV, N), mat(w, M_BC, N), mat(w, M_SH, N), N,
                 h->g.Vh, ga, s));
-  return restart_block(h, w, N, tol, 0, gr);
+  return restart_block(h, w, N, tol, 0, gr, cheap_ru);
 }
 
 blockcg_status status_to_result(blockcg_ctx* h, const SolverStatus& st) {
@@ -543,7 +551,8 @@ blockcg_status check_solve_args(blockcg_ctx* h, const void* B, const void* X, in
 // first iteration and the next reliable update rewrite them)
 void tune_block(blockcg_ctx* h, const Ws& w, int N) {
   stencil_R(h, h->sloppy, N, h->links_sloppy, w.P, w.Ts, w.AP);
-  stencil_R(h, h->ru, N, h->links_ru, w.Y, w.Tf, w.R);
+  stencil_R(h, h->fine, N, h->links_fine, w.Y, w.Tf, w.R);
+  if (h->ru != h->fine) stencil_R(h, h->ru, N, h->links_ru, w.Yru, w.Tf, w.Rru);
 }
 
 // Algorithm 1 set-up: B and X in internal layout, |b_i|, X = 0 (update),
@@ -558,7 +567,7 @@ blockcg_status solve_begin(blockcg_ctx* h, const Ws& w, const void* B, const voi
   CK(cudaMemsetAsync(w.tres, 0xff, N * sizeof(double), s));  // NaN until a true residual exists
   KL(to_internal(h->fine, (const double2*)B, w.B, N, h->g.Vh, s));
   if (w.Bru != w.B) KL(to_internal(h->ru, (const double2*)B, w.Bru, N, h->g.Vh, s));
-  KL(to_internal(h->ru, (const double2*)X, w.Y, N, h->g.Vh, s));
+  KL(to_internal(h->fine, (const double2*)X, w.Y, N, h->g.Vh, s));
   CK(zero_field(h->upd, w.X, nel, s));
   CK(zero_field(h->sloppy, w.P, nel, s));
   KL(gram_partials(h->fine, w.B, w.B, N, h->g.Vh, 1, w.partials, w.nblocks, g0, s));
@@ -567,11 +576,17 @@ blockcg_status solve_begin(blockcg_ctx* h, const Ws& w, const void* B, const voi
   return restart_block(h, w, N, tol, 1, ga);
 }
 
-// a convergence the solve may report: done in the reliable-update kind and,
-// unless that kind is FP64, confirmed by the native-FP64 true residual
+// a convergence the solve may report: reported by a native-FP64 reliable
+// update, or by a double-float one and confirmed in native FP64
 bool converged(const blockcg_ctx* h, const SolverStatus& hs) {
-  return hs.done && (h->ru == FK_F64 || hs.verified);
+  (void)h;
+  return hs.done && hs.verified;
 }
+
+// early reliable updates in the cheap kind while the last iterated residual
+// (as the host last read it) is above this factor times tol, and no FP64
+// confirmation has failed
+static constexpr double CHEAP_RU_ABOVE = 100.0;
 
 // Host-driven iteration from the current device state: enqueue chunks of
 // gated iterations and poll the status word between them; a convergence
@@ -593,8 +608,9 @@ blockcg_status host_loop(blockcg_ctx* h, const Ws& w, int N, double tol, SolverS
     int n = chunk;
     if (hs->iters + n > h->p.max_iter) n = h->p.max_iter - hs->iters;
     if (n <= 0) n = 1;
+    const bool cheap = h->ru != h->fine && !hs->fp64_only && hs->res_max > CHEAP_RU_ABOVE * tol;
     for (int i = 0; i < n; ++i) {
-      rc = iterate_block(h, w, N, tol);
+      rc = iterate_block(h, w, N, tol, cheap);
       if (rc) return rc;
     }
   }
@@ -608,10 +624,7 @@ blockcg_status solve_end(blockcg_ctx* h, const Ws& w, void* X, int N, double tol
   Gate g0{nullptr, GATE_ALWAYS};
   *result = status_to_result(h, *hs);
   if (!*result && !converged(h, *hs)) {
-    blockcg_status rc = BLOCKCG_OK;
-    if (!hs->done) rc = restart_block(h, w, N, tol, 1, g0);
-    if (rc) return rc;
-    if (h->ru != FK_F64) rc = verify_fp64(h, w, N, tol);
+    blockcg_status rc = hs->done ? verify_fp64(h, w, N, tol) : restart_block(h, w, N, tol, 1, g0);
     if (rc) return rc;
     rc = read_status(h, w, hs);
     if (rc) return rc;
@@ -619,7 +632,7 @@ blockcg_status solve_end(blockcg_ctx* h, const Ws& w, void* X, int N, double tol
     if (!*result && !converged(h, *hs))
       *result = fail(h, BLOCKCG_ERR_NOT_CONVERGED, "max_iter reached");
   }
-  KL(from_internal(h->ru, w.Y, (double2*)X, N, h->g.Vh, h->stream));
+  KL(from_internal(h->fine, w.Y, (double2*)X, N, h->g.Vh, h->stream));
   return BLOCKCG_OK;
 }
 
@@ -677,7 +690,8 @@ blockcg_status blockcg_create(blockcg_t* out, const int dims[4], double mass,
       prm.check_every < 0 || (int)prm.prec < 0 || (int)prm.prec > 4)
     return BLOCKCG_ERR_ARG;
   {
-    int r = prm.dslash_variant & ~(DSLASH_TMA | DSLASH_ASYNC);
+    int r = prm.dslash_variant & ~(DSLASH_TMA | DSLASH_ASYNC | DSLASH_RUNS);
+    if ((prm.dslash_variant & DSLASH_RUNS) && !(prm.dslash_variant & DSLASH_TMA)) return BLOCKCG_ERR_ARG;
     if (prm.dslash_variant != 0 && r != 1 && r != 2 && r != 4 && r != 8) return BLOCKCG_ERR_ARG;
   }
   if (prm.link_recon != 0 && prm.link_recon != 12) return BLOCKCG_ERR_ARG;

@@ -330,6 +330,164 @@ cudaError_t gram_reduce(const double2* partials, int nblocks, int N, int hermiti
   return cudaGetLastError();
 }
 
+// ------------------------------------------ W = Q - AP beta with W^dag W ----
+// The streaming W update of Algorithm 1 (Sec. 6.3) and the reduction that
+// follows it (the Gram W^dag W of the thin QR, Algorithm 2; Sec. 6.4) in one
+// pass: a CTA stages a tile of TS sites of Q and AP in shared memory, forms
+// W = Q - AP beta there (each entry by the one thread that writes it back
+// over Q), stores W, and accumulates the tile's Hermitian Gram from the
+// staged W with the register blocking of k_gram; the per-CTA partials go to
+// the same fixed-order reduction.  W is read from HBM once fewer than with a
+// separate Gram pass.
+template <class S, int B>
+__global__ void __launch_bounds__(GRAM_THREADS)
+    k_w_gram(typename S::elem* __restrict__ Q, const typename S::elem* __restrict__ AP,
+             const double2* __restrict__ beta, int N, int Vh, int TS,
+             double2* __restrict__ partials, Gate gate) {
+  using C = typename S::comp;
+  using real = typename C::real;
+  using acc = typename C::acc;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (gate_closed(gate)) return;
+  cpx<real>* sW = reinterpret_cast<cpx<real>*>(smem_raw);  // Q, then W
+  cpx<real>* sA = sW + TS * N * 3;                           // AP
+  cpx<real>* sb = sA + TS * N * 3;                           // beta [N][N]
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < N * N; idx += GRAM_THREADS) {
+    const double2 v = beta[idx];
+    sb[idx] = {C::from_double(v.x), C::from_double(v.y)};
+  }
+  const int nb = (N + B - 1) / B;
+  const int NB = nb * (nb + 1) / 2;
+  const int G = NB >= GRAM_THREADS ? 1 : GRAM_THREADS / NB;
+  const int grp = tid / NB;
+  const int blk = tid - grp * NB;
+  const bool active = grp < G && blk < NB;
+  int bi = 0, bj = 0;
+  {
+    int r = 0, off = 0;
+    while (off + (nb - r) <= blk) {
+      off += nb - r;
+      ++r;
+    }
+    bi = r;
+    bj = r + (blk - off);
+  }
+  const int i0 = bi * B, j0 = bj * B;
+  cpx<acc> a[B][B];
+#pragma unroll
+  for (int u = 0; u < B; ++u)
+#pragma unroll
+    for (int v = 0; v < B; ++v) a[u][v] = czero<C>();
+
+  for (long long tile = blockIdx.x; tile * TS < Vh; tile += gridDim.x) {
+    const long long site0 = tile * TS;
+    const int ns = (int)min((long long)TS, (long long)Vh - site0);
+    const int nel = ns * N * 3;
+    const long long base = site0 * N * 3;
+    __syncthreads();
+    for (int idx = tid; idx < nel; idx += GRAM_THREADS) {
+      sW[idx] = S::load_nc(Q + base + idx);
+      sA[idx] = S::load(AP + base + idx);
+    }
+    __syncthreads();
+    for (int idx = tid; idx < nel; idx += GRAM_THREADS) {
+      const int row = idx / N, j = idx - row * N;
+      const cpx<real>* apr = sA + row * N;
+      cpx<acc> w = cacc_from<C>(sW[idx]);
+      for (int i = 0; i < N; ++i) {
+        const cpx<real> ap = apr[i];
+        const cpx<real> bb = sb[i * N + j];
+        // w -= ap * bb
+        C::msub(w.re, ap.re, bb.re);
+        C::mac(w.re, ap.im, bb.im);
+        C::msub(w.im, ap.re, bb.im);
+        C::msub(w.im, ap.im, bb.re);
+      }
+      typename S::elem e;
+      S::store(&e, cfin<C>(w));
+      Q[base + idx] = e;
+      // the value as stored (rounded to the storage format) feeds the Gram
+      sW[idx] = S::load_nc(&e);
+    }
+    __syncthreads();
+    if (active) {
+      for (int r = grp; r < ns * 3; r += G) {
+        const cpx<real>* wr = sW + r * N;
+        cpx<real> xv[B], yv[B];
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+          xv[u] = (i0 + u < N) ? wr[i0 + u] : cpx<real>{C::rzero(), C::rzero()};
+          yv[u] = (j0 + u < N) ? wr[j0 + u] : cpx<real>{C::rzero(), C::rzero()};
+        }
+#pragma unroll
+        for (int u = 0; u < B; ++u)
+#pragma unroll
+          for (int v = 0; v < B; ++v) cmac_conj<C>(a[u][v], xv[u], yv[v]);
+      }
+    }
+  }
+  __syncthreads();
+  double2* red = reinterpret_cast<double2*>(smem_raw);
+  double2* out = partials + (long long)blockIdx.x * N * N;
+#pragma unroll
+  for (int u = 0; u < B; ++u)
+#pragma unroll
+    for (int v = 0; v < B; ++v) {
+      red[tid] = active ? make_double2(C::to_double(a[u][v].re), C::to_double(a[u][v].im))
+                        : make_double2(0.0, 0.0);
+      __syncthreads();
+      if (tid < NB) {
+        double2 sacc = red[tid];
+        for (int g2 = 1; g2 < G; ++g2) {
+          double2 w = red[g2 * NB + tid];
+          sacc.x += w.x;
+          sacc.y += w.y;
+        }
+        if (i0 + u < N && j0 + v < N) out[(i0 + u) * N + (j0 + v)] = sacc;
+      }
+      __syncthreads();
+    }
+}
+
+template <class S, int B>
+static void launch_w_gram_b(void* Q, const void* AP, const double2* beta, int N, int Vh,
+                            double2* partials, int nblocks, Gate gate, cudaStream_t s) {
+  using real = typename S::comp::real;
+  int TS = 256 / N;
+  if (TS < 1) TS = 1;
+  const size_t tiles = (2 * (size_t)TS * N * 3 + (size_t)N * N) * sizeof(cpx<real>);
+  const size_t red = GRAM_THREADS * sizeof(double2);
+  const size_t sm = tiles > red ? tiles : red;
+  cudaFuncSetAttribute(k_w_gram<S, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_w_gram<S, B><<<nblocks, GRAM_THREADS, sm, s>>>((typename S::elem*)Q,
+                                                  (const typename S::elem*)AP, beta, N, Vh, TS,
+                                                  partials, gate);
+}
+
+template <class S>
+static void launch_w_gram(void* Q, const void* AP, const double2* beta, int N, int Vh,
+                          double2* partials, int nblocks, Gate gate, cudaStream_t s) {
+  if (N == 1)
+    launch_w_gram_b<S, 1>(Q, AP, beta, N, Vh, partials, nblocks, gate, s);
+  else if (N <= 16)
+    launch_w_gram_b<S, 2>(Q, AP, beta, N, Vh, partials, nblocks, gate, s);
+  else
+    launch_w_gram_b<S, 4>(Q, AP, beta, N, Vh, partials, nblocks, gate, s);
+}
+
+cudaError_t w_update_gram(FieldKind k, void* Q, const void* AP, const double2* beta, int N, int Vh,
+                          double2* partials, int nblocks, Gate gate, cudaStream_t s) {
+  switch (k) {
+    case FK_DF: launch_w_gram<StoreDF>(Q, AP, beta, N, Vh, partials, nblocks, gate, s); break;
+    case FK_F32: launch_w_gram<StoreF32>(Q, AP, beta, N, Vh, partials, nblocks, gate, s); break;
+    case FK_F64: launch_w_gram<StoreF64>(Q, AP, beta, N, Vh, partials, nblocks, gate, s); break;
+    case FK_H16: launch_w_gram<StoreH16>(Q, AP, beta, N, Vh, partials, nblocks, gate, s); break;
+    case FK_BF16: launch_w_gram<StoreBF16>(Q, AP, beta, N, Vh, partials, nblocks, gate, s); break;
+  }
+  return cudaGetLastError();
+}
+
 // -------------------------------------------------- coefficient stage ----
 template <class C>
 __device__ __forceinline__ void stage_coef(cpx<typename C::real>* dst, const double2* __restrict__ M,
@@ -339,90 +497,6 @@ __device__ __forceinline__ void stage_coef(cpx<typename C::real>* dst, const dou
     double2 v = M[i * N + j0 + jj];
     dst[i * JT + jj] = {C::from_double(v.x), C::from_double(v.y)};
   }
-}
-
-// ---------------------------------------------------- W = Q - AP beta ----
-// thread = (row, group of WJB consecutive columns): each AP value read feeds
-// WJB outputs; beta staged once per CTA in shared memory
-static constexpr int WJB = 4;
-template <class S>
-__global__ void __launch_bounds__(256)
-    k_w_update(typename S::elem* __restrict__ Q, const typename S::elem* __restrict__ AP,
-               const double2* __restrict__ beta, int N, int Vh, Gate gate) {
-  using C = typename S::comp;
-  using real = typename C::real;
-  using acc = typename C::acc;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cpx<real>* sb = reinterpret_cast<cpx<real>*>(smem_raw);
-  if (gate_closed(gate)) return;
-  stage_coef<C>(sb, beta, N, 0, N, N);
-  __syncthreads();
-  const int ng = (N + WJB - 1) / WJB;
-  const long long total = (long long)Vh * 3 * ng;  // (row, column group)
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const long long row = idx / ng;
-    const int j0 = (int)(idx - row * ng) * WJB;
-    const typename S::elem* apr = AP + row * N;
-    typename S::elem* qr = Q + row * N;
-    cpx<acc> w[WJB];
-#pragma unroll
-    for (int u = 0; u < WJB; ++u)
-      w[u] = (j0 + u < N) ? cacc_from<C>(S::load_nc(qr + j0 + u)) : czero<C>();
-    for (int i = 0; i < N; ++i) {
-      const cpx<real> ap = S::load(apr + i);
-#pragma unroll
-      for (int u = 0; u < WJB; ++u) {
-        if (j0 + u < N) {
-          const cpx<real> bb = sb[i * N + j0 + u];
-          // w -= ap * bb
-          C::msub(w[u].re, ap.re, bb.re);
-          C::mac(w[u].re, ap.im, bb.im);
-          C::msub(w[u].im, ap.re, bb.im);
-          C::msub(w[u].im, ap.im, bb.re);
-        }
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < WJB; ++u)
-      if (j0 + u < N) S::store(qr + j0 + u, cfin<C>(w[u]));
-  }
-}
-
-cudaError_t w_update(FieldKind k, void* Q, const void* AP, const double2* beta, int N, int Vh,
-                     Gate gate, cudaStream_t s) {
-  long long total = (long long)Vh * 3 * ((N + WJB - 1) / WJB);
-  int th = 256;
-  switch (k) {
-    case FK_DF: {
-      size_t sm = (size_t)N * N * sizeof(cpx<df>);
-      cudaFuncSetAttribute(k_w_update<StoreDF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      k_w_update<StoreDF><<<gcap(total, th, 152 * 8), th, sm, s>>>((float4*)Q, (const float4*)AP, beta, N, Vh, gate);
-      break;
-    }
-    case FK_F32: {
-      size_t sm = (size_t)N * N * sizeof(cpx<float>);
-      k_w_update<StoreF32><<<gcap(total, th, 152 * 8), th, sm, s>>>((float2*)Q, (const float2*)AP, beta, N, Vh, gate);
-      break;
-    }
-    case FK_H16: {
-      size_t sm = (size_t)N * N * sizeof(cpx<float>);
-      k_w_update<StoreH16><<<gcap(total, th, 152 * 8), th, sm, s>>>((__half2*)Q, (const __half2*)AP, beta, N, Vh, gate);
-      break;
-    }
-    case FK_BF16: {
-      size_t sm = (size_t)N * N * sizeof(cpx<float>);
-      k_w_update<StoreBF16><<<gcap(total, th, 152 * 8), th, sm, s>>>((__nv_bfloat162*)Q, (const __nv_bfloat162*)AP, beta, N, Vh, gate);
-      break;
-    }
-    case FK_F64: {
-      size_t sm = (size_t)N * N * sizeof(cpx<double>);
-      cudaFuncSetAttribute(k_w_update<StoreF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      k_w_update<StoreF64><<<gcap(total, th, 152 * 8), th, sm, s>>>((double2*)Q, (const double2*)AP, beta, N, Vh, gate);
-      break;
-    }
-  }
-  return cudaGetLastError();
 }
 
 // ------------------------------------------------------ fused update ----

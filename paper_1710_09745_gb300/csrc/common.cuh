@@ -399,15 +399,9 @@ struct SolverStatus {
   double res_max;      // max relative iterated residual after the last iteration
   double res_at_ru;    // max relative residual at the last reliable update
   double true_res_max; // max relative true residual at the last check
-  int verified;        // 1: the native-FP64 true residual confirmed done
-  int tol_shift;       // failed FP64 confirmations so far: the double-float
-                       // convergence threshold is tol * 10^-tol_shift
+  int verified;        // 1: done rests on a native-FP64 true residual
+  int fp64_only;       // 1: a double-float convergence failed its FP64
+                       // confirmation; all later reliable updates are FP64
 };
-
-// the convergence threshold of the iterated and double-float residuals
-__host__ __device__ inline double shifted_tol(double tol, int shift) {
-  for (int k = 0; k < shift; ++k) tol *= 0.1;
-  return tol;
-}
 
 }  // namespace bcg

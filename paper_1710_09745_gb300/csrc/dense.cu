@@ -224,9 +224,8 @@ __global__ void __launch_bounds__(DENSE_THREADS)
     st->iters = it;
     st->res_max = rmax;
     int ru = 0;
-    const double tol = shifted_tol(p.tol, st->tol_shift);
-    if (!(rmax <= tol) && !isfinite(rmax)) st->error = BLOCKCG_ERR_NONFINITE;
-    if (rmax <= tol) ru = 1;
+    if (!(rmax <= p.tol) && !isfinite(rmax)) st->error = BLOCKCG_ERR_NONFINITE;
+    if (rmax <= p.tol) ru = 1;
     else if (p.delta > 0.0 && rmax < p.delta * st->res_at_ru) ru = 1;
     else if (p.ru_every > 0 && (it % p.ru_every) == 0) ru = 1;
     // the iterated residual has grown far above the last true one: the
@@ -252,8 +251,8 @@ __global__ void __launch_bounds__(DENSE_THREADS)
     k_dense_restart(const double2* __restrict__ G, double2* __restrict__ C,
                     double2* __restrict__ C_prev, double2* __restrict__ Cinv,
                     double2* __restrict__ SH, const double* __restrict__ bnorm,
-                    double* __restrict__ tres_out, double tol, int init, int N, SolverStatus* st,
-                    int gmode) {
+                    double* __restrict__ tres_out, double tol, int init, int confirmed, int N,
+                    SolverStatus* st, int gmode) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int flag;
   __shared__ double tres[64];
@@ -305,7 +304,10 @@ __global__ void __launch_bounds__(DENSE_THREADS)
     st->res_max = tmax;
     st->res_at_ru = tmax;
     if (!isfinite(tmax)) st->error = BLOCKCG_ERR_NONFINITE;
-    if (tmax <= shifted_tol(tol, st->tol_shift)) st->done = 1;
+    if (tmax <= tol) {
+      st->done = 1;
+      if (confirmed) st->verified = 1;
+    }
     if (!init) st->reliable_updates += 1;
   }
 }
@@ -313,9 +315,7 @@ __global__ void __launch_bounds__(DENSE_THREADS)
 // Native-FP64 confirmation of a convergence (see verify_fp64 in api.cu): G is
 // the Gram of R = B - A Y computed in FP64; the per-column true residuals
 // replace those of the double-float update.  All within tol: verified.
-// Otherwise the solve goes on with a double-float threshold ten times
-// tighter, so that the next convergence it reports leaves room for the
-// difference between the two residuals.
+// Otherwise the solve goes on and all its later reliable updates are FP64.
 __global__ void k_dense_verify(const double2* __restrict__ G, const double* __restrict__ bnorm,
                                double* __restrict__ tres, double tol, int N, SolverStatus* st) {
   __shared__ double r[64];
@@ -339,7 +339,7 @@ __global__ void k_dense_verify(const double2* __restrict__ G, const double* __re
     } else {
       st->done = 0;
       st->verified = 0;
-      st->tol_shift += 1;
+      st->fp64_only = 1;
     }
   }
 }
@@ -352,11 +352,11 @@ cudaError_t dense_verify(const double2* G, const double* bnorm, double* tres, do
 
 cudaError_t dense_restart(const double2* G, double2* C, double2* C_prev, double2* Cinv,
                           double2* SH, const double* bnorm, double* tres, double tol, int init,
-                          int N, SolverStatus* st, Gate gate, cudaStream_t s) {
+                          int confirmed, int N, SolverStatus* st, Gate gate, cudaStream_t s) {
   size_t sm = 3ull * N * N * sizeof(double2);
   cudaFuncSetAttribute(k_dense_restart, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_dense_restart<<<1, DENSE_THREADS, sm, s>>>(G, C, C_prev, Cinv, SH, bnorm, tres, tol, init, N,
-                                               st, gate.mode);
+  k_dense_restart<<<1, DENSE_THREADS, sm, s>>>(G, C, C_prev, Cinv, SH, bnorm, tres, tol, init,
+                                               confirmed, N, st, gate.mode);
   return cudaGetLastError();
 }
 

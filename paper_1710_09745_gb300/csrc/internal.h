@@ -62,6 +62,9 @@ static constexpr int DSLASH_ASYNC = 0x200;
 // R | DSLASH_RECON: links packed as two rows (pack_links recon); plain kernel
 // only, FP32 / FP16 / bfloat16 kinds
 static constexpr int DSLASH_RECON = 0x400;
+// R | DSLASH_TMA | DSLASH_RUNS: the bulk-copy kernel copies contiguous runs of
+// neighbour rows with one copy each into unpadded slots
+static constexpr int DSLASH_RUNS = 0x800;
 cudaError_t dslash(FieldKind k, int R, int epi, const void* links, const void* in, void* out,
                    const void* c1, const void* c2, double m2, const Geom& g, int out_parity,
                    int N, Gate gate, cudaStream_t s);
@@ -88,9 +91,10 @@ cudaError_t gram_partials(FieldKind k, const void* X, const void* Y, int N, int 
                           double2* partials, int nblocks, Gate gate, cudaStream_t s);
 cudaError_t gram_reduce(const double2* partials, int nblocks, int N, int hermitian, double2* out,
                         Gate gate, cudaStream_t s);
-// Q <- Q - AP beta
-cudaError_t w_update(FieldKind k, void* Q, const void* AP, const double2* beta, int N, int Vh,
-                     Gate gate, cudaStream_t s);
+// Q <- W = Q - AP beta, and the per-CTA partials of the Hermitian Gram W^dag W
+// (nblocks CTAs, reduced by gram_reduce)
+cudaError_t w_update_gram(FieldKind k, void* Q, const void* AP, const double2* beta, int N, int Vh,
+                          double2* partials, int nblocks, Gate gate, cudaStream_t s);
 // Q <- W Sinv ; X += P BC ; P <- Q + P SH unless st->ru_pending
 cudaError_t bcg_update(FieldKind sk, FieldKind xk, void* Q, void* P, void* X, const double2* Sinv,
                        const double2* BC, const double2* SH, int N, int Vh, Gate gate,
@@ -136,13 +140,14 @@ cudaError_t dense_qr_step(const double2* G, double2* C, double2* C_prev, double2
                           SolverStatus* st, Gate gate, cudaStream_t s);
 // Cholesky of the true-residual Gram -> C_new, Cinv; convergence on the true
 // residual; S = C_new C_prev^-1 -> SH = S^dag (unless init).
-// tres (N doubles) receives the per-column true relative residuals.
+// tres (N doubles) receives the per-column true relative residuals;
+// confirmed: G is the Gram of a native-FP64 residual, so a convergence it
+// shows is final (verified), else it awaits dense_verify.
 cudaError_t dense_restart(const double2* G, double2* C, double2* C_prev, double2* Cinv,
                           double2* SH, const double* bnorm, double* tres, double tol, int init,
-                          int N, SolverStatus* st, Gate gate, cudaStream_t s);
+                          int confirmed, int N, SolverStatus* st, Gate gate, cudaStream_t s);
 // native-FP64 confirmation of a convergence: true residuals from the FP64
-// Gram G of R = B - A Y into tres; verified, or done cleared and the
-// double-float threshold tightened
+// Gram G of R = B - A Y into tres; verified, or done cleared and fp64_only set
 cudaError_t dense_verify(const double2* G, const double* bnorm, double* tres, double tol, int N,
                          SolverStatus* st, cudaStream_t s);
 // bnorm_i = sqrt(Gb_ii); error if any is zero or not finite

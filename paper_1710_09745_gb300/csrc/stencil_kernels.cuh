@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(256)
     k_dslash_tma(const typename S::elem* __restrict__ links, const typename S::elem* __restrict__ in,
                  typename S::elem* __restrict__ out, const typename S::elem* __restrict__ c1,
                  const typename S::elem* __restrict__ c2, double m2d, Geom g, int parity, int N,
-                 int T, int sstride, Gate gate, SolverStatus* errst) {
+                 int T, int sstride, int runs, Gate gate, SolverStatus* errst) {
   using E = typename S::elem;
   using C = typename S::comp;
   using real = typename C::real;
@@ -292,13 +292,29 @@ __global__ void __launch_bounds__(256)
     if (lane == 0)
       bulk_g2s(base, links + link_offset(g, parity, (int)site0) + d * 9 * LINK_W,
                (uint32_t)(link_elems * sizeof(E)), &full[st]);
+    int nb = 0;
     if (lane < nvalid) {
       int x, y, z, t;
       const int site = (int)site0 + lane;
       site_xyzt(g, site, parity, x, y, z, t);
       const int lex = x + g.L[0] * (y + g.L[1] * (z + g.L[2] * t));
-      const int nb = neighbour_cb_s(g, lex, x, y, z, t, d >> 2, hop_k(d & 3));
-      bulk_g2s(base + link_elems + lane * sstride, in + (long long)nb * N * 3, spin_bytes, &full[st]);
+      nb = neighbour_cb_s(g, lex, x, y, z, t, d >> 2, hop_k(d & 3));
+    }
+    if (!runs) {
+      if (lane < nvalid)
+        bulk_g2s(base + link_elems + lane * sstride, in + (long long)nb * N * 3, spin_bytes, &full[st]);
+    } else {
+      // contiguous runs of neighbour rows (slots are unpadded, sstride = 3N):
+      // one bulk copy per run instead of one per site
+      const int prev = __shfl_up_sync(0xffffffffu, nb, 1);
+      const bool start = lane < nvalid && (lane == 0 || nb != prev + 1);
+      const unsigned m = __ballot_sync(0xffffffffu, start);
+      if (start) {
+        const unsigned higher = m & ~((2u << lane) - 1u);
+        const int next = higher ? __ffs(higher) - 1 : nvalid;
+        bulk_g2s(base + link_elems + lane * sstride, in + (long long)nb * N * 3,
+                 (uint32_t)(next - lane) * spin_bytes, &full[st]);
+      }
     }
   };
 
@@ -614,14 +630,14 @@ static int tma_site_stride(size_t eb, int N) {
 template <class S, int RV, int V, int EPI, int STAGES>
 static bool launch_tma_t(const void* links, const void* in, void* out, const void* c1,
                          const void* c2, double m2, const Geom& g, int parity, int N, Gate gate,
-                         SolverStatus* errst, cudaStream_t s) {
+                         SolverStatus* errst, int runs, cudaStream_t s) {
   using E = typename S::elem;
   const size_t eb = sizeof(E);
   const int NS = N / V;
   const int T = (NS + RV - 1) / RV;
   if (T * LINK_W > 256) return false;
   if ((3 * N * eb) % 16) return false;
-  const int sstride = tma_site_stride(eb, N);
+  const int sstride = runs ? 3 * N : tma_site_stride(eb, N);
   const size_t stage_bytes = (9 * LINK_W + (size_t)LINK_W * sstride) * eb;
   const size_t sm = STAGES * stage_bytes;
   if (sm > 200 * 1024) return false;
@@ -635,32 +651,33 @@ static bool launch_tma_t(const void* links, const void* in, void* out, const voi
   long long want = 152LL * per_sm;
   unsigned blocks = (unsigned)(units < want ? units : want);
   kern<<<blocks, T * LINK_W, sm, s>>>((const E*)links, (const E*)in, (E*)out, (const E*)c1,
-                                      (const E*)c2, m2, g, parity, N, T, sstride, gate, errst);
+                                      (const E*)c2, m2, g, parity, N, T, sstride, runs, gate,
+                                      errst);
   return true;
 }
 
 template <class S, int RV, int V>
 static bool launch_tma_r(int epi, const void* links, const void* in, void* out, const void* c1,
                          const void* c2, double m2, const Geom& g, int parity, int N, Gate gate,
-                         SolverStatus* errst, cudaStream_t s) {
+                         SolverStatus* errst, int runs, cudaStream_t s) {
   // three stages when they fit, else two
   switch (epi) {
     case EPI_NONE:
-      return launch_tma_t<S, RV, V, EPI_NONE, 3>(links, in, out, c1, c2, m2, g, parity, N, gate, errst, s) ||
-             launch_tma_t<S, RV, V, EPI_NONE, 2>(links, in, out, c1, c2, m2, g, parity, N, gate, errst, s);
+      return launch_tma_t<S, RV, V, EPI_NONE, 3>(links, in, out, c1, c2, m2, g, parity, N, gate, errst, runs, s) ||
+             launch_tma_t<S, RV, V, EPI_NONE, 2>(links, in, out, c1, c2, m2, g, parity, N, gate, errst, runs, s);
     case EPI_NORMAL:
-      return launch_tma_t<S, RV, V, EPI_NORMAL, 3>(links, in, out, c1, c2, m2, g, parity, N, gate, errst, s) ||
-             launch_tma_t<S, RV, V, EPI_NORMAL, 2>(links, in, out, c1, c2, m2, g, parity, N, gate, errst, s);
+      return launch_tma_t<S, RV, V, EPI_NORMAL, 3>(links, in, out, c1, c2, m2, g, parity, N, gate, errst, runs, s) ||
+             launch_tma_t<S, RV, V, EPI_NORMAL, 2>(links, in, out, c1, c2, m2, g, parity, N, gate, errst, runs, s);
     default:
-      return launch_tma_t<S, RV, V, EPI_RESIDUAL, 3>(links, in, out, c1, c2, m2, g, parity, N, gate, errst, s) ||
-             launch_tma_t<S, RV, V, EPI_RESIDUAL, 2>(links, in, out, c1, c2, m2, g, parity, N, gate, errst, s);
+      return launch_tma_t<S, RV, V, EPI_RESIDUAL, 3>(links, in, out, c1, c2, m2, g, parity, N, gate, errst, runs, s) ||
+             launch_tma_t<S, RV, V, EPI_RESIDUAL, 2>(links, in, out, c1, c2, m2, g, parity, N, gate, errst, runs, s);
   }
 }
 
 template <class S>
 static bool launch_tma_s(int R, int epi, const void* links, const void* in, void* out,
                      const void* c1, const void* c2, double m2, const Geom& g, int parity,
-                     int N, Gate gate, SolverStatus* errst, cudaStream_t s) {
+                     int N, Gate gate, SolverStatus* errst, int runs, cudaStream_t s) {
   // vector width V: complex numbers per load (FP32: 2 per 128 bits; 16-bit
   // kinds: 4 per 128 bits or 2 per 64 bits); RV = R / V slots per thread
   constexpr bool F32 = std::is_same<S, StoreF32>::value;
@@ -668,21 +685,21 @@ static bool launch_tma_s(int R, int epi, const void* links, const void* in, void
   constexpr int V2 = (F32 || H) ? 2 : 1;
   constexpr int V4 = H ? 4 : 1;
   if (H && (N % 4) == 0 && R >= 4) {
-    if (R == 4) return launch_tma_r<S, 1, V4>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, errst, s);
-    return launch_tma_r<S, 2, V4>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, errst, s);
+    if (R == 4) return launch_tma_r<S, 1, V4>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, errst, runs, s);
+    return launch_tma_r<S, 2, V4>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, errst, runs, s);
   }
   if ((F32 || H) && (N % 2) == 0 && R >= 2) {
     switch (R) {
-      case 2: return launch_tma_r<S, 1, V2>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, errst, s);
-      case 4: return launch_tma_r<S, 2, V2>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, errst, s);
-      default: return launch_tma_r<S, 4, V2>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, errst, s);
+      case 2: return launch_tma_r<S, 1, V2>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, errst, runs, s);
+      case 4: return launch_tma_r<S, 2, V2>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, errst, runs, s);
+      default: return launch_tma_r<S, 4, V2>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, errst, runs, s);
     }
   }
   switch (R) {
-    case 1: return launch_tma_r<S, 1, 1>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, errst, s);
-    case 2: return launch_tma_r<S, 2, 1>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, errst, s);
-    case 4: return launch_tma_r<S, 4, 1>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, errst, s);
-    default: return launch_tma_r<S, 8, 1>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, errst, s);
+    case 1: return launch_tma_r<S, 1, 1>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, errst, runs, s);
+    case 2: return launch_tma_r<S, 2, 1>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, errst, runs, s);
+    case 4: return launch_tma_r<S, 4, 1>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, errst, runs, s);
+    default: return launch_tma_r<S, 8, 1>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, errst, runs, s);
   }
 }
 
@@ -783,7 +800,8 @@ static cudaError_t dslash_kind(int R, int epi, const void* links, const void* in
   if (R & DSLASH_TMA) {
     const int r = R & 0xff;
     SolverStatus* errst = const_cast<SolverStatus*>(gate.st);
-    if (launch_tma_s<S>(r, epi, links, in, out, c1, c2, m2, g, out_parity, N, gate, errst, s))
+    if (launch_tma_s<S>(r, epi, links, in, out, c1, c2, m2, g, out_parity, N, gate, errst,
+                        (R & DSLASH_RUNS) ? 1 : 0, s))
       return cudaGetLastError();
     cudaGetLastError();
     R = r;
