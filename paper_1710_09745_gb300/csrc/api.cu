@@ -69,6 +69,10 @@ struct blockcg_ctx {
   double ms_st[5];
   // autotuned register tile of the stencil, keyed by kind * 128 + N
   std::map<int, int> tuned_R;
+  // autotuned shared-memory tiles of the block BLAS (sites per tile of the
+  // fused update, the Gram and the fused W update + Gram), same key, packed
+  // as upd | gram << 8 | wgram << 16
+  std::map<int, int> tuned_blas;
   // persisted tuning cache (blockcg_set_tune_cache): file path and entries
   std::string cache_path;
 };
@@ -412,6 +416,90 @@ int stencil_R(blockcg_ctx* h, FieldKind k, int N, const void* links, const void*
   return best;
 }
 
+// sites-per-tile choices of the block BLAS for (kind, N), packed as above
+struct BlasTiles {
+  int upd, gram, wgram;
+};
+BlasTiles unpack_tiles(int v) { return {v & 0xff, (v >> 8) & 0xff, (v >> 16) & 0xff}; }
+
+BlasTiles cached_tiles(const blockcg_ctx* h, FieldKind k, int N) {
+  auto it = h->tuned_blas.find((int)k * 128 + N);
+  return it != h->tuned_blas.end() ? unpack_tiles(it->second) : BlasTiles{0, 0, 0};
+}
+
+std::string blas_key(const blockcg_ctx* h, FieldKind k, int N) {
+  char buf[160];
+  snprintf(buf, sizeof(buf), "blas/%s/kind%d/N%d/%s", dims_tag(h).c_str(), (int)k, N,
+           device_tag().c_str());
+  return buf;
+}
+
+// Shared-memory tile sizes of the iteration's block BLAS (the streaming and
+// reduction multi-BLAS tile of Sec. 6.3/6.4, which the paper sizes by hand):
+// each candidate is timed over 3 launches on buffers that hold no state at
+// this point of a solve (AP and the odd temporary stand in for the blocks, R
+// for X, the partials buffer receives the Grams), the fastest kept per
+// (kind, N) and in the tuning cache.
+void tune_blas(blockcg_ctx* h, const Ws& w, int N) {
+  const FieldKind k = h->sloppy;
+  const int key = (int)k * 128 + N;
+  if (h->tuned_blas.count(key)) return;
+  long long cv = 0;
+  if (cache_get(h, blas_key(h, k, N), &cv)) {
+    h->tuned_blas[key] = (int)cv;
+    return;
+  }
+  EventPair ev;
+  if (ev.create() != cudaSuccess) {
+    cudaGetLastError();
+    h->tuned_blas[key] = 0;
+    return;
+  }
+  cudaStream_t s = h->stream;
+  Gate g0{nullptr, GATE_ALWAYS};
+  const int Vh = h->g.Vh;
+  auto time3 = [&](auto&& launch) -> float {
+    if (launch() != cudaSuccess) {
+      cudaGetLastError();
+      return 1e30f;
+    }
+    cudaEventRecord(ev.a, s);
+    for (int i = 0; i < 3; ++i) launch();
+    cudaEventRecord(ev.b, s);
+    float ms = 1e30f;
+    if (cudaEventSynchronize(ev.b) != cudaSuccess || cudaEventElapsedTime(&ms, ev.a, ev.b) != cudaSuccess) {
+      cudaGetLastError();
+      return 1e30f;
+    }
+    return ms;
+  };
+  int best_upd = 0, best_gram = 0, best_wgram = 0;
+  float t_upd = 1e30f, t_gram = 1e30f, t_wgram = 1e30f;
+  for (int ts : {4, 8, 16, 32}) {
+    float t = time3([&] {
+      return bcg_update(k, h->upd, w.AP, w.Ts, w.R, mat(w, M_SINV, N), mat(w, M_BC, N),
+                        mat(w, M_SH, N), N, Vh, g0, s, ts);
+    });
+    if (t < t_upd) t_upd = t, best_upd = ts;
+  }
+  int base = 256 / N;
+  if (base < 1) base = 1;
+  for (int ts : {base, 2 * base, 4 * base}) {
+    if (ts > 255) continue;
+    float t = time3([&] {
+      return gram_partials(k, w.AP, w.Ts, N, Vh, 1, w.partials, w.nblocks, g0, s, ts);
+    });
+    if (t < t_gram) t_gram = t, best_gram = ts;
+    t = time3([&] {
+      return w_update_gram(k, w.AP, w.Ts, mat(w, M_BETA, N), N, Vh, w.partials, w.nblocks, g0, s, ts);
+    });
+    if (t < t_wgram) t_wgram = t, best_wgram = ts;
+  }
+  const int packed = best_upd | (best_gram << 8) | (best_wgram << 16);
+  h->tuned_blas[key] = packed;
+  cache_put(h, blas_key(h, k, N), packed);
+}
+
 int cached_R(const blockcg_ctx* h, FieldKind k, int N) {
   const int rf = recon_flag(h, k);
   if (h->p.dslash_variant) return h->p.dslash_variant | rf;
@@ -459,12 +547,13 @@ int default_check_every(const blockcg_ctx* h, int N) {
 }
 
 // R = B - A Y, thin QR, restart of Q and P (Algorithm 3; init: Algorithm 1 set-up)
-// cheap = true: the residual R = B - A Y of the restart in the early-update
-// kind (double-float, from a rounded copy of Y; accurate to ~2^-48 |A| |Y|,
-// far below residuals well above tol); otherwise in native FP64, and a
-// convergence it reports is confirmed.  Y itself is always FP64.
-blockcg_status restart_block(blockcg_ctx* h, const Ws& w, int N, double tol, int init, Gate gate,
-                             bool cheap = false) {
+// The residual R = B - A Y of a restart (Y += X first, unless skip_acc).
+// cheap: in the early-update kind (double-float, from a rounded copy of Y;
+// accurate to ~2^-48 |A| |Y|, far below residuals well above tol), a
+// convergence it reports awaiting FP64 confirmation; otherwise native FP64.
+// Y itself is always FP64.
+blockcg_status restart_residual(blockcg_ctx* h, const Ws& w, int N, double tol, int init,
+                                Gate gate, bool cheap, bool skip_acc) {
   const FieldKind rk = cheap ? h->ru : h->fine;
   const void* links = cheap ? h->links_ru : h->links_fine;
   void* Yk = cheap ? w.Yru : w.Y;
@@ -474,7 +563,7 @@ blockcg_status restart_block(blockcg_ctx* h, const Ws& w, int N, double tol, int
   double m2 = h->mass * h->mass;
   size_t nel = (size_t)h->g.Vh * N * 3;
   cudaStream_t s = h->stream;
-  TL(TC_STREAM, accumulate(h->fine, h->upd, w.Y, w.X, nel, gate, s));
+  if (!skip_acc) TL(TC_STREAM, accumulate(h->fine, h->upd, w.Y, w.X, nel, gate, s));
   if (cheap) TL(TC_STREAM, convert_field(h->fine, rk, w.Y, Yk, nel, nullptr, gate, s));
   SL(1, dslash(rk, R, EPI_NONE, links, Yk, w.Tf, nullptr, nullptr, 0.0, h->g, 1, N, gate, s));
   SL(1, dslash(rk, R, EPI_RESIDUAL, links, w.Tf, Rk, Yk, Bk, m2, h->g, 0, N, gate, s));
@@ -485,6 +574,25 @@ blockcg_status restart_block(blockcg_ctx* h, const Ws& w, int N, double tol, int
   TL(TC_STREAM, restart_update(rk, h->sloppy, Rk, w.Q, w.P, mat(w, M_CINV, N), mat(w, M_SHRU, N), init,
                     N, h->g.Vh, gate, s));
   return BLOCKCG_OK;
+}
+
+// early reliable updates use the cheap (double-float) residual while the
+// iterated residual of that iteration is above this factor times tol, and
+// no FP64 confirmation has failed
+static constexpr double CHEAP_RU_ABOVE = 1e4;
+
+// A reliable update (Algorithm 3) gated by `gate`: with a cheaper kind, two
+// residual blocks gated on this iteration's residual (GATE_RU_CHEAP /
+// GATE_RU_FINE, exactly one of them runs); otherwise the FP64 one.
+blockcg_status restart_block(blockcg_ctx* h, const Ws& w, int N, double tol, int init, Gate gate) {
+  if (h->ru == h->fine || gate.mode != GATE_RU)
+    return restart_residual(h, w, N, tol, init, gate, false, false);
+  const size_t nel = (size_t)h->g.Vh * N * 3;
+  TL(TC_STREAM, accumulate(h->fine, h->upd, w.Y, w.X, nel, gate, h->stream));
+  const double thr = CHEAP_RU_ABOVE * tol;
+  blockcg_status rc = restart_residual(h, w, N, tol, init, Gate{gate.st, GATE_RU_CHEAP, thr}, true, true);
+  if (rc) return rc;
+  return restart_residual(h, w, N, tol, init, Gate{gate.st, GATE_RU_FINE, thr}, false, true);
 }
 
 // The true residual of the current Y in native FP64 (R = B - A Y with the
@@ -505,7 +613,7 @@ blockcg_status verify_fp64(blockcg_ctx* h, const Ws& w, int N, double tol) {
   return BLOCKCG_OK;
 }
 
-blockcg_status iterate_block(blockcg_ctx* h, const Ws& w, int N, double tol, bool cheap_ru = false) {
+blockcg_status iterate_block(blockcg_ctx* h, const Ws& w, int N, double tol) {
   Gate ga{w.st, GATE_ACTIVE};
   Gate gr{w.st, GATE_RU};
   int R = cached_R(h, h->sloppy, N);
@@ -514,19 +622,20 @@ blockcg_status iterate_block(blockcg_ctx* h, const Ws& w, int N, double tol, boo
   FieldKind k = h->sloppy;
   SL(0, dslash(k, R, EPI_NONE, h->links_sloppy, w.P, w.Ts, nullptr, nullptr, 0.0, h->g, 1, N, ga, s));
   SL(0, dslash(k, R, EPI_NORMAL, h->links_sloppy, w.Ts, w.AP, w.P, nullptr, m2, h->g, 0, N, ga, s));
-  TL(TC_GRAM, gram_partials(k, w.P, w.AP, N, h->g.Vh, 1, w.partials, w.nblocks, ga, s));
+  const BlasTiles bt = cached_tiles(h, k, N);
+  TL(TC_GRAM, gram_partials(k, w.P, w.AP, N, h->g.Vh, 1, w.partials, w.nblocks, ga, s, bt.gram));
   TL(TC_GRAM, gram_reduce(w.partials, w.nblocks, N, 1, mat(w, M_H, N), ga, s));
   TL(TC_DENSE, dense_beta(mat(w, M_H, N), mat(w, M_C, N), mat(w, M_BETA, N), mat(w, M_BC, N), N, w.st, ga, s));
   // W = Q - AP beta (over Q) with the partials of W^dag W in the same pass
   TL(TC_STREAM, w_update_gram(k, w.Q, w.AP, mat(w, M_BETA, N), N, h->g.Vh, w.partials, w.nblocks,
-                              ga, s));
+                              ga, s, bt.wgram));
   TL(TC_GRAM, gram_reduce(w.partials, w.nblocks, N, 1, mat(w, M_G, N), ga, s));
   QrStepParams qp{tol, h->p.ru_delta, h->p.ru_every, h->p.max_iter};
   TL(TC_DENSE, dense_qr_step(mat(w, M_G, N), mat(w, M_C, N), mat(w, M_CPREV, N), mat(w, M_SINV, N),
                    mat(w, M_SH, N), w.bnorm, qp, N, w.st, ga, s));
   TL(TC_STREAM, bcg_update(k, h->upd, w.Q, w.P, w.X, mat(w, M_SINV, N), mat(w, M_BC, N), mat(w, M_SH, N), N,
-                h->g.Vh, ga, s));
-  return restart_block(h, w, N, tol, 0, gr, cheap_ru);
+                h->g.Vh, ga, s, bt.upd));
+  return restart_block(h, w, N, tol, 0, gr);
 }
 
 blockcg_status status_to_result(blockcg_ctx* h, const SolverStatus& st) {
@@ -550,6 +659,7 @@ blockcg_status check_solve_args(blockcg_ctx* h, const void* B, const void* X, in
 // (after the set-up: P and Y hold data; AP, Ts, R and Tf are free until the
 // first iteration and the next reliable update rewrite them)
 void tune_block(blockcg_ctx* h, const Ws& w, int N) {
+  tune_blas(h, w, N);
   stencil_R(h, h->sloppy, N, h->links_sloppy, w.P, w.Ts, w.AP);
   stencil_R(h, h->fine, N, h->links_fine, w.Y, w.Tf, w.R);
   if (h->ru != h->fine) stencil_R(h, h->ru, N, h->links_ru, w.Yru, w.Tf, w.Rru);
@@ -583,10 +693,7 @@ bool converged(const blockcg_ctx* h, const SolverStatus& hs) {
   return hs.done && hs.verified;
 }
 
-// early reliable updates in the cheap kind while the last iterated residual
-// (as the host last read it) is above this factor times tol, and no FP64
-// confirmation has failed
-static constexpr double CHEAP_RU_ABOVE = 100.0;
+
 
 // Host-driven iteration from the current device state: enqueue chunks of
 // gated iterations and poll the status word between them; a convergence
@@ -608,9 +715,8 @@ blockcg_status host_loop(blockcg_ctx* h, const Ws& w, int N, double tol, SolverS
     int n = chunk;
     if (hs->iters + n > h->p.max_iter) n = h->p.max_iter - hs->iters;
     if (n <= 0) n = 1;
-    const bool cheap = h->ru != h->fine && !hs->fp64_only && hs->res_max > CHEAP_RU_ABOVE * tol;
     for (int i = 0; i < n; ++i) {
-      rc = iterate_block(h, w, N, tol, cheap);
+      rc = iterate_block(h, w, N, tol);
       if (rc) return rc;
     }
   }

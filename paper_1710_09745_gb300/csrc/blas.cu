@@ -283,13 +283,21 @@ __global__ void k_gram_reduce(const double2* __restrict__ partials, int nblocks,
   }
 }
 
+// sites per Gram tile: the requested count, else 256 / N; never more than
+// fits 200 KB of shared memory
+static int gram_tile(int req, int N, size_t per_site) {
+  int TS = req > 0 ? req : 256 / N;
+  if (TS < 1) TS = 1;
+  while (TS > 1 && (size_t)TS * per_site > 200 * 1024) TS >>= 1;
+  return TS;
+}
+
 template <class S, int B>
 static void launch_gram_b(const void* X, const void* Y, int N, int Vh, int herm, double2* partials,
-                          int nblocks, Gate gate, cudaStream_t s) {
+                          int nblocks, Gate gate, int tile, cudaStream_t s) {
   using real = typename S::comp::real;
-  int TS = 256 / N;
-  if (TS < 1) TS = 1;
   int same = (X == Y);
+  const int TS = gram_tile(tile, N, (same ? 1 : 2) * (size_t)N * 3 * sizeof(cpx<real>));
   size_t tiles = (same ? 1 : 2) * (size_t)TS * N * 3 * sizeof(cpx<real>);
   size_t red = GRAM_THREADS * sizeof(double2);
   size_t sm = tiles > red ? tiles : red;
@@ -301,23 +309,23 @@ static void launch_gram_b(const void* X, const void* Y, int N, int Vh, int herm,
 
 template <class S>
 static void launch_gram(const void* X, const void* Y, int N, int Vh, int herm, double2* partials,
-                        int nblocks, Gate gate, cudaStream_t s) {
+                        int nblocks, Gate gate, int tile, cudaStream_t s) {
   if (N == 1)
-    launch_gram_b<S, 1>(X, Y, N, Vh, herm, partials, nblocks, gate, s);
+    launch_gram_b<S, 1>(X, Y, N, Vh, herm, partials, nblocks, gate, tile, s);
   else if (N <= 16)
-    launch_gram_b<S, 2>(X, Y, N, Vh, herm, partials, nblocks, gate, s);
+    launch_gram_b<S, 2>(X, Y, N, Vh, herm, partials, nblocks, gate, tile, s);
   else
-    launch_gram_b<S, 4>(X, Y, N, Vh, herm, partials, nblocks, gate, s);
+    launch_gram_b<S, 4>(X, Y, N, Vh, herm, partials, nblocks, gate, tile, s);
 }
 
 cudaError_t gram_partials(FieldKind k, const void* X, const void* Y, int N, int Vh, int hermitian,
-                          double2* partials, int nblocks, Gate gate, cudaStream_t s) {
+                          double2* partials, int nblocks, Gate gate, cudaStream_t s, int tile) {
   switch (k) {
-    case FK_DF: launch_gram<StoreDF>(X, Y, N, Vh, hermitian, partials, nblocks, gate, s); break;
-    case FK_F32: launch_gram<StoreF32>(X, Y, N, Vh, hermitian, partials, nblocks, gate, s); break;
-    case FK_F64: launch_gram<StoreF64>(X, Y, N, Vh, hermitian, partials, nblocks, gate, s); break;
-    case FK_H16: launch_gram<StoreH16>(X, Y, N, Vh, hermitian, partials, nblocks, gate, s); break;
-    case FK_BF16: launch_gram<StoreBF16>(X, Y, N, Vh, hermitian, partials, nblocks, gate, s); break;
+    case FK_DF: launch_gram<StoreDF>(X, Y, N, Vh, hermitian, partials, nblocks, gate, tile, s); break;
+    case FK_F32: launch_gram<StoreF32>(X, Y, N, Vh, hermitian, partials, nblocks, gate, tile, s); break;
+    case FK_F64: launch_gram<StoreF64>(X, Y, N, Vh, hermitian, partials, nblocks, gate, tile, s); break;
+    case FK_H16: launch_gram<StoreH16>(X, Y, N, Vh, hermitian, partials, nblocks, gate, tile, s); break;
+    case FK_BF16: launch_gram<StoreBF16>(X, Y, N, Vh, hermitian, partials, nblocks, gate, tile, s); break;
   }
   return cudaGetLastError();
 }
@@ -452,10 +460,9 @@ __global__ void __launch_bounds__(GRAM_THREADS)
 
 template <class S, int B>
 static void launch_w_gram_b(void* Q, const void* AP, const double2* beta, int N, int Vh,
-                            double2* partials, int nblocks, Gate gate, cudaStream_t s) {
+                            double2* partials, int nblocks, Gate gate, int tile, cudaStream_t s) {
   using real = typename S::comp::real;
-  int TS = 256 / N;
-  if (TS < 1) TS = 1;
+  const int TS = gram_tile(tile, N, 2 * (size_t)N * 3 * sizeof(cpx<real>));
   const size_t tiles = (2 * (size_t)TS * N * 3 + (size_t)N * N) * sizeof(cpx<real>);
   const size_t red = GRAM_THREADS * sizeof(double2);
   const size_t sm = tiles > red ? tiles : red;
@@ -467,23 +474,23 @@ static void launch_w_gram_b(void* Q, const void* AP, const double2* beta, int N,
 
 template <class S>
 static void launch_w_gram(void* Q, const void* AP, const double2* beta, int N, int Vh,
-                          double2* partials, int nblocks, Gate gate, cudaStream_t s) {
+                          double2* partials, int nblocks, Gate gate, int tile, cudaStream_t s) {
   if (N == 1)
-    launch_w_gram_b<S, 1>(Q, AP, beta, N, Vh, partials, nblocks, gate, s);
+    launch_w_gram_b<S, 1>(Q, AP, beta, N, Vh, partials, nblocks, gate, tile, s);
   else if (N <= 16)
-    launch_w_gram_b<S, 2>(Q, AP, beta, N, Vh, partials, nblocks, gate, s);
+    launch_w_gram_b<S, 2>(Q, AP, beta, N, Vh, partials, nblocks, gate, tile, s);
   else
-    launch_w_gram_b<S, 4>(Q, AP, beta, N, Vh, partials, nblocks, gate, s);
+    launch_w_gram_b<S, 4>(Q, AP, beta, N, Vh, partials, nblocks, gate, tile, s);
 }
 
 cudaError_t w_update_gram(FieldKind k, void* Q, const void* AP, const double2* beta, int N, int Vh,
-                          double2* partials, int nblocks, Gate gate, cudaStream_t s) {
+                          double2* partials, int nblocks, Gate gate, cudaStream_t s, int tile) {
   switch (k) {
-    case FK_DF: launch_w_gram<StoreDF>(Q, AP, beta, N, Vh, partials, nblocks, gate, s); break;
-    case FK_F32: launch_w_gram<StoreF32>(Q, AP, beta, N, Vh, partials, nblocks, gate, s); break;
-    case FK_F64: launch_w_gram<StoreF64>(Q, AP, beta, N, Vh, partials, nblocks, gate, s); break;
-    case FK_H16: launch_w_gram<StoreH16>(Q, AP, beta, N, Vh, partials, nblocks, gate, s); break;
-    case FK_BF16: launch_w_gram<StoreBF16>(Q, AP, beta, N, Vh, partials, nblocks, gate, s); break;
+    case FK_DF: launch_w_gram<StoreDF>(Q, AP, beta, N, Vh, partials, nblocks, gate, tile, s); break;
+    case FK_F32: launch_w_gram<StoreF32>(Q, AP, beta, N, Vh, partials, nblocks, gate, tile, s); break;
+    case FK_F64: launch_w_gram<StoreF64>(Q, AP, beta, N, Vh, partials, nblocks, gate, tile, s); break;
+    case FK_H16: launch_w_gram<StoreH16>(Q, AP, beta, N, Vh, partials, nblocks, gate, tile, s); break;
+    case FK_BF16: launch_w_gram<StoreBF16>(Q, AP, beta, N, Vh, partials, nblocks, gate, tile, s); break;
   }
   return cudaGetLastError();
 }
@@ -507,8 +514,12 @@ struct TileCfg {
 
 static TileCfg tile_cfg(int N, size_t real_cplx_bytes, int n_tiles, int n_coefs,
                         size_t budget = 96 * 1024) {
-  int JT = N < 16 ? N : 16;
+  // all N coefficient columns at once when they fit 64 KB (staged once per
+  // tile pass instead of once per 16-column chunk), else chunks of 16
+  int JT = (size_t)n_coefs * N * N * real_cplx_bytes <= 64 * 1024 ? N : 16;
+  if (JT > N) JT = N;
   size_t coef = (size_t)n_coefs * N * JT * real_cplx_bytes;
+  if (budget < coef + 32 * 1024) budget = coef + 32 * 1024;
   int TS = 32;
   while (TS > 1 && coef + (size_t)n_tiles * TS * N * 3 * real_cplx_bytes > budget) TS >>= 1;
   return {TS, JT};
@@ -742,7 +753,7 @@ __global__ void __launch_bounds__(256, 3)
 template <class SS, class XS>
 static cudaError_t launch_bcg_update(void* Q, void* P, void* X, const double2* Sinv,
                                      const double2* BC, const double2* SH, int N, int Vh,
-                                     Gate gate, cudaStream_t s) {
+                                     Gate gate, int tile, cudaStream_t s) {
   using real = typename SS::comp::real;
   // double-float: 2 output columns per thread keep the accumulators within the
   // register budget of four resident blocks (no spills); other kinds use 4
@@ -752,15 +763,24 @@ static cudaError_t launch_bcg_update(void* Q, void* P, void* X, const double2* S
   constexpr bool DB = !std::is_same<SS, StoreDF>::value;
   const size_t cb = sizeof(cpx<real>), xb = sizeof(typename XS::elem);
   const size_t tb = DB ? sizeof(typename SS::elem) : cb;  // tile element bytes
-  const int JT = (N + 1) < 16 ? (N + 1) : 16;
+  // coefficient columns staged per chunk: all N when the three N x N
+  // matrices fit 64 KB (then once per CTA, not once per tile), else 32 or 16
+  int JT = N;
+  while (JT > 16 && 3ull * N * JT * cb > 64 * 1024) JT = JT > 32 ? 32 : 16;
+  if (JT < N && JT < 16) JT = 16;
   const size_t coef = 3ull * N * JT * cb;
-  const size_t budget = N <= 16 ? 56 * 1024 : 96 * 1024;
-  int TS = 32;
   auto tile_bytes = [&](int ts) {
     size_t one = upd_wp_bytes(ts, N, tb) + (DB ? (size_t)ts * 3 * N * xb : 0);
     return (DB ? 2 : 1) * one;
   };
-  while (TS > 1 && coef + tile_bytes(TS) > budget) TS >>= 1;
+  int TS = 32;
+  if (tile > 0) {
+    TS = tile;  // the tuner's choice (sites per tile)
+    while (TS > 1 && coef + tile_bytes(TS) > 200 * 1024) TS >>= 1;
+  } else {
+    const size_t budget = (N <= 16 ? 56 * 1024 : 96 * 1024) + coef;
+    while (TS > 1 && coef + tile_bytes(TS) > budget) TS >>= 1;
+  }
   const size_t sm = coef + tile_bytes(TS);
   cudaFuncSetAttribute(k_bcg_update<SS, XS, JB, DB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)sm);
@@ -795,17 +815,17 @@ static cudaError_t launch_bcg_update(void* Q, void* P, void* X, const double2* S
 
 cudaError_t bcg_update(FieldKind sk, FieldKind xk, void* Q, void* P, void* X, const double2* Sinv,
                        const double2* BC, const double2* SH, int N, int Vh, Gate gate,
-                       cudaStream_t s) {
+                       cudaStream_t s, int tile) {
   if (sk == FK_DF && xk == FK_DF)
-    return launch_bcg_update<StoreDF, StoreDF>(Q, P, X, Sinv, BC, SH, N, Vh, gate, s);
+    return launch_bcg_update<StoreDF, StoreDF>(Q, P, X, Sinv, BC, SH, N, Vh, gate, tile, s);
   if (sk == FK_F32 && xk == FK_DF)
-    return launch_bcg_update<StoreF32, StoreDF>(Q, P, X, Sinv, BC, SH, N, Vh, gate, s);
+    return launch_bcg_update<StoreF32, StoreDF>(Q, P, X, Sinv, BC, SH, N, Vh, gate, tile, s);
   if (sk == FK_F64 && xk == FK_F64)
-    return launch_bcg_update<StoreF64, StoreF64>(Q, P, X, Sinv, BC, SH, N, Vh, gate, s);
+    return launch_bcg_update<StoreF64, StoreF64>(Q, P, X, Sinv, BC, SH, N, Vh, gate, tile, s);
   if (sk == FK_H16 && xk == FK_DF)
-    return launch_bcg_update<StoreH16, StoreDF>(Q, P, X, Sinv, BC, SH, N, Vh, gate, s);
+    return launch_bcg_update<StoreH16, StoreDF>(Q, P, X, Sinv, BC, SH, N, Vh, gate, tile, s);
   if (sk == FK_BF16 && xk == FK_DF)
-    return launch_bcg_update<StoreBF16, StoreDF>(Q, P, X, Sinv, BC, SH, N, Vh, gate, s);
+    return launch_bcg_update<StoreBF16, StoreDF>(Q, P, X, Sinv, BC, SH, N, Vh, gate, tile, s);
   return cudaErrorInvalidValue;
 }
 
@@ -827,6 +847,11 @@ __global__ void __launch_bounds__(256)
   cpx<rreal>* sA = sR + TS * N * 3;                                 // Cinv chunk (fine)
   cpx<real>* sP = reinterpret_cast<cpx<real>*>(sA + N * JT);       // P tile (sloppy)
   cpx<real>* sC = sP + TS * N * 3;                                  // SH chunk (sloppy)
+  const bool one_chunk = JT >= N;  // all coefficients staged once per CTA
+  if (one_chunk) {
+    stage_coef<CR>(sA, Cinv, N, 0, N, JT);
+    if (!init) stage_coef<C>(sC, SH, N, 0, N, JT);
+  }
   for (long long tile = blockIdx.x; tile * TS < Vh; tile += gridDim.x) {
     const long long site0 = tile * TS;
     const int ns = (int)min((long long)TS, (long long)Vh - site0);
@@ -839,9 +864,11 @@ __global__ void __launch_bounds__(256)
     }
     for (int j0 = 0; j0 < N; j0 += JT) {
       const int jn = min(JT, N - j0);
-      __syncthreads();
-      stage_coef<CR>(sA, Cinv, N, j0, jn, JT);
-      if (!init) stage_coef<C>(sC, SH, N, j0, jn, JT);
+      if (!one_chunk) {
+        __syncthreads();
+        stage_coef<CR>(sA, Cinv, N, j0, jn, JT);
+        if (!init) stage_coef<C>(sC, SH, N, j0, jn, JT);
+      }
       __syncthreads();
       const int nrows = ns * 3;
       const int nout = nrows * jn;

@@ -117,23 +117,15 @@ __device__ void load_mat(double2* dst, const double2* __restrict__ src, int N) {
   __syncthreads();
 }
 
-__device__ __forceinline__ bool dense_gate_closed(const SolverStatus* st, int mode) {
-  if (mode == GATE_ALWAYS || st == nullptr) return false;
-  const volatile SolverStatus* s = st;
-  if (s->done || s->error || s->stopped) return true;
-  if (mode == GATE_RU && !s->ru_pending) return true;
-  if (mode == GATE_ITER && s->ru_pending) return true;
-  return false;
-}
 
 // ---------------------------------------------------------------- beta ----
 __global__ void __launch_bounds__(DENSE_THREADS)
     k_dense_beta(const double2* __restrict__ H, const double2* __restrict__ Cm,
                  double2* __restrict__ beta, double2* __restrict__ BC, int N, SolverStatus* st,
-                 int gmode) {
+                 Gate gate) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int flag;
-  if (dense_gate_closed(st, gmode)) return;
+  if (gate_closed(gate)) return;
   double2* A = reinterpret_cast<double2*>(smem_raw);
   double2* Li = A + N * N;
   double2* Bt = Li + N * N;
@@ -166,7 +158,7 @@ cudaError_t dense_beta(const double2* H, const double2* C, double2* beta, double
                        SolverStatus* st, Gate gate, cudaStream_t s) {
   size_t sm = 3ull * N * N * sizeof(double2);
   cudaFuncSetAttribute(k_dense_beta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_dense_beta<<<1, DENSE_THREADS, sm, s>>>(H, C, beta, BC, N, st, gate.mode);
+  k_dense_beta<<<1, DENSE_THREADS, sm, s>>>(H, C, beta, BC, N, st, gate);
   return cudaGetLastError();
 }
 
@@ -175,11 +167,11 @@ __global__ void __launch_bounds__(DENSE_THREADS)
     k_dense_qr_step(const double2* __restrict__ G, double2* __restrict__ C,
                     double2* __restrict__ C_prev, double2* __restrict__ Sinv,
                     double2* __restrict__ SH, const double* __restrict__ bnorm, QrStepParams p,
-                    int N, SolverStatus* st, int gmode) {
+                    int N, SolverStatus* st, Gate gate) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int flag;
   __shared__ double resv[64];
-  if (dense_gate_closed(st, gmode)) return;
+  if (gate_closed(gate)) return;
   double2* A = reinterpret_cast<double2*>(smem_raw);
   double2* Li = A + N * N;
   double2* Cs = Li + N * N;
@@ -242,7 +234,7 @@ cudaError_t dense_qr_step(const double2* G, double2* C, double2* C_prev, double2
                           SolverStatus* st, Gate gate, cudaStream_t s) {
   size_t sm = 3ull * N * N * sizeof(double2);
   cudaFuncSetAttribute(k_dense_qr_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_dense_qr_step<<<1, DENSE_THREADS, sm, s>>>(G, C, C_prev, Sinv, SH, bnorm, p, N, st, gate.mode);
+  k_dense_qr_step<<<1, DENSE_THREADS, sm, s>>>(G, C, C_prev, Sinv, SH, bnorm, p, N, st, gate);
   return cudaGetLastError();
 }
 
@@ -252,11 +244,11 @@ __global__ void __launch_bounds__(DENSE_THREADS)
                     double2* __restrict__ C_prev, double2* __restrict__ Cinv,
                     double2* __restrict__ SH, const double* __restrict__ bnorm,
                     double* __restrict__ tres_out, double tol, int init, int confirmed, int N,
-                    SolverStatus* st, int gmode) {
+                    SolverStatus* st, Gate gate) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int flag;
   __shared__ double tres[64];
-  if (dense_gate_closed(st, gmode)) return;
+  if (gate_closed(gate)) return;
   double2* A = reinterpret_cast<double2*>(smem_raw);  // -> L of the true residual
   double2* Wk = A + N * N;                            // L^-1, then C_prev^dag (lower)
   double2* Pi = Wk + N * N;                           // (C_prev^dag)^-1
@@ -356,7 +348,7 @@ cudaError_t dense_restart(const double2* G, double2* C, double2* C_prev, double2
   size_t sm = 3ull * N * N * sizeof(double2);
   cudaFuncSetAttribute(k_dense_restart, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_dense_restart<<<1, DENSE_THREADS, sm, s>>>(G, C, C_prev, Cinv, SH, bnorm, tres, tol, init,
-                                               confirmed, N, st, gate.mode);
+                                               confirmed, N, st, gate);
   return cudaGetLastError();
 }
 
@@ -408,8 +400,8 @@ cudaError_t dense_chol_upper(const double2* H, double2* R, double2* Rinv, int N,
 // ------------------------------------------------------------ CG scalars ----
 __global__ void k_cg_alpha(const double2* __restrict__ pAp, const double* __restrict__ rr,
                            const double* __restrict__ gam, double* __restrict__ alpha,
-                           double* __restrict__ alpha_x, SolverStatus* st, int gmode) {
-  if (dense_gate_closed(st, gmode)) return;
+                           double* __restrict__ alpha_x, SolverStatus* st, Gate gate) {
+  if (gate_closed(gate)) return;
   double d = pAp[0].x;
   if (!isfinite(d)) {
     st->error = BLOCKCG_ERR_NONFINITE;
@@ -427,8 +419,8 @@ __global__ void k_cg_alpha(const double2* __restrict__ pAp, const double* __rest
 __global__ void k_cg_beta(const double2* __restrict__ rr_new_sum, double* __restrict__ rr,
                           double* __restrict__ beta, const double* __restrict__ bnorm,
                           const double* __restrict__ gam, double tol, double delta,
-                          SolverStatus* st, int gmode) {
-  if (dense_gate_closed(st, gmode)) return;
+                          SolverStatus* st, Gate gate) {
+  if (gate_closed(gate)) return;
   double bnorm2 = bnorm[0] * bnorm[0];
   double rn = rr_new_sum[0].x;  // |gamma r|^2
   int it = st->iters + 1;
@@ -452,14 +444,14 @@ __global__ void k_cg_beta(const double2* __restrict__ rr_new_sum, double* __rest
 
 cudaError_t cg_scalar_alpha(const double2* pAp, const double* rr, const double* gam, double* alpha,
                             double* alpha_x, SolverStatus* st, Gate gate, cudaStream_t s) {
-  k_cg_alpha<<<1, 1, 0, s>>>(pAp, rr, gam, alpha, alpha_x, st, gate.mode);
+  k_cg_alpha<<<1, 1, 0, s>>>(pAp, rr, gam, alpha, alpha_x, st, gate);
   return cudaGetLastError();
 }
 
 cudaError_t cg_scalar_beta(const double2* rr_new_sum, double* rr, double* beta,
                            const double* bnorm, const double* gam, double tol, double delta,
                            SolverStatus* st, Gate gate, cudaStream_t s) {
-  k_cg_beta<<<1, 1, 0, s>>>(rr_new_sum, rr, beta, bnorm, gam, tol, delta, st, gate.mode);
+  k_cg_beta<<<1, 1, 0, s>>>(rr_new_sum, rr, beta, bnorm, gam, tol, delta, st, gate);
   return cudaGetLastError();
 }
 

@@ -19,20 +19,34 @@ inline size_t elem_bytes(FieldKind k) {
 // whole iterations without reading back the convergence state.
 // GATE_ACTIVE: run unless done or failed; GATE_RU: additionally only when a
 // reliable update is pending; GATE_ITER: run unless done, failed or a
-// convergence check is pending (CG baseline).
-enum GateMode { GATE_ALWAYS = 0, GATE_ACTIVE = 1, GATE_RU = 2, GATE_ITER = 3 };
+// convergence check is pending (CG baseline).  GATE_RU_CHEAP / GATE_RU_FINE
+// split a pending reliable update by the iterated residual of this iteration:
+// the cheap (double-float) residual while res_max > thr and no FP64
+// confirmation has failed, the native-FP64 one otherwise.
+enum GateMode {
+  GATE_ALWAYS = 0,
+  GATE_ACTIVE = 1,
+  GATE_RU = 2,
+  GATE_ITER = 3,
+  GATE_RU_CHEAP = 4,
+  GATE_RU_FINE = 5
+};
 struct Gate {
   const SolverStatus* st;
   int mode;
+  double thr;  // res_max threshold of GATE_RU_CHEAP / GATE_RU_FINE
 };
 
 __device__ __forceinline__ bool gate_closed(const Gate& g) {
   if (g.mode == GATE_ALWAYS || g.st == nullptr) return false;
   const volatile SolverStatus* s = g.st;
   if (s->done || s->error || s->stopped) return true;
-  if (g.mode == GATE_RU && !s->ru_pending) return true;
-  if (g.mode == GATE_ITER && s->ru_pending) return true;
-  return false;
+  if (g.mode == GATE_ITER) return s->ru_pending != 0;
+  if (g.mode == GATE_ACTIVE) return false;
+  if (!s->ru_pending) return true;  // the reliable-update modes
+  if (g.mode == GATE_RU) return false;
+  const bool cheap = !s->fp64_only && s->res_max > g.thr;
+  return g.mode == GATE_RU_CHEAP ? !cheap : cheap;
 }
 
 // Stencil epilogues.
@@ -87,18 +101,20 @@ cudaError_t from_internal(FieldKind k, const void* internal, double2* user, int 
                           cudaStream_t s);
 cudaError_t zero_field(FieldKind k, void* f, size_t n_elems, cudaStream_t s);
 int gram_blocks(int N, int rows);
+// tile (here and below): sites per shared-memory tile, 0 = the default;
+// the solver's autotuner picks it per storage kind and N
 cudaError_t gram_partials(FieldKind k, const void* X, const void* Y, int N, int Vh, int hermitian,
-                          double2* partials, int nblocks, Gate gate, cudaStream_t s);
+                          double2* partials, int nblocks, Gate gate, cudaStream_t s, int tile = 0);
 cudaError_t gram_reduce(const double2* partials, int nblocks, int N, int hermitian, double2* out,
                         Gate gate, cudaStream_t s);
 // Q <- W = Q - AP beta, and the per-CTA partials of the Hermitian Gram W^dag W
 // (nblocks CTAs, reduced by gram_reduce)
 cudaError_t w_update_gram(FieldKind k, void* Q, const void* AP, const double2* beta, int N, int Vh,
-                          double2* partials, int nblocks, Gate gate, cudaStream_t s);
+                          double2* partials, int nblocks, Gate gate, cudaStream_t s, int tile = 0);
 // Q <- W Sinv ; X += P BC ; P <- Q + P SH unless st->ru_pending
 cudaError_t bcg_update(FieldKind sk, FieldKind xk, void* Q, void* P, void* X, const double2* Sinv,
                        const double2* BC, const double2* SH, int N, int Vh, Gate gate,
-                       cudaStream_t s);
+                       cudaStream_t s, int tile = 0);
 // Q <- R Cinv (converted to Q's kind) ; P <- Q + P SH (or P <- Q when init)
 cudaError_t restart_update(FieldKind rk, FieldKind sk, const void* R, void* Q, void* P,
                            const double2* Cinv, const double2* SH, int init, int N, int Vh,
