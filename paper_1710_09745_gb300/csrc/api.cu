@@ -576,10 +576,16 @@ blockcg_status restart_residual(blockcg_ctx* h, const Ws& w, int N, double tol, 
   return BLOCKCG_OK;
 }
 
-// early reliable updates use the cheap (double-float) residual while the
-// iterated residual of that iteration is above this factor times tol, and
-// no FP64 confirmation has failed
-static constexpr double CHEAP_RU_ABOVE = 1e4;
+// Early reliable updates use the cheap (double-float) residual while the
+// iterated residual of that iteration is above this factor times tol and no
+// FP64 confirmation has failed.  The double-float residual's error (~2^-48
+// |A| |Y|, about 1e-12 |b| on the 32^4, m = 0.01 workload) has to stay small
+// against the residual relative to the rounding of the iteration's storage:
+// 2^-24 for FP32 and double-float iterations (factor 1e4), 2^-11 or 2^-8
+// for the 16-bit ones (factor 100).
+double cheap_ru_above(const blockcg_ctx* h) {
+  return (h->sloppy == FK_H16 || h->sloppy == FK_BF16) ? 1e2 : 1e4;
+}
 
 // A reliable update (Algorithm 3) gated by `gate`: with a cheaper kind, two
 // residual blocks gated on this iteration's residual (GATE_RU_CHEAP /
@@ -589,7 +595,7 @@ blockcg_status restart_block(blockcg_ctx* h, const Ws& w, int N, double tol, int
     return restart_residual(h, w, N, tol, init, gate, false, false);
   const size_t nel = (size_t)h->g.Vh * N * 3;
   TL(TC_STREAM, accumulate(h->fine, h->upd, w.Y, w.X, nel, gate, h->stream));
-  const double thr = CHEAP_RU_ABOVE * tol;
+  const double thr = cheap_ru_above(h) * tol;
   blockcg_status rc = restart_residual(h, w, N, tol, init, Gate{gate.st, GATE_RU_CHEAP, thr}, true, true);
   if (rc) return rc;
   return restart_residual(h, w, N, tol, init, Gate{gate.st, GATE_RU_FINE, thr}, false, true);
@@ -796,7 +802,7 @@ blockcg_status blockcg_create(blockcg_t* out, const int dims[4], double mass,
       prm.check_every < 0 || (int)prm.prec < 0 || (int)prm.prec > 4)
     return BLOCKCG_ERR_ARG;
   {
-    int r = prm.dslash_variant & ~(DSLASH_TMA | DSLASH_ASYNC | DSLASH_RUNS);
+    int r = prm.dslash_variant & ~(DSLASH_TMA | DSLASH_ASYNC | DSLASH_RUNS | DSLASH_BLOCKED);
     if ((prm.dslash_variant & DSLASH_RUNS) && !(prm.dslash_variant & DSLASH_TMA)) return BLOCKCG_ERR_ARG;
     if (prm.dslash_variant != 0 && r != 1 && r != 2 && r != 4 && r != 8) return BLOCKCG_ERR_ARG;
   }

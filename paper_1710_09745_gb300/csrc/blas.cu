@@ -347,6 +347,8 @@ cudaError_t gram_reduce(const double2* partials, int nblocks, int N, int hermiti
 // staged W with the register blocking of k_gram; the per-CTA partials go to
 // the same fixed-order reduction.  W is read from HBM once fewer than with a
 // separate Gram pass.
+static constexpr int WGJ = 4;  // columns of W per thread in k_w_gram
+
 template <class S, int B>
 __global__ void __launch_bounds__(GRAM_THREADS)
     k_w_gram(typename S::elem* __restrict__ Q, const typename S::elem* __restrict__ AP,
@@ -399,24 +401,40 @@ __global__ void __launch_bounds__(GRAM_THREADS)
       sA[idx] = S::load(AP + base + idx);
     }
     __syncthreads();
-    for (int idx = tid; idx < nel; idx += GRAM_THREADS) {
-      const int row = idx / N, j = idx - row * N;
+    // W = Q - AP beta: a thread owns WGJ consecutive columns of one row, so
+    // each AP value read from shared memory feeds WGJ multiply-adds
+    const int ng = (N + WGJ - 1) / WGJ;
+    for (int u = tid; u < ns * 3 * ng; u += GRAM_THREADS) {
+      const int row = u / ng, j0 = (u - row * ng) * WGJ;
       const cpx<real>* apr = sA + row * N;
-      cpx<acc> w = cacc_from<C>(sW[idx]);
+      cpx<acc> w[WGJ];
+#pragma unroll
+      for (int v = 0; v < WGJ; ++v)
+        w[v] = (j0 + v < N) ? cacc_from<C>(sW[row * N + j0 + v]) : czero<C>();
       for (int i = 0; i < N; ++i) {
         const cpx<real> ap = apr[i];
-        const cpx<real> bb = sb[i * N + j];
-        // w -= ap * bb
-        C::msub(w.re, ap.re, bb.re);
-        C::mac(w.re, ap.im, bb.im);
-        C::msub(w.im, ap.re, bb.im);
-        C::msub(w.im, ap.im, bb.re);
+#pragma unroll
+        for (int v = 0; v < WGJ; ++v) {
+          if (j0 + v < N) {
+            const cpx<real> bb = sb[i * N + j0 + v];
+            // w -= ap * bb
+            C::msub(w[v].re, ap.re, bb.re);
+            C::mac(w[v].re, ap.im, bb.im);
+            C::msub(w[v].im, ap.re, bb.im);
+            C::msub(w[v].im, ap.im, bb.re);
+          }
+        }
       }
-      typename S::elem e;
-      S::store(&e, cfin<C>(w));
-      Q[base + idx] = e;
-      // the value as stored (rounded to the storage format) feeds the Gram
-      sW[idx] = S::load_nc(&e);
+#pragma unroll
+      for (int v = 0; v < WGJ; ++v) {
+        if (j0 + v < N) {
+          typename S::elem e;
+          S::store(&e, cfin<C>(w[v]));
+          Q[base + row * N + j0 + v] = e;
+          // the value as stored (rounded to the storage format) feeds the Gram
+          sW[row * N + j0 + v] = S::load_nc(&e);
+        }
+      }
     }
     __syncthreads();
     if (active) {

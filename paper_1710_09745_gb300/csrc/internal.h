@@ -79,6 +79,9 @@ static constexpr int DSLASH_RECON = 0x400;
 // R | DSLASH_TMA | DSLASH_RUNS: the bulk-copy kernel copies contiguous runs of
 // neighbour rows with one copy each into unpadded slots
 static constexpr int DSLASH_RUNS = 0x800;
+// R | DSLASH_BLOCKED: the plain kernel on a persistent grid whose blocks each
+// walk one contiguous range of sites (cache reuse of neighbours in L1)
+static constexpr int DSLASH_BLOCKED = 0x1000;
 cudaError_t dslash(FieldKind k, int R, int epi, const void* links, const void* in, void* out,
                    const void* c1, const void* c2, double m2, const Geom& g, int out_parity,
                    int N, Gate gate, cudaStream_t s);

@@ -14,6 +14,21 @@ namespace bcg {
 
 static constexpr int LINK_W = 32;  // sites per link block
 
+// streaming multiprocessors of the current device (looked up once)
+static int stencil_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) {
+      cudaGetLastError();
+      v = 152;
+    }
+    n = v;
+  }
+  return n;
+}
+
 // number of link blocks per parity (the last one may be partly used)
 __host__ __device__ inline long long link_blocks(const Geom& g) {
   return ((long long)g.Vh + LINK_W - 1) / LINK_W;
@@ -108,16 +123,31 @@ struct VecLoad<StoreBF16, 4> {
 #ifndef BCG_DSLASH_TPB
 #define BCG_DSLASH_TPB 128
 #endif
-#ifndef BCG_DSLASH_MINB
-#define BCG_DSLASH_MINB 1
-#endif
+
+// Resident blocks per SM requested from the compiler for the plain kernel,
+// and hop unrolling: the FP32 kernel is latency-bound on its gathers;
+// capping it at six 128-thread blocks per SM (at most 85 registers a thread)
+// without hop unrolling raised its HBM fraction at 32^4 from 0.30 to 0.34
+// (N = 16) and from 0.44 to 0.51 (N = 8) with four right-hand sides per
+// thread, and no unrolling alone from 0.27 to 0.30 (N = 16) with eight; the
+// other kinds showed no gain and keep the compiler's choice.
+template <class S, int RV>
+struct PlainBounds {
+  static constexpr int minb = 1;
+  static constexpr int unroll = 1;  // hops unrolled per direction
+};
+template <int RV>
+struct PlainBounds<StoreF32, RV> {
+  static constexpr int minb = RV == 2 ? 6 : 1;      // R = 4 (two 128-bit slots)
+  static constexpr int unroll = RV >= 2 ? 0 : 1;    // R = 8 also gains without unrolling
+};
 
 template <class S, int RV, int V, int EPI, int UNROLL_HOPS, bool RC = false>
-__global__ void __launch_bounds__(BCG_DSLASH_TPB, BCG_DSLASH_MINB)
+__global__ void __launch_bounds__(BCG_DSLASH_TPB, (PlainBounds<S, RV>::minb))
     k_dslash(const typename S::elem* __restrict__ links, const typename S::elem* __restrict__ in,
              typename S::elem* __restrict__ out, const typename S::elem* __restrict__ c1,
              const typename S::elem* __restrict__ c2, double m2d, Geom g, int parity, int N,
-             int T, Gate gate) {
+             int T, long long span, Gate gate) {
   using C = typename S::comp;
   using real = typename C::real;
   using acc = typename C::acc;
@@ -125,8 +155,14 @@ __global__ void __launch_bounds__(BCG_DSLASH_TPB, BCG_DSLASH_MINB)
   const int NS = N / V;
   const long long total = (long long)g.Vh * T;
   const real m2 = C::from_double(m2d);
-  for (long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x; gid < total;
-       gid += (long long)gridDim.x * blockDim.x) {
+  // span = 0: grid-stride over (site, slot) pairs; span > 0: this block walks
+  // the contiguous range [blockIdx.x * span, (blockIdx.x + 1) * span) in order,
+  // so that the neighbours a block reads in y (and partly z) were loaded by
+  // the same block shortly before and can still be in its SM's L1
+  const long long g0 = span ? (long long)blockIdx.x * span : (long long)blockIdx.x * blockDim.x;
+  const long long gend = span ? min(total, g0 + span) : total;
+  const long long gstep = span ? (long long)blockDim.x : (long long)gridDim.x * blockDim.x;
+  for (long long gid = g0 + threadIdx.x; gid < gend; gid += gstep) {
     const int site = (int)(gid / T);
     const int k = (int)(gid - (long long)site * T);
     int x, y, z, t;
@@ -223,163 +259,190 @@ __global__ void __launch_bounds__(BCG_DSLASH_TPB, BCG_DSLASH_MINB)
 }
 
 // ---------------------------------------------------------------------------
-// Bulk-copy pipelined stencil.  A CTA owns blocks of LINK_W = 32 consecutive
-// output sites (one link block) with T threads per site; its work is the
-// stream of (block, hop) tasks.  Warp 0 keeps STAGES - 1 hops ahead: for each
-// task it posts the expected byte count on the stage's mbarrier, copies the
-// hop's 9 x 32 link words (contiguous in the blocked link layout) with one
-// cp.async.bulk and the 32 neighbour spinor blocks (3N complex each) with one
-// cp.async.bulk per lane into the stage.  All threads wait for the stage,
-// multiply from shared memory and accumulate in registers; after hop 15 they
-// write their outputs.  Loads for later hops are in flight while a hop is
-// computed, so the kernel no longer waits on one hop's loads at a time.
+// Bulk-copy pipelined stencil (producer / consumer).  A CTA owns link blocks
+// of LINK_W = 32 consecutive output sites: T consumer warps (T threads per
+// site, R = RV * V right-hand sides each) and one producer warp.  Its work is
+// the stream of (block, hop) tasks.  For each task the producer waits until
+// the consumers have released the task's stage (empty mbarrier, one arrival
+// per consumer warp), posts the expected bytes on the stage's full mbarrier
+// and copies the hop's 9 x 32 link words (one cp.async.bulk) and the 32
+// neighbour spinor rows, one bulk copy per run of consecutive rows: for hops
+// in y, z and t the rows of 32 consecutive sites are consecutive unless the
+// hop wraps, and for x hops they form at most a few runs.  The rows land
+// unpadded (3N elements each, slot = site); a consumer thread visits its
+// right-hand-side slots in an order rotated by its site, so that the 8 lanes
+// of a quarter-warp (two or more sites) read different banks.  Consumers
+// wait on full, multiply from shared memory, release the stage and
+// accumulate in registers; after hop 15 they write their outputs.  No CTA
+// barrier inside the pipeline.
+//
 // Every wait is bounded by a watchdog deadline: Geom::wait_ns (default 4 s)
 // after the CTA started.  Once it has passed, the CTA records
 // BLOCKCG_ERR_TIMEOUT in the status word and, before it returns, waits for
-// every stage it has issued, the stage that timed out included, so that no
-// bulk copy is still writing into its shared memory when it exits.  That
-// drain has its own limit of TMA_DRAIN_LIMIT (copies of a few KB land in
-// microseconds; the limit only keeps a broken copy from hanging the kernel).
+// the last issued phase of every stage (at most one phase per stage can be
+// outstanding: the producer refills a stage only after the consumers saw its
+// previous copies land), so that no bulk copy is still writing into its
+// shared memory when it exits.  That drain has its own limit of
+// TMA_DRAIN_LIMIT (copies of a few KB land in microseconds; the limit only
+// keeps a broken copy from hanging the kernel).
 static constexpr uint64_t TMA_WAIT_LIMIT = 4000000000ull;   // 4 s of wall-clock time
 static constexpr uint64_t TMA_DRAIN_LIMIT = 4000000000ull;  // 4 s
+static constexpr int TMA_MAX_T = 8;                         // consumer warps per CTA
 
 template <class S, int RV, int V, int EPI, int STAGES>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__((TMA_MAX_T + 1) * 32)
     k_dslash_tma(const typename S::elem* __restrict__ links, const typename S::elem* __restrict__ in,
                  typename S::elem* __restrict__ out, const typename S::elem* __restrict__ c1,
                  const typename S::elem* __restrict__ c2, double m2d, Geom g, int parity, int N,
-                 int T, int sstride, int runs, Gate gate, SolverStatus* errst) {
+                 int T, Gate gate, SolverStatus* errst) {
   using E = typename S::elem;
   using C = typename S::comp;
   using real = typename C::real;
   using acc = typename C::acc;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full[STAGES];
+  __shared__ __align__(8) uint64_t empty[STAGES];
   __shared__ int abort_flag;
+  __shared__ long long sh_issued;
   if (gate_closed(gate)) return;
   const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int nconsumer = T * LINK_W;
+  const bool producer = tid >= nconsumer;
   const int NS = N / V;
-  const int sl = tid / T;  // local site
-  const int k = tid - sl * T;
+  const int row = 3 * N;  // elements per spinor row (one site, all right-hand sides)
   const int link_elems = 9 * LINK_W;
-  const int stage_elems = link_elems + LINK_W * sstride;
+  const int stage_elems = link_elems + LINK_W * row;
   E* sbase = reinterpret_cast<E*>(smem_raw);
   const long long units = link_blocks(g);
   const long long my_units =
       units > (long long)blockIdx.x ? (units - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const long long ntasks = my_units * 16;
   if (tid == 0) {
-    for (int i = 0; i < STAGES; ++i) mbar_init(&full[i], 1);
+    for (int i = 0; i < STAGES; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], T);
+    }
     abort_flag = 0;
+    sh_issued = 0;
     fence_mbar_init();
   }
   __syncthreads();
-  const uint32_t spin_bytes = 3u * N * sizeof(E);
   const uint64_t deadline =
       global_ns() + (g.wait_ns ? (uint64_t)g.wait_ns : TMA_WAIT_LIMIT);
+  const uint32_t row_bytes = (uint32_t)(row * sizeof(E));
 
-  auto issue = [&](long long task) {  // warp 0
-    const long long unit = blockIdx.x + (task >> 4) * (long long)gridDim.x;
-    const int d = (int)(task & 15);
-    const int st = (int)(task % STAGES);
-    E* base = sbase + (size_t)st * stage_elems;
-    const int lane = tid;
-    const long long site0 = unit * LINK_W;
-    const int nvalid = (int)min((long long)LINK_W, (long long)g.Vh - site0);
-    if (lane == 0)
-      mbar_arrive_expect_tx(&full[st], (uint32_t)(link_elems * sizeof(E)) + nvalid * spin_bytes);
-    __syncwarp();
-    if (lane == 0)
-      bulk_g2s(base, links + link_offset(g, parity, (int)site0) + d * 9 * LINK_W,
-               (uint32_t)(link_elems * sizeof(E)), &full[st]);
-    int nb = 0;
-    if (lane < nvalid) {
-      int x, y, z, t;
-      const int site = (int)site0 + lane;
-      site_xyzt(g, site, parity, x, y, z, t);
-      const int lex = x + g.L[0] * (y + g.L[1] * (z + g.L[2] * t));
-      nb = neighbour_cb_s(g, lex, x, y, z, t, d >> 2, hop_k(d & 3));
-    }
-    if (!runs) {
-      if (lane < nvalid)
-        bulk_g2s(base + link_elems + lane * sstride, in + (long long)nb * N * 3, spin_bytes, &full[st]);
-    } else {
-      // contiguous runs of neighbour rows (slots are unpadded, sstride = 3N):
-      // one bulk copy per run instead of one per site
+  if (producer) {
+    long long q = 0;
+    for (; q < ntasks; ++q) {
+      const int st = (int)(q % STAGES);
+      if (q >= STAGES) {
+        int ok = 1;
+        if (lane == 0)
+          ok = mbar_wait_until(&empty[st], (uint32_t)(((q / STAGES) - 1) & 1), deadline) ? 1 : 0;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok || *(volatile int*)&abort_flag) {
+          if (lane == 0) abort_flag = 1;
+          break;
+        }
+      }
+      const long long unit = blockIdx.x + (q >> 4) * (long long)gridDim.x;
+      const int d = (int)(q & 15);
+      E* base = sbase + (size_t)st * stage_elems;
+      const long long site0 = unit * LINK_W;
+      const int nvalid = (int)min((long long)LINK_W, (long long)g.Vh - site0);
+      int nb = 0;
+      if (lane < nvalid) {
+        int x, y, z, t;
+        site_xyzt(g, (int)site0 + lane, parity, x, y, z, t);
+        const int lex = x + g.L[0] * (y + g.L[1] * (z + g.L[2] * t));
+        nb = neighbour_cb_s(g, lex, x, y, z, t, d >> 2, hop_k(d & 3));
+      }
       const int prev = __shfl_up_sync(0xffffffffu, nb, 1);
       const bool start = lane < nvalid && (lane == 0 || nb != prev + 1);
       const unsigned m = __ballot_sync(0xffffffffu, start);
+      if (lane == 0)
+        mbar_arrive_expect_tx(&full[st], (uint32_t)(link_elems * sizeof(E)) + nvalid * row_bytes);
+      __syncwarp();
+      if (lane == 0)
+        bulk_g2s(base, links + link_offset(g, parity, (int)site0) + d * 9 * LINK_W,
+                 (uint32_t)(link_elems * sizeof(E)), &full[st]);
       if (start) {
         const unsigned higher = m & ~((2u << lane) - 1u);
         const int next = higher ? __ffs(higher) - 1 : nvalid;
-        bulk_g2s(base + link_elems + lane * sstride, in + (long long)nb * N * 3,
-                 (uint32_t)(next - lane) * spin_bytes, &full[st]);
+        bulk_g2s(base + link_elems + lane * row, in + (long long)nb * row,
+                 (uint32_t)(next - lane) * row_bytes, &full[st]);
       }
     }
-  };
-
-  long long issued = 0;
-  if (tid < 32) {
-    for (; issued < STAGES - 1 && issued < ntasks; ++issued) issue(issued);
-  }
-  const real m2 = C::from_double(m2d);
-  cpx<acc> a[RV][V][3];
-  const int nr = (NS - k + T - 1) / T;  // slots k + r*T < NS
-  long long tau = 0;
-  for (; tau < ntasks; ++tau) {
-    if (tid < 32 && tau + STAGES - 1 < ntasks) {
-      issue(tau + STAGES - 1);
-    }
-    if (tid < 32) issued = min(ntasks, tau + STAGES);
-    const int d = (int)(tau & 15);
-    const int st = (int)(tau % STAGES);
-    const long long unit = blockIdx.x + (tau >> 4) * (long long)gridDim.x;
-    const long long site = unit * LINK_W + sl;
-    const bool valid = site < g.Vh && sl < LINK_W;
-    if (d == 0) {
+    if (lane == 0) sh_issued = q;
+  } else {
+    const int warp = tid >> 5;
+    (void)warp;
+    const int sl = tid / T;  // local site
+    const int k = tid - sl * T;
+    const int nr = (NS - k + T - 1) / T;  // valid slots: slot index < nr
+    const real m2 = C::from_double(m2d);
+    cpx<acc> a[RV][V][3];
+    for (long long tau = 0; tau < ntasks; ++tau) {
+      const int d = (int)(tau & 15);
+      const int st = (int)(tau % STAGES);
+      if (d == 0) {
 #pragma unroll
-      for (int r = 0; r < RV; ++r)
-#pragma unroll
-        for (int w = 0; w < V; ++w)
-#pragma unroll
-          for (int i = 0; i < 3; ++i) a[r][w][i] = czero<C>();
-    }
-    if (!mbar_wait_until(&full[st], (uint32_t)((tau / STAGES) & 1), deadline)) {
-      abort_flag = 1;
-    } else if (valid) {
-      const E* base = sbase + (size_t)st * stage_elems;
-      cpx<real> U[9];
-#pragma unroll
-      for (int e = 0; e < 9; ++e) U[e] = S::load_nc(base + e * LINK_W + sl);
-      const E* ip = base + link_elems + sl * sstride + k * V;
-#pragma unroll
-      for (int r = 0; r < RV; ++r) {
-        if (r < nr) {
-          cpx<real> v[3][V];
-#pragma unroll
-          for (int b = 0; b < 3; ++b)
-#pragma unroll
-            for (int w = 0; w < V; ++w) v[b][w] = S::load_nc(ip + b * N + r * T * V + w);
+        for (int r = 0; r < RV; ++r)
 #pragma unroll
           for (int w = 0; w < V; ++w)
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-              cmac<C>(a[r][w][i], U[i * 3 + 0], v[0][w]);
-              cmac<C>(a[r][w][i], U[i * 3 + 1], v[1][w]);
-              cmac<C>(a[r][w][i], U[i * 3 + 2], v[2][w]);
-            }
-        }
+            for (int i = 0; i < 3; ++i) a[r][w][i] = czero<C>();
       }
-      if (d == 15) {
-        const long long ob = site * N * 3 + k * V;
+      const bool ok = mbar_wait_until(&full[st], (uint32_t)((tau / STAGES) & 1), deadline);
+      if (!__all_sync(0xffffffffu, ok)) {
+        if (lane == 0) abort_flag = 1;
+        break;
+      }
+      const long long unit = blockIdx.x + (tau >> 4) * (long long)gridDim.x;
+      const long long site = unit * LINK_W + sl;
+      const bool valid = site < g.Vh;
+      const E* base = sbase + (size_t)st * stage_elems;
+      if (valid) {
+        cpx<real> U[9];
+#pragma unroll
+        for (int e = 0; e < 9; ++e) U[e] = S::load_nc(base + e * LINK_W + sl);
+        const E* ip = base + link_elems + sl * row + k * V;
 #pragma unroll
         for (int r = 0; r < RV; ++r) {
-          if (r < nr) {
+          const int sr = (r + sl) & (RV - 1);  // rotated slot: quarter-warp lanes hit distinct banks
+          if (sr < nr) {
+            cpx<real> v[3][V];
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+#pragma unroll
+              for (int w = 0; w < V; ++w) v[b][w] = S::load_nc(ip + b * N + sr * T * V + w);
 #pragma unroll
             for (int w = 0; w < V; ++w)
 #pragma unroll
               for (int i = 0; i < 3; ++i) {
-                const long long oi = ob + i * N + r * T * V + w;
+                cmac<C>(a[r][w][i], U[i * 3 + 0], v[0][w]);
+                cmac<C>(a[r][w][i], U[i * 3 + 1], v[1][w]);
+                cmac<C>(a[r][w][i], U[i * 3 + 2], v[2][w]);
+              }
+          }
+        }
+      }
+      // release the stage to the producer (its next copies into it are async-proxy writes)
+      fence_proxy_async_shared();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[st]);
+      if (d == 15 && valid) {
+        const long long ob = site * N * 3 + k * V;
+#pragma unroll
+        for (int r = 0; r < RV; ++r) {
+          const int sr = (r + sl) & (RV - 1);
+          if (sr < nr) {
+#pragma unroll
+            for (int w = 0; w < V; ++w)
+#pragma unroll
+              for (int i = 0; i < 3; ++i) {
+                const long long oi = ob + i * N + sr * T * V + w;
                 cpx<acc> vv = a[r][w][i];
                 if (EPI != EPI_NONE) {
                   C::neg(vv.re);
@@ -401,20 +464,100 @@ __global__ void __launch_bounds__(256)
         }
       }
     }
-    fence_proxy_async_shared();
-    __syncthreads();
-    if (abort_flag) break;
   }
+  __syncthreads();
   if (abort_flag) {
-    // record the failure, then wait for every stage issued and not yet
-    // consumed: tau (the one whose wait gave up) up to issued - 1.  Each of
-    // these STAGES at most distinct stages has exactly one phase pending.
+    // record the failure, then wait for the last issued phase of every stage
     if (tid == 0) {
       if (errst) atomicExch(&errst->error, (int)7 /* BLOCKCG_ERR_TIMEOUT */);
-      for (long long q = tau; q < issued; ++q)
-        mbar_wait_bounded(&full[q % STAGES], (uint32_t)((q / STAGES) & 1), TMA_DRAIN_LIMIT);
+      const long long issued = sh_issued;
+      for (long long q = issued - STAGES; q < issued; ++q)
+        if (q >= 0)
+          mbar_wait_bounded(&full[q % STAGES], (uint32_t)((q / STAGES) & 1), TMA_DRAIN_LIMIT);
     }
     __syncthreads();
+  }
+}
+
+template <class S, int RV, int V, int EPI, int STAGES>
+static bool launch_tma_t(const void* links, const void* in, void* out, const void* c1,
+                         const void* c2, double m2, const Geom& g, int parity, int N, Gate gate,
+                         SolverStatus* errst, cudaStream_t s) {
+  using E = typename S::elem;
+  const size_t eb = sizeof(E);
+  const int NS = N / V;
+  const int T = (NS + RV - 1) / RV;
+  if (T > TMA_MAX_T) return false;
+  if ((3 * N * eb) % 16) return false;                // rows must be 16-byte multiples
+  if (RV & (RV - 1)) return false;                    // slot rotation needs a power of two
+  const size_t stage_bytes = (9 * LINK_W + (size_t)LINK_W * 3 * N) * eb;
+  const size_t sm = STAGES * stage_bytes;
+  if (sm > 200 * 1024) return false;
+  auto kern = k_dslash_tma<S, RV, V, EPI, STAGES>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+    return false;
+  const int threads = T * LINK_W + 32;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, sm) != cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    return false;
+  }
+  const long long units = link_blocks(g);
+  const long long want = (long long)stencil_sms() * per_sm;
+  unsigned blocks = (unsigned)(units < want ? units : want);
+  kern<<<blocks, threads, sm, s>>>((const E*)links, (const E*)in, (E*)out, (const E*)c1,
+                                   (const E*)c2, m2, g, parity, N, T, gate, errst);
+  return true;
+}
+
+template <class S, int RV, int V>
+static bool launch_tma_r(int epi, const void* links, const void* in, void* out, const void* c1,
+                         const void* c2, double m2, const Geom& g, int parity, int N, Gate gate,
+                         SolverStatus* errst, cudaStream_t s) {
+  // four stages when they fit, else three, else two
+  switch (epi) {
+    case EPI_NONE:
+      return launch_tma_t<S, RV, V, EPI_NONE, 4>(links, in, out, c1, c2, m2, g, parity, N, gate, errst, s) ||
+             launch_tma_t<S, RV, V, EPI_NONE, 3>(links, in, out, c1, c2, m2, g, parity, N, gate, errst, s) ||
+             launch_tma_t<S, RV, V, EPI_NONE, 2>(links, in, out, c1, c2, m2, g, parity, N, gate, errst, s);
+    case EPI_NORMAL:
+      return launch_tma_t<S, RV, V, EPI_NORMAL, 4>(links, in, out, c1, c2, m2, g, parity, N, gate, errst, s) ||
+             launch_tma_t<S, RV, V, EPI_NORMAL, 3>(links, in, out, c1, c2, m2, g, parity, N, gate, errst, s) ||
+             launch_tma_t<S, RV, V, EPI_NORMAL, 2>(links, in, out, c1, c2, m2, g, parity, N, gate, errst, s);
+    default:
+      return launch_tma_t<S, RV, V, EPI_RESIDUAL, 4>(links, in, out, c1, c2, m2, g, parity, N, gate, errst, s) ||
+             launch_tma_t<S, RV, V, EPI_RESIDUAL, 3>(links, in, out, c1, c2, m2, g, parity, N, gate, errst, s) ||
+             launch_tma_t<S, RV, V, EPI_RESIDUAL, 2>(links, in, out, c1, c2, m2, g, parity, N, gate, errst, s);
+  }
+}
+
+template <class S>
+static bool launch_tma_s(int R, int epi, const void* links, const void* in, void* out,
+                     const void* c1, const void* c2, double m2, const Geom& g, int parity,
+                     int N, Gate gate, SolverStatus* errst, cudaStream_t s) {
+  // vector width V: complex numbers per load (FP32: 2 per 128 bits; 16-bit
+  // kinds: 4 per 128 bits or 2 per 64 bits); RV = R / V slots per thread
+  constexpr bool F32 = std::is_same<S, StoreF32>::value;
+  constexpr bool H = std::is_same<S, StoreH16>::value || std::is_same<S, StoreBF16>::value;
+  constexpr int V2 = (F32 || H) ? 2 : 1;
+  constexpr int V4 = H ? 4 : 1;
+  if (H && (N % 4) == 0 && R >= 4) {
+    if (R == 4) return launch_tma_r<S, 1, V4>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, errst, s);
+    return launch_tma_r<S, 2, V4>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, errst, s);
+  }
+  if ((F32 || H) && (N % 2) == 0 && R >= 2) {
+    switch (R) {
+      case 2: return launch_tma_r<S, 1, V2>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, errst, s);
+      case 4: return launch_tma_r<S, 2, V2>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, errst, s);
+      default: return launch_tma_r<S, 4, V2>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, errst, s);
+    }
+  }
+  switch (R) {
+    case 1: return launch_tma_r<S, 1, 1>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, errst, s);
+    case 2: return launch_tma_r<S, 2, 1>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, errst, s);
+    case 4: return launch_tma_r<S, 4, 1>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, errst, s);
+    default: return launch_tma_r<S, 8, 1>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, errst, s);
   }
 }
 
@@ -615,130 +758,57 @@ static bool launch_async_s(int R, int epi, const void* links, const void* in, vo
   }
 }
 
-// smem site stride (elements): 3N padded so that consecutive sites start 16
-// banks apart, and a multiple of 16 bytes
-static int tma_site_stride(size_t eb, int N) {
-  const int wpe = (int)(eb / 4);
-  for (int p = 0; p < 64; ++p) {
-    int s = 3 * N + p;
-    if ((s * eb) % 16) continue;
-    if (((s * wpe) % 32) == 16) return s;
-  }
-  return 3 * N + (eb == 8 ? ((3 * N) & 1) : 0);
-}
-
-template <class S, int RV, int V, int EPI, int STAGES>
-static bool launch_tma_t(const void* links, const void* in, void* out, const void* c1,
-                         const void* c2, double m2, const Geom& g, int parity, int N, Gate gate,
-                         SolverStatus* errst, int runs, cudaStream_t s) {
-  using E = typename S::elem;
-  const size_t eb = sizeof(E);
-  const int NS = N / V;
-  const int T = (NS + RV - 1) / RV;
-  if (T * LINK_W > 256) return false;
-  if ((3 * N * eb) % 16) return false;
-  const int sstride = runs ? 3 * N : tma_site_stride(eb, N);
-  const size_t stage_bytes = (9 * LINK_W + (size_t)LINK_W * sstride) * eb;
-  const size_t sm = STAGES * stage_bytes;
-  if (sm > 200 * 1024) return false;
-  auto kern = k_dslash_tma<S, RV, V, EPI, STAGES>;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
-    return false;
-  long long units = link_blocks(g);
-  int per_sm = (int)((220 * 1024) / (sm + 1024));
-  if (per_sm < 1) per_sm = 1;
-  if (per_sm > 8) per_sm = 8;
-  long long want = 152LL * per_sm;
-  unsigned blocks = (unsigned)(units < want ? units : want);
-  kern<<<blocks, T * LINK_W, sm, s>>>((const E*)links, (const E*)in, (E*)out, (const E*)c1,
-                                      (const E*)c2, m2, g, parity, N, T, sstride, runs, gate,
-                                      errst);
-  return true;
-}
-
-template <class S, int RV, int V>
-static bool launch_tma_r(int epi, const void* links, const void* in, void* out, const void* c1,
-                         const void* c2, double m2, const Geom& g, int parity, int N, Gate gate,
-                         SolverStatus* errst, int runs, cudaStream_t s) {
-  // three stages when they fit, else two
-  switch (epi) {
-    case EPI_NONE:
-      return launch_tma_t<S, RV, V, EPI_NONE, 3>(links, in, out, c1, c2, m2, g, parity, N, gate, errst, runs, s) ||
-             launch_tma_t<S, RV, V, EPI_NONE, 2>(links, in, out, c1, c2, m2, g, parity, N, gate, errst, runs, s);
-    case EPI_NORMAL:
-      return launch_tma_t<S, RV, V, EPI_NORMAL, 3>(links, in, out, c1, c2, m2, g, parity, N, gate, errst, runs, s) ||
-             launch_tma_t<S, RV, V, EPI_NORMAL, 2>(links, in, out, c1, c2, m2, g, parity, N, gate, errst, runs, s);
-    default:
-      return launch_tma_t<S, RV, V, EPI_RESIDUAL, 3>(links, in, out, c1, c2, m2, g, parity, N, gate, errst, runs, s) ||
-             launch_tma_t<S, RV, V, EPI_RESIDUAL, 2>(links, in, out, c1, c2, m2, g, parity, N, gate, errst, runs, s);
-  }
-}
-
-template <class S>
-static bool launch_tma_s(int R, int epi, const void* links, const void* in, void* out,
-                     const void* c1, const void* c2, double m2, const Geom& g, int parity,
-                     int N, Gate gate, SolverStatus* errst, int runs, cudaStream_t s) {
-  // vector width V: complex numbers per load (FP32: 2 per 128 bits; 16-bit
-  // kinds: 4 per 128 bits or 2 per 64 bits); RV = R / V slots per thread
-  constexpr bool F32 = std::is_same<S, StoreF32>::value;
-  constexpr bool H = std::is_same<S, StoreH16>::value || std::is_same<S, StoreBF16>::value;
-  constexpr int V2 = (F32 || H) ? 2 : 1;
-  constexpr int V4 = H ? 4 : 1;
-  if (H && (N % 4) == 0 && R >= 4) {
-    if (R == 4) return launch_tma_r<S, 1, V4>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, errst, runs, s);
-    return launch_tma_r<S, 2, V4>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, errst, runs, s);
-  }
-  if ((F32 || H) && (N % 2) == 0 && R >= 2) {
-    switch (R) {
-      case 2: return launch_tma_r<S, 1, V2>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, errst, runs, s);
-      case 4: return launch_tma_r<S, 2, V2>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, errst, runs, s);
-      default: return launch_tma_r<S, 4, V2>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, errst, runs, s);
-    }
-  }
-  switch (R) {
-    case 1: return launch_tma_r<S, 1, 1>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, errst, runs, s);
-    case 2: return launch_tma_r<S, 2, 1>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, errst, runs, s);
-    case 4: return launch_tma_r<S, 4, 1>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, errst, runs, s);
-    default: return launch_tma_r<S, 8, 1>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, errst, runs, s);
-  }
-}
-
 
 template <class S, int RV, int V, int EPI, bool RC = false>
 static void launch_dslash_t(const void* links, const void* in, void* out, const void* c1,
                             const void* c2, double m2, const Geom& g, int parity, int N,
-                            Gate gate, cudaStream_t s) {
+                            Gate gate, bool blocked, cudaStream_t s) {
   using E = typename S::elem;
-#ifndef BCG_UNROLL_F32
-#define BCG_UNROLL_F32 1
-#endif
 #ifndef BCG_UNROLL_DF
 #define BCG_UNROLL_DF 0
 #endif
-  constexpr int UNROLL = std::is_same<S, StoreDF>::value ? BCG_UNROLL_DF : BCG_UNROLL_F32;
+  constexpr int UNROLL =
+      std::is_same<S, StoreDF>::value ? BCG_UNROLL_DF : PlainBounds<S, RV>::unroll;
   const int NS = N / V;
   int T = (NS + RV - 1) / RV;
   long long threads_total = (long long)g.Vh * T;
   int threads = BCG_DSLASH_TPB;
   long long want = (threads_total + threads - 1) / threads;
   unsigned blocks = (unsigned)(want < 152 * 32 ? want : 152 * 32);
+  long long span = 0;
+  if (blocked) {
+    // a persistent grid of the resident blocks, each owning one contiguous
+    // range of (site, slot) pairs, a whole number of blocks of threads long
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dslash<S, RV, V, EPI, UNROLL, RC>,
+                                                      threads, 0) != cudaSuccess || per_sm < 1) {
+      cudaGetLastError();
+      per_sm = 1;
+    }
+    long long nb = (long long)stencil_sms() * per_sm;
+    if (nb > want) nb = want;
+    const long long per = (want + nb - 1) / nb;  // thread blocks' worth of pairs per CTA
+    span = per * threads;
+    blocks = (unsigned)((threads_total + span - 1) / span);
+  }
   k_dslash<S, RV, V, EPI, UNROLL, RC><<<blocks, threads, 0, s>>>(
-      (const E*)links, (const E*)in, (E*)out, (const E*)c1, (const E*)c2, m2, g, parity, N, T, gate);
+      (const E*)links, (const E*)in, (E*)out, (const E*)c1, (const E*)c2, m2, g, parity, N, T, span,
+      gate);
 }
 
 template <class S, int RV, int V, bool RC = false>
 static void launch_dslash_r(int epi, const void* links, const void* in, void* out, const void* c1,
                             const void* c2, double m2, const Geom& g, int parity, int N,
-                            Gate gate, cudaStream_t s) {
+                            Gate gate, bool blocked, cudaStream_t s) {
   switch (epi) {
     case EPI_NONE:
-      launch_dslash_t<S, RV, V, EPI_NONE, RC>(links, in, out, c1, c2, m2, g, parity, N, gate, s);
+      launch_dslash_t<S, RV, V, EPI_NONE, RC>(links, in, out, c1, c2, m2, g, parity, N, gate, blocked, s);
       break;
     case EPI_NORMAL:
-      launch_dslash_t<S, RV, V, EPI_NORMAL, RC>(links, in, out, c1, c2, m2, g, parity, N, gate, s);
+      launch_dslash_t<S, RV, V, EPI_NORMAL, RC>(links, in, out, c1, c2, m2, g, parity, N, gate, blocked, s);
       break;
     default:
-      launch_dslash_t<S, RV, V, EPI_RESIDUAL, RC>(links, in, out, c1, c2, m2, g, parity, N, gate, s);
+      launch_dslash_t<S, RV, V, EPI_RESIDUAL, RC>(links, in, out, c1, c2, m2, g, parity, N, gate, blocked, s);
       break;
   }
 }
@@ -748,7 +818,7 @@ static void launch_dslash_r(int epi, const void* links, const void* in, void* ou
 template <class S, bool RC = false>
 static void launch_dslash_s(int R, int epi, const void* links, const void* in, void* out,
                      const void* c1, const void* c2, double m2, const Geom& g, int parity,
-                     int N, Gate gate, cudaStream_t s) {
+                     int N, Gate gate, bool blocked, cudaStream_t s) {
   // vector width V: complex numbers per load (FP32: 2 per 128 bits; 16-bit
   // kinds: 4 per 128 bits or 2 per 64 bits); RV = R / V slots per thread
   constexpr bool F32 = std::is_same<S, StoreF32>::value;
@@ -756,21 +826,21 @@ static void launch_dslash_s(int R, int epi, const void* links, const void* in, v
   constexpr int V2 = (F32 || H) ? 2 : 1;
   constexpr int V4 = H ? 4 : 1;
   if (H && (N % 4) == 0 && R >= 4) {
-    if (R == 4) return launch_dslash_r<S, 1, V4, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, s);
-    return launch_dslash_r<S, 2, V4, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, s);
+    if (R == 4) return launch_dslash_r<S, 1, V4, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, blocked, s);
+    return launch_dslash_r<S, 2, V4, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, blocked, s);
   }
   if ((F32 || H) && (N % 2) == 0 && R >= 2) {
     switch (R) {
-      case 2: return launch_dslash_r<S, 1, V2, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, s);
-      case 4: return launch_dslash_r<S, 2, V2, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, s);
-      default: return launch_dslash_r<S, 4, V2, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, s);
+      case 2: return launch_dslash_r<S, 1, V2, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, blocked, s);
+      case 4: return launch_dslash_r<S, 2, V2, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, blocked, s);
+      default: return launch_dslash_r<S, 4, V2, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, blocked, s);
     }
   }
   switch (R) {
-    case 1: return launch_dslash_r<S, 1, 1, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, s);
-    case 2: return launch_dslash_r<S, 2, 1, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, s);
-    case 4: return launch_dslash_r<S, 4, 1, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, s);
-    default: return launch_dslash_r<S, 8, 1, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, s);
+    case 1: return launch_dslash_r<S, 1, 1, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, blocked, s);
+    case 2: return launch_dslash_r<S, 2, 1, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, blocked, s);
+    case 4: return launch_dslash_r<S, 4, 1, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, blocked, s);
+    default: return launch_dslash_r<S, 8, 1, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, blocked, s);
   }
 }
 
@@ -784,7 +854,8 @@ static cudaError_t dslash_kind(int R, int epi, const void* links, const void* in
                                int out_parity, int N, Gate gate, cudaStream_t s) {
   if (R & DSLASH_RECON) {  // two-row links: plain kernel, 32- and 16-bit kinds only
     if constexpr (std::is_same<typename S::comp::real, float>::value) {
-      launch_dslash_s<S, true>(R & 0xff, epi, links, in, out, c1, c2, m2, g, out_parity, N, gate, s);
+      launch_dslash_s<S, true>(R & 0xff, epi, links, in, out, c1, c2, m2, g, out_parity, N, gate,
+                               (R & DSLASH_BLOCKED) != 0, s);
       return cudaGetLastError();
     } else {
       return cudaErrorInvalidValue;
@@ -800,13 +871,13 @@ static cudaError_t dslash_kind(int R, int epi, const void* links, const void* in
   if (R & DSLASH_TMA) {
     const int r = R & 0xff;
     SolverStatus* errst = const_cast<SolverStatus*>(gate.st);
-    if (launch_tma_s<S>(r, epi, links, in, out, c1, c2, m2, g, out_parity, N, gate, errst,
-                        (R & DSLASH_RUNS) ? 1 : 0, s))
+    if (launch_tma_s<S>(r, epi, links, in, out, c1, c2, m2, g, out_parity, N, gate, errst, s))
       return cudaGetLastError();
     cudaGetLastError();
     R = r;
   }
-  launch_dslash_s<S>(R, epi, links, in, out, c1, c2, m2, g, out_parity, N, gate, s);
+  launch_dslash_s<S>(R & 0xff, epi, links, in, out, c1, c2, m2, g, out_parity, N, gate,
+                     (R & DSLASH_BLOCKED) != 0, s);
   return cudaGetLastError();
 }
 

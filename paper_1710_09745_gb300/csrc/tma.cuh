@@ -27,6 +27,11 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                : "memory");
 }
 
+// one plain arrival (no transaction bytes)
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // bytes (a multiple of 16) from global src to shared dst (both 16-byte
 // aligned); completion is reported to bar as transaction bytes
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
