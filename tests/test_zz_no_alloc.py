@@ -81,6 +81,8 @@ def test_noalloc_cdot_allocates_nothing():
                                               N, X.shape[1], ct.c_void_p(K.data_ptr()),
                                               ct.c_void_p(stream.cuda_stream))
     assert call() == 0
+    import gc
+    gc.collect()  # tensors left by earlier tests are freed now, not during the measurement
     torch.cuda.synchronize()
     alloc0 = torch.cuda.memory_allocated()
     free0, _ = torch.cuda.mem_get_info()
@@ -88,7 +90,7 @@ def test_noalloc_cdot_allocates_nothing():
         assert call() == 0
     torch.cuda.synchronize()
     free1, _ = torch.cuda.mem_get_info()
-    assert torch.cuda.memory_allocated() == alloc0
+    assert torch.cuda.memory_allocated() <= alloc0
     assert free1 >= free0
     Kref = oblock.block_cdot(oblock.as_columns(X.cpu().numpy()), oblock.as_columns(Y.cpu().numpy()))
     assert np.abs(K.cpu().numpy() - Kref).max() < 1e-9
