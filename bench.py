@@ -67,7 +67,7 @@ def parse_args():
                     help="only the differentiable-solve leg (16^4, N = 8)")
     ap.add_argument("--legs", nargs="*", default=None,
                     help="run only these context legs (cg f64_native mixed dslash width "
-                         "fine_tol config3 batched autograd cpu)")
+                         "fine_tol many config3 batched autograd cpu)")
     return ap.parse_args()
 
 
@@ -648,6 +648,22 @@ def main():
                                  "true_rel_res_max": iN["true_rel_res_max"]}
             out["block_width"] = width
 
+        def many_leg():
+            # 64 right-hand sides in blocks whose width the library picks by
+            # timing its first blocks (blockcg_solve_many), F64 form
+            import hisq_inputs as hi
+            b64 = torch.as_tensor(hi.gaussian_sources(dims, 64, SRC_SEED + 7)).to(dev)
+            sM = BlockCG(dims, fat, lng, a.mass, prec=a.prec, max_rhs=32, device=dev)
+            _, im = sM.solve_many(b64, tol=a.tol)
+            out["solve_many"] = {
+                "workload": f"{'x'.join(map(str, dims))} m={a.mass} 64 RHS {a.prec} to {a.tol:g}",
+                "chosen_width": im["width"], "from_cache": im["from_cache"],
+                "candidates_ms_per_rhs": {str(k): v for k, v in im["candidates"].items()},
+                "blocks": im["blocks"], "ms_per_rhs": im["ms_total"] / 64,
+                "true_rel_res_max": im["true_rel_res_max"], "status": im["status"]}
+            del sM, b64
+            free_cuda()
+
         def fine_tol_leg():
             # the F64 form at the paper's fine tolerance, for the solution error
             # against the oracle (column 0; the oracle solves to the same 1e-12)
@@ -737,6 +753,7 @@ def main():
         free_cuda()
         leg("width", width_leg)
         leg("fine_tol", fine_tol_leg)
+        leg("many", many_leg)
         leg("config3", config3_leg)
         leg("batched", lambda: out.__setitem__("batched", batched_leg(a.tol, dev)))
         leg("autograd", lambda: out.__setitem__("autograd", autograd_leg(dev)))

@@ -401,38 +401,55 @@ __global__ void __launch_bounds__(GRAM_THREADS)
       sA[idx] = S::load(AP + base + idx);
     }
     __syncthreads();
-    // W = Q - AP beta: a thread owns WGJ consecutive columns of one row, so
-    // each AP value read from shared memory feeds WGJ multiply-adds
+    // W = Q - AP beta: a thread owns WR rows x WGJ consecutive columns, so
+    // each beta value read from shared memory feeds WR multiply-adds and each
+    // AP value WGJ of them (WR = 2 for the FP32-arithmetic kinds, whose
+    // multiply-adds are cheap enough that shared-memory reads would bound them)
+    constexpr int WR = std::is_same<real, float>::value ? 2 : 1;
     const int ng = (N + WGJ - 1) / WGJ;
-    for (int u = tid; u < ns * 3 * ng; u += GRAM_THREADS) {
-      const int row = u / ng, j0 = (u - row * ng) * WGJ;
-      const cpx<real>* apr = sA + row * N;
-      cpx<acc> w[WGJ];
+    const int nrg = (ns * 3 + WR - 1) / WR;
+    for (int u = tid; u < nrg * ng; u += GRAM_THREADS) {
+      const int rg = u / ng, j0 = (u - rg * ng) * WGJ;
+      cpx<acc> w[WR][WGJ];
 #pragma unroll
-      for (int v = 0; v < WGJ; ++v)
-        w[v] = (j0 + v < N) ? cacc_from<C>(sW[row * N + j0 + v]) : czero<C>();
+      for (int rr = 0; rr < WR; ++rr) {
+        const int row = rg * WR + rr;
+#pragma unroll
+        for (int v = 0; v < WGJ; ++v)
+          w[rr][v] = (row < ns * 3 && j0 + v < N) ? cacc_from<C>(sW[row * N + j0 + v]) : czero<C>();
+      }
       for (int i = 0; i < N; ++i) {
-        const cpx<real> ap = apr[i];
+        cpx<real> bb[WGJ];
 #pragma unroll
-        for (int v = 0; v < WGJ; ++v) {
-          if (j0 + v < N) {
-            const cpx<real> bb = sb[i * N + j0 + v];
+        for (int v = 0; v < WGJ; ++v)
+          bb[v] = (j0 + v < N) ? sb[i * N + j0 + v] : cpx<real>{C::rzero(), C::rzero()};
+#pragma unroll
+        for (int rr = 0; rr < WR; ++rr) {
+          const int row = min(rg * WR + rr, ns * 3 - 1);  // a ragged group repeats a row
+          const cpx<real> ap = sA[row * N + i];
+#pragma unroll
+          for (int v = 0; v < WGJ; ++v) {
             // w -= ap * bb
-            C::msub(w[v].re, ap.re, bb.re);
-            C::mac(w[v].re, ap.im, bb.im);
-            C::msub(w[v].im, ap.re, bb.im);
-            C::msub(w[v].im, ap.im, bb.re);
+            C::msub(w[rr][v].re, ap.re, bb[v].re);
+            C::mac(w[rr][v].re, ap.im, bb[v].im);
+            C::msub(w[rr][v].im, ap.re, bb[v].im);
+            C::msub(w[rr][v].im, ap.im, bb[v].re);
           }
         }
       }
 #pragma unroll
-      for (int v = 0; v < WGJ; ++v) {
-        if (j0 + v < N) {
-          typename S::elem e;
-          S::store(&e, cfin<C>(w[v]));
-          Q[base + row * N + j0 + v] = e;
-          // the value as stored (rounded to the storage format) feeds the Gram
-          sW[row * N + j0 + v] = S::load_nc(&e);
+      for (int rr = 0; rr < WR; ++rr) {
+        const int row = rg * WR + rr;
+        if (row >= ns * 3) continue;
+#pragma unroll
+        for (int v = 0; v < WGJ; ++v) {
+          if (j0 + v < N) {
+            typename S::elem e;
+            S::store(&e, cfin<C>(w[rr][v]));
+            Q[base + row * N + j0 + v] = e;
+            // the value as stored (rounded to the storage format) feeds the Gram
+            sW[row * N + j0 + v] = S::load_nc(&e);
+          }
         }
       }
     }
@@ -566,7 +583,7 @@ struct UpdTile<SS, true> {
 __host__ __device__ inline size_t upd_wp_bytes(int TS, int N, size_t tile_elem) {
   return (2 * (size_t)TS * 3 * (N + 1) * tile_elem + 15) / 16 * 16;
 }
-template <class SS, class XS, int JB, bool DB>
+template <class SS, class XS, int JB, bool DB, int RT>
 __global__ void __launch_bounds__(256, 3)
     k_bcg_update(typename SS::elem* __restrict__ Q, typename SS::elem* __restrict__ P,
                  typename XS::elem* __restrict__ X, const double2* __restrict__ Sinv,
@@ -659,22 +676,33 @@ __global__ void __launch_bounds__(256, 3)
       __syncthreads();
       const int ng = (jn + JB - 1) / JB;  // column groups
       const int nrows = ns * 3;
-      const int nout = nrows * ng;
+      const int nrg = (nrows + RT - 1) / RT;  // groups of RT rows
+      const int nout = nrg * ng;
       // column group major: the lanes of a warp share the group (and hence
-      // the triangular loop bounds) and differ only in the row
+      // the triangular loop bounds) and differ only in the rows.  A thread
+      // owns RT rows x JB columns, so every coefficient read from shared
+      // memory feeds RT multiply-adds and every W, P value JB of them.
       for (int o = threadIdx.x; o < nout; o += blockDim.x) {
-        const int jg = o / nrows;
-        const int row = o - jg * nrows;  // (site, colour)
+        const int jg = o / nrg;
+        const int row0 = (o - jg * nrg) * RT;  // first (site, colour) row
         const int jj0 = jg * JB;
-        const TT* w = sW + row * RS;
-        const TT* p = sP + row * RS;
-        cpx<acc> q[JB], x[JB], pn[JB];
+        const TT* w[RT];
+        const TT* p[RT];
 #pragma unroll
-        for (int u = 0; u < JB; ++u) {
-          q[u] = czero<C>();
-          x[u] = czero<C>();
-          pn[u] = czero<C>();
+        for (int rr = 0; rr < RT; ++rr) {
+          const int row = (row0 + rr < nrows) ? row0 + rr : row0;  // a ragged group repeats a row
+          w[rr] = sW + row * RS;
+          p[rr] = sP + row * RS;
         }
+        cpx<acc> q[RT][JB], x[RT][JB], pn[RT][JB];
+#pragma unroll
+        for (int rr = 0; rr < RT; ++rr)
+#pragma unroll
+          for (int u = 0; u < JB; ++u) {
+            q[rr][u] = czero<C>();
+            x[rr][u] = czero<C>();
+            pn[rr][u] = czero<C>();
+          }
         // i ranges: [0, jlo) feeds Q and X of every column of the group;
         // [jlo, jlo + JB) is the diagonal band (per-column conditions);
         // [jlo + JB, N) feeds X and P S^dag of every column
@@ -683,83 +711,113 @@ __global__ void __launch_bounds__(256, 3)
         const int i_band_end = min(N, jlo + JB);
         if (full) {
           for (int i = 0; i < jlo; ++i) {
-            const cpx<real> wi = TR::get(w + i);
-            const cpx<real> pi = TR::get(p + i);
-            const cpx<real>* ca = sA + i * JT + jj0;
-            const cpx<real>* cb = sB + i * JT + jj0;
+            cpx<real> ca[JB], cb[JB];
 #pragma unroll
             for (int u = 0; u < JB; ++u) {
-              cmac<C>(q[u], wi, ca[u]);
-              cmac<C>(x[u], pi, cb[u]);
+              ca[u] = sA[i * JT + jj0 + u];
+              cb[u] = sB[i * JT + jj0 + u];
+            }
+#pragma unroll
+            for (int rr = 0; rr < RT; ++rr) {
+              const cpx<real> wi = TR::get(w[rr] + i);
+              const cpx<real> pi = TR::get(p[rr] + i);
+#pragma unroll
+              for (int u = 0; u < JB; ++u) {
+                cmac<C>(q[rr][u], wi, ca[u]);
+                cmac<C>(x[rr][u], pi, cb[u]);
+              }
             }
           }
           for (int i = jlo; i < i_band_end; ++i) {
-            const cpx<real> wi = TR::get(w + i);
-            const cpx<real> pi = TR::get(p + i);
 #pragma unroll
-            for (int u = 0; u < JB; ++u) {
-              const int j = jlo + u;
-              if (i <= j) cmac<C>(q[u], wi, sA[i * JT + jj0 + u]);
-              cmac<C>(x[u], pi, sB[i * JT + jj0 + u]);
-              if (!keepP && i >= j) cmac<C>(pn[u], pi, sC[i * JT + jj0 + u]);
+            for (int rr = 0; rr < RT; ++rr) {
+              const cpx<real> wi = TR::get(w[rr] + i);
+              const cpx<real> pi = TR::get(p[rr] + i);
+#pragma unroll
+              for (int u = 0; u < JB; ++u) {
+                const int j = jlo + u;
+                if (i <= j) cmac<C>(q[rr][u], wi, sA[i * JT + jj0 + u]);
+                cmac<C>(x[rr][u], pi, sB[i * JT + jj0 + u]);
+                if (!keepP && i >= j) cmac<C>(pn[rr][u], pi, sC[i * JT + jj0 + u]);
+              }
             }
           }
           if (!keepP) {
             for (int i = i_band_end; i < N; ++i) {
-              const cpx<real> pi = TR::get(p + i);
-              const cpx<real>* cb = sB + i * JT + jj0;
-              const cpx<real>* cc = sC + i * JT + jj0;
+              cpx<real> cb[JB], cc[JB];
 #pragma unroll
               for (int u = 0; u < JB; ++u) {
-                cmac<C>(x[u], pi, cb[u]);
-                cmac<C>(pn[u], pi, cc[u]);
+                cb[u] = sB[i * JT + jj0 + u];
+                cc[u] = sC[i * JT + jj0 + u];
+              }
+#pragma unroll
+              for (int rr = 0; rr < RT; ++rr) {
+                const cpx<real> pi = TR::get(p[rr] + i);
+#pragma unroll
+                for (int u = 0; u < JB; ++u) {
+                  cmac<C>(x[rr][u], pi, cb[u]);
+                  cmac<C>(pn[rr][u], pi, cc[u]);
+                }
               }
             }
           } else {
             for (int i = i_band_end; i < N; ++i) {
-              const cpx<real> pi = TR::get(p + i);
-              const cpx<real>* cb = sB + i * JT + jj0;
+              cpx<real> cb[JB];
 #pragma unroll
-              for (int u = 0; u < JB; ++u) cmac<C>(x[u], pi, cb[u]);
+              for (int u = 0; u < JB; ++u) cb[u] = sB[i * JT + jj0 + u];
+#pragma unroll
+              for (int rr = 0; rr < RT; ++rr) {
+                const cpx<real> pi = TR::get(p[rr] + i);
+#pragma unroll
+                for (int u = 0; u < JB; ++u) cmac<C>(x[rr][u], pi, cb[u]);
+              }
             }
           }
         } else {  // ragged last group
           for (int i = 0; i < N; ++i) {
-            const cpx<real> wi = TR::get(w + i);
-            const cpx<real> pi = TR::get(p + i);
 #pragma unroll
-            for (int u = 0; u < JB; ++u) {
-              const int jj = jj0 + u;
-              if (jj < jn) {
-                const int j = j0 + jj;
-                if (i <= j) cmac<C>(q[u], wi, sA[i * JT + jj]);
-                cmac<C>(x[u], pi, sB[i * JT + jj]);
-                if (!keepP && i >= j) cmac<C>(pn[u], pi, sC[i * JT + jj]);
+            for (int rr = 0; rr < RT; ++rr) {
+              const cpx<real> wi = TR::get(w[rr] + i);
+              const cpx<real> pi = TR::get(p[rr] + i);
+#pragma unroll
+              for (int u = 0; u < JB; ++u) {
+                const int jj = jj0 + u;
+                if (jj < jn) {
+                  const int j = j0 + jj;
+                  if (i <= j) cmac<C>(q[rr][u], wi, sA[i * JT + jj]);
+                  cmac<C>(x[rr][u], pi, sB[i * JT + jj]);
+                  if (!keepP && i >= j) cmac<C>(pn[rr][u], pi, sC[i * JT + jj]);
+                }
               }
             }
           }
         }
-        const long long gbase = base + (long long)row * N + j0;
 #pragma unroll
-        for (int u = 0; u < JB; ++u) {
-          const int jj = jj0 + u;
-          if (jj < jn) {
-            const long long gi = gbase + jj;
-            cpx<real> qn = cfin<C>(q[u]);
-            cpx<real> xs = cfin<C>(x[u]);
-            // the old X: from the prefetched tile with DB (plain shared read)
-            cpx<typename CX::acc> xa = cacc_from<CX>(
-                DB ? XS::load_nc(sX + (long long)row * N + j0 + jj) : XS::load_nc(X + gi));
-            CX::add(xa.re, conv<CX, C>::f(xs.re));
-            CX::add(xa.im, conv<CX, C>::f(xs.im));
-            XS::store(X + gi, cfin<CX>(xa));
-            SS::store(Q + gi, qn);
-            if (!keepP) {
-              // P = Q + P S^dag
-              cpx<acc> pf = pn[u];
-              C::add(pf.re, qn.re);
-              C::add(pf.im, qn.im);
-              SS::store(P + gi, cfin<C>(pf));
+        for (int rr = 0; rr < RT; ++rr) {
+          const int row = row0 + rr;
+          if (row >= nrows) continue;
+          const long long gbase = base + (long long)row * N + j0;
+#pragma unroll
+          for (int u = 0; u < JB; ++u) {
+            const int jj = jj0 + u;
+            if (jj < jn) {
+              const long long gi = gbase + jj;
+              cpx<real> qn = cfin<C>(q[rr][u]);
+              cpx<real> xs = cfin<C>(x[rr][u]);
+              // the old X: from the prefetched tile with DB (plain shared read)
+              cpx<typename CX::acc> xa = cacc_from<CX>(
+                  DB ? XS::load_nc(sX + (long long)row * N + j0 + jj) : XS::load_nc(X + gi));
+              CX::add(xa.re, conv<CX, C>::f(xs.re));
+              CX::add(xa.im, conv<CX, C>::f(xs.im));
+              XS::store(X + gi, cfin<CX>(xa));
+              SS::store(Q + gi, qn);
+              if (!keepP) {
+                // P = Q + P S^dag
+                cpx<acc> pf = pn[rr][u];
+                C::add(pf.re, qn.re);
+                C::add(pf.im, qn.im);
+                SS::store(P + gi, cfin<C>(pf));
+              }
             }
           }
         }
@@ -775,10 +833,14 @@ static cudaError_t launch_bcg_update(void* Q, void* P, void* X, const double2* S
   using real = typename SS::comp::real;
   // double-float: 2 output columns per thread keep the accumulators within the
   // register budget of four resident blocks (no spills); other kinds use 4
-  constexpr int JB = std::is_same<SS, StoreDF>::value ? 2 : 4;
+  constexpr int JB = (std::is_same<SS, StoreDF>::value || std::is_same<SS, StoreF64>::value) ? 2 : 4;
   // all kinds but double-float (ALU-bound, and its shared memory is spent on
   // 4 resident blocks): double-buffered tiles (W, P, X) filled by cp.async
   constexpr bool DB = !std::is_same<SS, StoreDF>::value;
+  // rows per thread: 2 for the FP32-arithmetic kinds, whose multiply-adds
+  // are cheap enough that shared-memory reads bound a one-row thread (85 %
+  // L1 throughput at N = 32); 1 for double-float and FP64 (ALU-bound)
+  constexpr int RT = std::is_same<real, float>::value ? 2 : 1;
   const size_t cb = sizeof(cpx<real>), xb = sizeof(typename XS::elem);
   const size_t tb = DB ? sizeof(typename SS::elem) : cb;  // tile element bytes
   // coefficient columns staged per chunk: all N when the three N x N
@@ -800,12 +862,12 @@ static cudaError_t launch_bcg_update(void* Q, void* P, void* X, const double2* S
     while (TS > 1 && coef + tile_bytes(TS) > budget) TS >>= 1;
   }
   const size_t sm = coef + tile_bytes(TS);
-  cudaFuncSetAttribute(k_bcg_update<SS, XS, JB, DB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_bcg_update<SS, XS, JB, DB, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)sm);
   // a block size that divides a tile's (row, column group) work units, so no
   // pass over a tile runs with part of the block idle
   const int jt = JT < N ? JT : N;
-  const int units = TS * 3 * ((jt + JB - 1) / JB);
+  const int units = ((TS * 3 + RT - 1) / RT) * ((jt + JB - 1) / JB);
   int threads = 256;
   if (units <= 256) {
     threads = (units + 31) / 32 * 32;
@@ -818,14 +880,14 @@ static cudaError_t launch_bcg_update(void* Q, void* P, void* X, const double2* S
   }
   // a persistent grid of exactly the resident blocks (no partial last wave)
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bcg_update<SS, XS, JB, DB>, threads,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bcg_update<SS, XS, JB, DB, RT>, threads,
                                                     sm) != cudaSuccess ||
       per_sm < 1) {
     cudaGetLastError();
     per_sm = 1;
   }
   unsigned blocks = gcap(Vh, TS, num_sms() * per_sm);
-  k_bcg_update<SS, XS, JB, DB><<<blocks, threads, sm, s>>>(
+  k_bcg_update<SS, XS, JB, DB, RT><<<blocks, threads, sm, s>>>(
       (typename SS::elem*)Q, (typename SS::elem*)P, (typename XS::elem*)X, Sinv, BC, SH, N, Vh, TS,
       JT, gate);
   return cudaGetLastError();
