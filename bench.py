@@ -61,6 +61,8 @@ def parse_args():
     ap.add_argument("--dslash-only", action="store_true",
                     help="only the stencil sweep (Fig. 1 analogue) for --prec over --sweep")
     ap.add_argument("--sweep", type=int, nargs="+", default=[1, 4, 8, 16, 32])
+    ap.add_argument("--dslash-variant", type=int, default=0,
+                    help="with --dslash-only: force a stencil kernel (blockcg_params.dslash_variant)")
     ap.add_argument("--batched-only", action="store_true",
                     help="only the batched leg (64 small problems, one CUDA graph)")
     ap.add_argument("--autograd-only", action="store_true",
@@ -354,7 +356,8 @@ def dslash_only(a):
     Vh = int(np.prod(dims)) // 2
     fat, lng, _ = cpu_inputs(a)
     dev = torch.device("cuda", 0)
-    h = BlockCG(dims, fat.to(dev), lng.to(dev), a.mass, prec=a.prec, max_rhs=max(a.sweep), device=dev)
+    h = BlockCG(dims, fat.to(dev), lng.to(dev), a.mass, prec=a.prec, max_rhs=max(a.sweep),
+                dslash_variant=a.dslash_variant, device=dev)
     hbm_peak, _ = load_peaks()
     bpr = {"f64": 8, "f64_native": 8, "mixed_f32": 4, "mixed_f16": 2, "mixed_bf16": 2}[a.prec]
     rows = {}
@@ -363,7 +366,8 @@ def dslash_only(a):
         gbs = (288 + 12 * n) * bpr * Vh / (ms * 1e-3) / 1e9
         rows[str(n)] = {"ms": ms, "gbs": gbs, "hbm_frac": gbs / hbm_peak,
                         "gflops": STENCIL_FLOPS * n * Vh / (ms * 1e-3) / 1e9}
-    print(json.dumps({"dslash": rows, "prec": a.prec, "dims": list(dims)}))
+    print(json.dumps({"dslash": rows, "prec": a.prec, "dims": list(dims),
+                      "dslash_variant": a.dslash_variant}))
 
 
 def main():

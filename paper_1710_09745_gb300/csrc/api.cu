@@ -475,12 +475,17 @@ void tune_blas(blockcg_ctx* h, const Ws& w, int N) {
   };
   int best_upd = 0, best_gram = 0, best_wgram = 0;
   float t_upd = 1e30f, t_gram = 1e30f, t_wgram = 1e30f;
-  for (int ts : {4, 8, 16, 32}) {
-    float t = time3([&] {
-      return bcg_update(k, h->upd, w.AP, w.Ts, w.R, mat(w, M_SINV, N), mat(w, M_BC, N),
-                        mat(w, M_SH, N), N, Vh, g0, s, ts);
-    });
-    if (t < t_upd) t_upd = t, best_upd = ts;
+  const bool float_kind = (k == FK_F32 || k == FK_H16 || k == FK_BF16);
+  for (int rows : {1, 2}) {
+    if (rows == 2 && !float_kind) continue;
+    for (int ts : {4, 8, 16, 32}) {
+      const int tile = ts | (rows == 2 ? UPD_TWO_ROWS : 0);
+      float t = time3([&] {
+        return bcg_update(k, h->upd, w.AP, w.Ts, w.R, mat(w, M_SINV, N), mat(w, M_BC, N),
+                          mat(w, M_SH, N), N, Vh, g0, s, tile);
+      });
+      if (t < t_upd) t_upd = t, best_upd = tile;
+    }
   }
   int base = 256 / N;
   if (base < 1) base = 1;

@@ -826,10 +826,10 @@ __global__ void __launch_bounds__(256, 3)
   }
 }
 
-template <class SS, class XS>
-static cudaError_t launch_bcg_update(void* Q, void* P, void* X, const double2* Sinv,
-                                     const double2* BC, const double2* SH, int N, int Vh,
-                                     Gate gate, int tile, cudaStream_t s) {
+template <class SS, class XS, int RT>
+static cudaError_t launch_bcg_update_rt(void* Q, void* P, void* X, const double2* Sinv,
+                                        const double2* BC, const double2* SH, int N, int Vh,
+                                        Gate gate, int tile, cudaStream_t s) {
   using real = typename SS::comp::real;
   // double-float: 2 output columns per thread keep the accumulators within the
   // register budget of four resident blocks (no spills); other kinds use 4
@@ -837,10 +837,6 @@ static cudaError_t launch_bcg_update(void* Q, void* P, void* X, const double2* S
   // all kinds but double-float (ALU-bound, and its shared memory is spent on
   // 4 resident blocks): double-buffered tiles (W, P, X) filled by cp.async
   constexpr bool DB = !std::is_same<SS, StoreDF>::value;
-  // rows per thread: 2 for the FP32-arithmetic kinds, whose multiply-adds
-  // are cheap enough that shared-memory reads bound a one-row thread (85 %
-  // L1 throughput at N = 32); 1 for double-float and FP64 (ALU-bound)
-  constexpr int RT = std::is_same<real, float>::value ? 2 : 1;
   const size_t cb = sizeof(cpx<real>), xb = sizeof(typename XS::elem);
   const size_t tb = DB ? sizeof(typename SS::elem) : cb;  // tile element bytes
   // coefficient columns staged per chunk: all N when the three N x N
@@ -891,6 +887,22 @@ static cudaError_t launch_bcg_update(void* Q, void* P, void* X, const double2* S
       (typename SS::elem*)Q, (typename SS::elem*)P, (typename XS::elem*)X, Sinv, BC, SH, N, Vh, TS,
       JT, gate);
   return cudaGetLastError();
+}
+
+// tile = sites per tile (bits 0..5, 0 = default) + UPD_TWO_ROWS: two rows per
+// thread (FP32-arithmetic kinds; shared-memory reads bound a one-row thread
+// at large N, but the larger thread footprint can cost occupancy, so the
+// tuner decides)
+template <class SS, class XS>
+static cudaError_t launch_bcg_update(void* Q, void* P, void* X, const double2* Sinv,
+                                     const double2* BC, const double2* SH, int N, int Vh,
+                                     Gate gate, int tile, cudaStream_t s) {
+  const int ts = tile & (UPD_TWO_ROWS - 1);
+  if constexpr (std::is_same<typename SS::comp::real, float>::value) {
+    if (tile & UPD_TWO_ROWS)
+      return launch_bcg_update_rt<SS, XS, 2>(Q, P, X, Sinv, BC, SH, N, Vh, gate, ts, s);
+  }
+  return launch_bcg_update_rt<SS, XS, 1>(Q, P, X, Sinv, BC, SH, N, Vh, gate, ts, s);
 }
 
 cudaError_t bcg_update(FieldKind sk, FieldKind xk, void* Q, void* P, void* X, const double2* Sinv,
