@@ -476,10 +476,11 @@ void tune_blas(blockcg_ctx* h, const Ws& w, int N) {
   int best_upd = 0, best_gram = 0, best_wgram = 0;
   float t_upd = 1e30f, t_gram = 1e30f, t_wgram = 1e30f;
   const bool float_kind = (k == FK_F32 || k == FK_H16 || k == FK_BF16);
-  for (int rows : {1, 2}) {
-    if (rows == 2 && !float_kind) continue;
+  for (int variant = 0; variant < 4; ++variant) {
+    const bool two_rows = variant & 1, x_global = variant & 2;
+    if ((two_rows || x_global) && !float_kind) continue;
     for (int ts : {4, 8, 16, 32}) {
-      const int tile = ts | (rows == 2 ? UPD_TWO_ROWS : 0);
+      const int tile = ts | (two_rows ? UPD_TWO_ROWS : 0) | (x_global ? UPD_X_GLOBAL : 0);
       float t = time3([&] {
         return bcg_update(k, h->upd, w.AP, w.Ts, w.R, mat(w, M_SINV, N), mat(w, M_BC, N),
                           mat(w, M_SH, N), N, Vh, g0, s, tile);

@@ -583,7 +583,7 @@ struct UpdTile<SS, true> {
 __host__ __device__ inline size_t upd_wp_bytes(int TS, int N, size_t tile_elem) {
   return (2 * (size_t)TS * 3 * (N + 1) * tile_elem + 15) / 16 * 16;
 }
-template <class SS, class XS, int JB, bool DB, int RT>
+template <class SS, class XS, int JB, bool DB, int RT, bool XSTAGE>
 __global__ void __launch_bounds__(256, 3)
     k_bcg_update(typename SS::elem* __restrict__ Q, typename SS::elem* __restrict__ P,
                  typename XS::elem* __restrict__ X, const double2* __restrict__ Sinv,
@@ -606,7 +606,10 @@ __global__ void __launch_bounds__(256, 3)
   const int tile_w = TS * 3 * RS;
   // one set = [W tile][P tile][X tile (DB only)]; set b starts b * set_bytes in
   const size_t wp_bytes = upd_wp_bytes(TS, N, sizeof(TT));
-  const size_t set_bytes = wp_bytes + (DB ? (size_t)TS * 3 * N * sizeof(XE) : 0);
+  // XSTAGE: the old X is copied into the tile set too (else read from global
+  // memory in the epilogue: each thread reads JB consecutive elements, whole
+  // sectors, and the smaller tiles allow more resident blocks)
+  const size_t set_bytes = wp_bytes + (DB && XSTAGE ? (size_t)TS * 3 * N * sizeof(XE) : 0);
   auto tW = [&](int bsel) { return reinterpret_cast<TT*>(smem_raw + bsel * set_bytes); };
   auto tP = [&](int bsel) { return tW(bsel) + tile_w; };
   auto tX = [&](int bsel) { return reinterpret_cast<XE*>(smem_raw + bsel * set_bytes + wp_bytes); };
@@ -632,7 +635,7 @@ __global__ void __launch_bounds__(256, 3)
       const int rr = idx / N, cc = idx - rr * N;
       cp_async_bytes(tW(bsel) + rr * RS + cc, Q + bs + idx, sizeof(typename SS::elem));
       cp_async_bytes(tP(bsel) + rr * RS + cc, P + bs + idx, sizeof(typename SS::elem));
-      cp_async_bytes(tX(bsel) + idx, X + bs + idx, sizeof(XE));
+      if (XSTAGE) cp_async_bytes(tX(bsel) + idx, X + bs + idx, sizeof(XE));
     }
     cp_async_commit();
   };
@@ -806,7 +809,7 @@ __global__ void __launch_bounds__(256, 3)
               cpx<real> xs = cfin<C>(x[rr][u]);
               // the old X: from the prefetched tile with DB (plain shared read)
               cpx<typename CX::acc> xa = cacc_from<CX>(
-                  DB ? XS::load_nc(sX + (long long)row * N + j0 + jj) : XS::load_nc(X + gi));
+                  DB && XSTAGE ? XS::load_nc(sX + (long long)row * N + j0 + jj) : XS::load_nc(X + gi));
               CX::add(xa.re, conv<CX, C>::f(xs.re));
               CX::add(xa.im, conv<CX, C>::f(xs.im));
               XS::store(X + gi, cfin<CX>(xa));
@@ -826,7 +829,7 @@ __global__ void __launch_bounds__(256, 3)
   }
 }
 
-template <class SS, class XS, int RT>
+template <class SS, class XS, int RT, bool XSTAGE>
 static cudaError_t launch_bcg_update_rt(void* Q, void* P, void* X, const double2* Sinv,
                                         const double2* BC, const double2* SH, int N, int Vh,
                                         Gate gate, int tile, cudaStream_t s) {
@@ -846,7 +849,7 @@ static cudaError_t launch_bcg_update_rt(void* Q, void* P, void* X, const double2
   if (JT < N && JT < 16) JT = 16;
   const size_t coef = 3ull * N * JT * cb;
   auto tile_bytes = [&](int ts) {
-    size_t one = upd_wp_bytes(ts, N, tb) + (DB ? (size_t)ts * 3 * N * xb : 0);
+    size_t one = upd_wp_bytes(ts, N, tb) + (DB && XSTAGE ? (size_t)ts * 3 * N * xb : 0);
     return (DB ? 2 : 1) * one;
   };
   int TS = 32;
@@ -858,7 +861,7 @@ static cudaError_t launch_bcg_update_rt(void* Q, void* P, void* X, const double2
     while (TS > 1 && coef + tile_bytes(TS) > budget) TS >>= 1;
   }
   const size_t sm = coef + tile_bytes(TS);
-  cudaFuncSetAttribute(k_bcg_update<SS, XS, JB, DB, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_bcg_update<SS, XS, JB, DB, RT, XSTAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)sm);
   // a block size that divides a tile's (row, column group) work units, so no
   // pass over a tile runs with part of the block idle
@@ -876,14 +879,14 @@ static cudaError_t launch_bcg_update_rt(void* Q, void* P, void* X, const double2
   }
   // a persistent grid of exactly the resident blocks (no partial last wave)
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bcg_update<SS, XS, JB, DB, RT>, threads,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bcg_update<SS, XS, JB, DB, RT, XSTAGE>, threads,
                                                     sm) != cudaSuccess ||
       per_sm < 1) {
     cudaGetLastError();
     per_sm = 1;
   }
   unsigned blocks = gcap(Vh, TS, num_sms() * per_sm);
-  k_bcg_update<SS, XS, JB, DB, RT><<<blocks, threads, sm, s>>>(
+  k_bcg_update<SS, XS, JB, DB, RT, XSTAGE><<<blocks, threads, sm, s>>>(
       (typename SS::elem*)Q, (typename SS::elem*)P, (typename XS::elem*)X, Sinv, BC, SH, N, Vh, TS,
       JT, gate);
   return cudaGetLastError();
@@ -892,17 +895,21 @@ static cudaError_t launch_bcg_update_rt(void* Q, void* P, void* X, const double2
 // tile = sites per tile (bits 0..5, 0 = default) + UPD_TWO_ROWS: two rows per
 // thread (FP32-arithmetic kinds; shared-memory reads bound a one-row thread
 // at large N, but the larger thread footprint can cost occupancy, so the
-// tuner decides)
+// tuner decides) + UPD_X_GLOBAL: the old X read from global memory rather
+// than staged (FP32-arithmetic kinds)
 template <class SS, class XS>
 static cudaError_t launch_bcg_update(void* Q, void* P, void* X, const double2* Sinv,
                                      const double2* BC, const double2* SH, int N, int Vh,
                                      Gate gate, int tile, cudaStream_t s) {
   const int ts = tile & (UPD_TWO_ROWS - 1);
   if constexpr (std::is_same<typename SS::comp::real, float>::value) {
+    const bool xg = (tile & UPD_X_GLOBAL) != 0;
     if (tile & UPD_TWO_ROWS)
-      return launch_bcg_update_rt<SS, XS, 2>(Q, P, X, Sinv, BC, SH, N, Vh, gate, ts, s);
+      return xg ? launch_bcg_update_rt<SS, XS, 2, false>(Q, P, X, Sinv, BC, SH, N, Vh, gate, ts, s)
+                : launch_bcg_update_rt<SS, XS, 2, true>(Q, P, X, Sinv, BC, SH, N, Vh, gate, ts, s);
+    if (xg) return launch_bcg_update_rt<SS, XS, 1, false>(Q, P, X, Sinv, BC, SH, N, Vh, gate, ts, s);
   }
-  return launch_bcg_update_rt<SS, XS, 1>(Q, P, X, Sinv, BC, SH, N, Vh, gate, ts, s);
+  return launch_bcg_update_rt<SS, XS, 1, true>(Q, P, X, Sinv, BC, SH, N, Vh, gate, ts, s);
 }
 
 cudaError_t bcg_update(FieldKind sk, FieldKind xk, void* Q, void* P, void* X, const double2* Sinv,

@@ -167,6 +167,9 @@ __device__ __forceinline__ cpx<typename C::real> cfin(const cpx<typename C::acc>
 struct StoreDF {  // {re.hi, im.hi, re.lo, im.lo}: one 128-bit word per complex
   using elem = float4;
   using comp = CompDF;
+  static constexpr float RAW_SCALE = 1.f;  // see StoreH16
+  static __device__ __forceinline__ cpx<df> load_raw(const elem* p) { return load(p); }
+  static __device__ __forceinline__ cpx<df> load_nc_raw(const elem* p) { return load_nc(p); }
   static __device__ __forceinline__ cpx<df> load(const elem* p) {
     float4 v = __ldg(p);
     return {{v.x, v.z}, {v.y, v.w}};
@@ -190,6 +193,7 @@ struct StoreDF {  // {re.hi, im.hi, re.lo, im.lo}: one 128-bit word per complex
 struct StoreF32 {
   using elem = float2;
   using comp = CompF32;
+  static constexpr float RAW_SCALE = 1.f;
   // two consecutive complex numbers with one 128-bit load (16-byte aligned)
   static __device__ __forceinline__ void load2(const elem* p, cpx<float>& a, cpx<float>& b) {
     float4 v = __ldg(reinterpret_cast<const float4*>(p));
@@ -204,6 +208,8 @@ struct StoreF32 {
     float2 v = *p;
     return {v.x, v.y};
   }
+  static __device__ __forceinline__ cpx<float> load_raw(const elem* p) { return load(p); }
+  static __device__ __forceinline__ cpx<float> load_nc_raw(const elem* p) { return load_nc(p); }
   static __device__ __forceinline__ void store(elem* p, const cpx<float>& a) {
     *p = make_float2(a.re, a.im);
   }
@@ -218,6 +224,9 @@ struct StoreF32 {
 struct StoreF64 {
   using elem = double2;
   using comp = CompF64;
+  static constexpr float RAW_SCALE = 1.f;
+  static __device__ __forceinline__ cpx<double> load_raw(const elem* p) { return load(p); }
+  static __device__ __forceinline__ cpx<double> load_nc_raw(const elem* p) { return load_nc(p); }
   static __device__ __forceinline__ cpx<double> load(const elem* p) {
     double2 v = __ldg(p);
     return {v.x, v.y};
@@ -246,10 +255,21 @@ struct StoreH16 {
   using comp = CompF32;
   static constexpr float SCALE = 16.f;
   static constexpr float INV = 1.f / 16.f;
+  // The raw loads keep the stored 2^4 factor: kernels that multiply stored
+  // values by stored values (the stencil: links times spinors) take the
+  // products in the scaled domain and remove RAW_SCALE^2 once per output,
+  // saving two multiplications per loaded element (exact: powers of two).
+  static constexpr float RAW_SCALE = SCALE;
   static __device__ __forceinline__ cpx<float> cvt(__half2 h) {
     float2 f = __half22float2(h);
     return {f.x * INV, f.y * INV};
   }
+  static __device__ __forceinline__ cpx<float> cvt_raw(__half2 h) {
+    float2 f = __half22float2(h);
+    return {f.x, f.y};
+  }
+  static __device__ __forceinline__ cpx<float> load_raw(const elem* p) { return cvt_raw(__ldg(p)); }
+  static __device__ __forceinline__ cpx<float> load_nc_raw(const elem* p) { return cvt_raw(*p); }
   static __device__ __forceinline__ cpx<float> load(const elem* p) { return cvt(__ldg(p)); }
   static __device__ __forceinline__ cpx<float> load_nc(const elem* p) { return cvt(*p); }
   static __device__ __forceinline__ void store(elem* p, const cpx<float>& a) {
@@ -267,10 +287,14 @@ struct StoreH16 {
 struct StoreBF16 {
   using elem = __nv_bfloat162;
   using comp = CompF32;
+  static constexpr float RAW_SCALE = 1.f;
   static __device__ __forceinline__ cpx<float> cvt(__nv_bfloat162 h) {
     float2 f = __bfloat1622float2(h);
     return {f.x, f.y};
   }
+  static __device__ __forceinline__ cpx<float> cvt_raw(__nv_bfloat162 h) { return cvt(h); }
+  static __device__ __forceinline__ cpx<float> load_raw(const elem* p) { return cvt(__ldg(p)); }
+  static __device__ __forceinline__ cpx<float> load_nc_raw(const elem* p) { return cvt(*p); }
   static __device__ __forceinline__ cpx<float> load(const elem* p) { return cvt(__ldg(p)); }
   static __device__ __forceinline__ cpx<float> load_nc(const elem* p) { return cvt(*p); }
   static __device__ __forceinline__ void store(elem* p, const cpx<float>& a) {

@@ -114,8 +114,10 @@ cudaError_t gram_reduce(const double2* partials, int nblocks, int N, int hermiti
 // (nblocks CTAs, reduced by gram_reduce)
 cudaError_t w_update_gram(FieldKind k, void* Q, const void* AP, const double2* beta, int N, int Vh,
                           double2* partials, int nblocks, Gate gate, cudaStream_t s, int tile = 0);
-// tile of bcg_update: sites per tile, plus UPD_TWO_ROWS for two rows per thread
+// tile of bcg_update: sites per tile, plus UPD_TWO_ROWS for two rows per
+// thread and UPD_X_GLOBAL for the old X read from global memory (not staged)
 static constexpr int UPD_TWO_ROWS = 64;
+static constexpr int UPD_X_GLOBAL = 128;
 // Q <- W Sinv ; X += P BC ; P <- Q + P SH unless st->ru_pending
 cudaError_t bcg_update(FieldKind sk, FieldKind xk, void* Q, void* P, void* X, const double2* Sinv,
                        const double2* BC, const double2* SH, int N, int Vh, Gate gate,

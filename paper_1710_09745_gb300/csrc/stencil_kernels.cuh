@@ -66,7 +66,7 @@ template <class S>
 struct VecLoad<S, 1> {
   static __device__ __forceinline__ void get(const typename S::elem* p,
                                              cpx<typename S::comp::real>* v) {
-    v[0] = S::load(p);
+    v[0] = S::load_raw(p);
   }
 };
 template <>
@@ -83,15 +83,15 @@ struct VecLoad16 {
     if (V == 4) {
       uint4 u = __ldg(reinterpret_cast<const uint4*>(p));
       const typename S::elem* e = reinterpret_cast<const typename S::elem*>(&u);
-      v[0] = S::cvt(e[0]);
-      v[1] = S::cvt(e[1]);
-      v[2] = S::cvt(e[2]);
-      v[3] = S::cvt(e[3]);
+      v[0] = S::cvt_raw(e[0]);
+      v[1] = S::cvt_raw(e[1]);
+      v[2] = S::cvt_raw(e[2]);
+      v[3] = S::cvt_raw(e[3]);
     } else {
       uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
       const typename S::elem* e = reinterpret_cast<const typename S::elem*>(&u);
-      v[0] = S::cvt(e[0]);
-      v[1] = S::cvt(e[1]);
+      v[0] = S::cvt_raw(e[0]);
+      v[1] = S::cvt_raw(e[1]);
     }
   }
 };
@@ -142,6 +142,17 @@ struct PlainBounds<StoreF32, RV> {
   static constexpr int unroll = RV >= 2 ? 0 : 1;    // R = 8 also gains without unrolling
 };
 
+// The hop loops multiply raw loads (StoreH16 keeps 2^4 x value): remove the
+// factor RAW_SCALE^2 from an output accumulator once (exact, a power of two)
+template <class S, class A>
+__device__ __forceinline__ void unscale_raw(cpx<A>& v) {
+  if constexpr (S::RAW_SCALE != 1.f) {
+    constexpr float k = 1.f / (S::RAW_SCALE * S::RAW_SCALE);
+    v.re *= k;
+    v.im *= k;
+  }
+}
+
 template <class S, int RV, int V, int EPI, int UNROLL_HOPS, bool RC = false>
 __global__ void __launch_bounds__(BCG_DSLASH_TPB, (PlainBounds<S, RV>::minb))
     k_dslash(const typename S::elem* __restrict__ links, const typename S::elem* __restrict__ in,
@@ -185,7 +196,7 @@ __global__ void __launch_bounds__(BCG_DSLASH_TPB, (PlainBounds<S, RV>::minb))
       const int nb = neighbour_cb_s(g, lex, x, y, z, t, mu, kk);
       cpx<real> U[9];
 #pragma unroll
-      for (int e = 0; e < LE; ++e) U[e] = S::load(lp + (d * LE + e) * LINK_W);
+      for (int e = 0; e < LE; ++e) U[e] = S::load_raw(lp + (d * LE + e) * LINK_W);
       if constexpr (RC) {
         // sign of the stored matrix's scale: staggered phase, boundary, backward hop
         const int ps = mu == 0 ? 0 : mu == 1 ? x : mu == 2 ? x + y : x + y + z;
@@ -193,7 +204,8 @@ __global__ void __launch_bounds__(BCG_DSLASH_TPB, (PlainBounds<S, RV>::minb))
         if (kk < 0) sg = -sg;
         if (g.antiperiodic && mu == 3 && (t + kk < 0 || t + kk >= g.L[3])) sg = -sg;
         const real inv = (real)sg * (real)g.inv_c[(d & 2) ? 1 : 0];
-        rebuild_row2<real>(U, inv);
+        // rows 0 and 1 were loaded raw (times RAW_SCALE): keep row 2 raw too
+        rebuild_row2<real>(U, inv / (real)S::RAW_SCALE);
       }
       const typename S::elem* ip = in + (long long)nb * N * 3 + k * V;
 #pragma unroll
@@ -236,6 +248,7 @@ __global__ void __launch_bounds__(BCG_DSLASH_TPB, (PlainBounds<S, RV>::minb))
           for (int i = 0; i < 3; ++i) {
             const long long oi = ob + i * N + r * T * V + w;
             cpx<acc> v = a[r][w][i];
+            unscale_raw<S>(v);
             if (EPI != EPI_NONE) {
               // m2 * c1 - D in
               C::neg(v.re);
@@ -406,7 +419,7 @@ __global__ void __launch_bounds__((TMA_MAX_T + 1) * 32)
       if (valid) {
         cpx<real> U[9];
 #pragma unroll
-        for (int e = 0; e < 9; ++e) U[e] = S::load_nc(base + e * LINK_W + sl);
+        for (int e = 0; e < 9; ++e) U[e] = S::load_nc_raw(base + e * LINK_W + sl);
         const E* ip = base + link_elems + sl * row + k * V;
 #pragma unroll
         for (int r = 0; r < RV; ++r) {
@@ -416,7 +429,7 @@ __global__ void __launch_bounds__((TMA_MAX_T + 1) * 32)
 #pragma unroll
             for (int b = 0; b < 3; ++b)
 #pragma unroll
-              for (int w = 0; w < V; ++w) v[b][w] = S::load_nc(ip + b * N + sr * T * V + w);
+              for (int w = 0; w < V; ++w) v[b][w] = S::load_nc_raw(ip + b * N + sr * T * V + w);
 #pragma unroll
             for (int w = 0; w < V; ++w)
 #pragma unroll
@@ -444,6 +457,7 @@ __global__ void __launch_bounds__((TMA_MAX_T + 1) * 32)
               for (int i = 0; i < 3; ++i) {
                 const long long oi = ob + i * N + sr * T * V + w;
                 cpx<acc> vv = a[r][w][i];
+                unscale_raw<S>(vv);
                 if (EPI != EPI_NONE) {
                   C::neg(vv.re);
                   C::neg(vv.im);
@@ -640,7 +654,7 @@ __global__ void __launch_bounds__(ASYNC_TPB)
         const E* l = sL + (buf * sites_cta + ls) * 9;
         cpx<real> U[9];
 #pragma unroll
-        for (int e = 0; e < 9; ++e) U[e] = S::load_nc(l + e);
+        for (int e = 0; e < 9; ++e) U[e] = S::load_nc_raw(l + e);
         const E* sp = sS + ((long long)buf * ASYNC_TPB + tid) * SPT;
 #pragma unroll
         for (int r = 0; r < RV; ++r) {
@@ -649,7 +663,7 @@ __global__ void __launch_bounds__(ASYNC_TPB)
 #pragma unroll
             for (int b = 0; b < 3; ++b)
 #pragma unroll
-              for (int w = 0; w < V; ++w) v[b][w] = S::load_nc(sp + (r * 3 + b) * V + w);
+              for (int w = 0; w < V; ++w) v[b][w] = S::load_nc_raw(sp + (r * 3 + b) * V + w);
 #pragma unroll
             for (int w = 0; w < V; ++w)
 #pragma unroll
@@ -674,6 +688,7 @@ __global__ void __launch_bounds__(ASYNC_TPB)
             for (int i = 0; i < 3; ++i) {
               const long long oi = ob + i * N + r * T * V + w;
               cpx<acc> vv = a[r][w][i];
+                unscale_raw<S>(vv);
               if (EPI != EPI_NONE) {
                 C::neg(vv.re);
                 C::neg(vv.im);

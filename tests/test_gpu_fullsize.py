@@ -122,3 +122,15 @@ def test_config_48x96_n32_mixed_f16():
         rms_r = np.sqrt(np.mean(np.abs(r) ** 2))
         rms_b = np.sqrt(np.mean(np.abs(bh[j][sites >> 1]) ** 2))
         assert rms_r / rms_b < 3e-10
+    # column 0 against a whole oracle solve (textbook CG in FP64 to 1e-11): the
+    # true residual of the full column, and the solution error, which
+    # |e|/|x| <= kappa (|r_gpu| + |r_oracle|)/|b| bounds with kappa =
+    # lambda_max / m^2, about 4.4e4 here (lambda_max ~ 4.3, near the free-field
+    # value 4 (1 + 1/24)^2 for these smooth links)
+    r0 = bh[0] - hisq.apply_A(dims, fat_h, lng_h, MASS, Xh[0])
+    assert np.linalg.norm(r0) / np.linalg.norm(bh[0]) <= 1e-10
+    x0, it, res = hisq.cg(dims, fat_h, lng_h, MASS, bh[:1], tol=1e-11, max_iter=5000)
+    assert res[0] <= 1e-11
+    err = np.linalg.norm(Xh[0] - x0[0]) / np.linalg.norm(x0[0])
+    assert err < 4.4e4 * (1e-10 + 1e-11), err
+    assert err < 1e-7, err

@@ -490,3 +490,26 @@ def test_solve_many_picks_width_and_persists_it(tmp_path):
     X3, info3 = s.solve_many(b[:10], tol=1e-10, width=4)
     assert info3["blocks"] == 3 and info3["width"] == 4
     assert _oracle_rel_res(dims, fat, lng, mass, b[:10], gh.to_np(X3)).max() <= 1e-10
+
+
+@pytest.mark.parametrize("prec,kind", [("mixed_f32", 1), ("mixed_f16", 3)])
+@pytest.mark.parametrize("upd", [4, 8 | 64, 8 | 128, 16 | 64 | 128, 32])
+def test_forced_blas_tiles_converge(tmp_path, prec, kind, upd):
+    """Every shape the block-BLAS tile tuner can choose, forced through the
+    tuning cache (sites per tile of the fused update, one or two rows per
+    thread (64), X staged or read from global memory (128); Gram tiles of 16
+    and 32 sites): each solve meets tol on the oracle's residual."""
+    import json
+    torch = gh.torch_mod()
+    dims, mass, N = (8, 8, 8, 8), 0.05, 8
+    dev = torch.cuda.get_device_name(0).replace(" ", "_").replace('"', "_").replace("\\", "_")
+    cache = tmp_path / "tiles.json"
+    packed = upd | (16 << 8) | (32 << 16)
+    cache.write_text(json.dumps({f"blas/8.8.8.8/kind{kind}/N{N}/{dev}": packed}))
+    s, fat, lng = gh.make_solver(dims, mass, prec=prec, seed=1025, max_rhs=N)
+    s.set_tune_cache(cache)
+    b = hi.gaussian_sources(dims, N, seed=2025)
+    X, info = s.solve(b, tol=1e-10)
+    assert info["status"] == 0
+    assert _oracle_rel_res(dims, fat, lng, mass, b, gh.to_np(X)).max() <= 1e-10
+    assert f'"blas/8.8.8.8/kind{kind}/N{N}/{dev}": {packed}' in cache.read_text()
