@@ -596,8 +596,15 @@ double cheap_ru_above(const blockcg_ctx* h) {
 // A reliable update (Algorithm 3) gated by `gate`: with a cheaper kind, two
 // residual blocks gated on this iteration's residual (GATE_RU_CHEAP /
 // GATE_RU_FINE, exactly one of them runs); otherwise the FP64 one.
+// The cheap updates pay only where the FP64 stencil is expensive: on small
+// problems (V/2 x N below 2^21 site-columns) the extra gated-off launches of
+// a second update block cost more per iteration than the cheap updates save.
+bool use_cheap_ru(const blockcg_ctx* h, int N) {
+  return h->ru != h->fine && (double)h->g.Vh * N >= (double)(1 << 21);
+}
+
 blockcg_status restart_block(blockcg_ctx* h, const Ws& w, int N, double tol, int init, Gate gate) {
-  if (h->ru == h->fine || gate.mode != GATE_RU)
+  if (!use_cheap_ru(h, N) || gate.mode != GATE_RU)
     return restart_residual(h, w, N, tol, init, gate, false, false);
   const size_t nel = (size_t)h->g.Vh * N * 3;
   TL(TC_STREAM, accumulate(h->fine, h->upd, w.Y, w.X, nel, gate, h->stream));
@@ -674,7 +681,7 @@ void tune_block(blockcg_ctx* h, const Ws& w, int N) {
   tune_blas(h, w, N);
   stencil_R(h, h->sloppy, N, h->links_sloppy, w.P, w.Ts, w.AP);
   stencil_R(h, h->fine, N, h->links_fine, w.Y, w.Tf, w.R);
-  if (h->ru != h->fine) stencil_R(h, h->ru, N, h->links_ru, w.Yru, w.Tf, w.Rru);
+  if (use_cheap_ru(h, N)) stencil_R(h, h->ru, N, h->links_ru, w.Yru, w.Tf, w.Rru);
 }
 
 // Algorithm 1 set-up: B and X in internal layout, |b_i|, X = 0 (update),

@@ -1057,14 +1057,20 @@ __global__ void k_accumulate(typename YS::elem* __restrict__ Y, typename XS::ele
   }
 }
 
+// grid of a streaming kernel: reliable-update launches (gated off in most
+// iterations) use 2 blocks per SM, others up to 8
+static unsigned stream_grid(size_t n, const Gate& gate) {
+  return gcap(n, 256, gate_mostly_off(gate) ? 152 * 2 : 152 * 8);
+}
+
 cudaError_t accumulate(FieldKind yk, FieldKind xk, void* Y, void* X, size_t n, Gate gate,
                        cudaStream_t s) {
   if (yk == FK_F64 && xk == FK_DF)
-    k_accumulate<StoreF64, StoreDF><<<gcap(n, 256), 256, 0, s>>>((double2*)Y, (float4*)X, n, gate);
+    k_accumulate<StoreF64, StoreDF><<<stream_grid(n, gate), 256, 0, s>>>((double2*)Y, (float4*)X, n, gate);
   else if (yk == FK_F64 && xk == FK_F64)
-    k_accumulate<StoreF64, StoreF64><<<gcap(n, 256), 256, 0, s>>>((double2*)Y, (double2*)X, n, gate);
+    k_accumulate<StoreF64, StoreF64><<<stream_grid(n, gate), 256, 0, s>>>((double2*)Y, (double2*)X, n, gate);
   else if (yk == FK_DF && xk == FK_DF)
-    k_accumulate<StoreDF, StoreDF><<<gcap(n, 256), 256, 0, s>>>((float4*)Y, (float4*)X, n, gate);
+    k_accumulate<StoreDF, StoreDF><<<stream_grid(n, gate), 256, 0, s>>>((float4*)Y, (float4*)X, n, gate);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();
@@ -1088,17 +1094,17 @@ __global__ void k_convert(const typename SS::elem* __restrict__ in, typename DS:
 cudaError_t convert_field(FieldKind from, FieldKind to, const void* in, void* out, size_t n,
                           const double* scale, Gate gate, cudaStream_t s) {
   if (from == FK_F64 && to == FK_DF)
-    k_convert<StoreDF, StoreF64><<<gcap(n, 256), 256, 0, s>>>((const double2*)in, (float4*)out, n, scale, gate);
+    k_convert<StoreDF, StoreF64><<<stream_grid(n, gate), 256, 0, s>>>((const double2*)in, (float4*)out, n, scale, gate);
   else if (from == FK_F64 && to == FK_F32)
-    k_convert<StoreF32, StoreF64><<<gcap(n, 256), 256, 0, s>>>((const double2*)in, (float2*)out, n, scale, gate);
+    k_convert<StoreF32, StoreF64><<<stream_grid(n, gate), 256, 0, s>>>((const double2*)in, (float2*)out, n, scale, gate);
   else if (from == FK_F64 && to == FK_H16)
-    k_convert<StoreH16, StoreF64><<<gcap(n, 256), 256, 0, s>>>((const double2*)in, (__half2*)out, n, scale, gate);
+    k_convert<StoreH16, StoreF64><<<stream_grid(n, gate), 256, 0, s>>>((const double2*)in, (__half2*)out, n, scale, gate);
   else if (from == FK_F64 && to == FK_BF16)
-    k_convert<StoreBF16, StoreF64><<<gcap(n, 256), 256, 0, s>>>((const double2*)in, (__nv_bfloat162*)out, n, scale, gate);
+    k_convert<StoreBF16, StoreF64><<<stream_grid(n, gate), 256, 0, s>>>((const double2*)in, (__nv_bfloat162*)out, n, scale, gate);
   else if (from == FK_F64 && to == FK_F64)
-    k_convert<StoreF64, StoreF64><<<gcap(n, 256), 256, 0, s>>>((const double2*)in, (double2*)out, n, scale, gate);
+    k_convert<StoreF64, StoreF64><<<stream_grid(n, gate), 256, 0, s>>>((const double2*)in, (double2*)out, n, scale, gate);
   else if (from == FK_DF && to == FK_F64)
-    k_convert<StoreF64, StoreDF><<<gcap(n, 256), 256, 0, s>>>((const float4*)in, (double2*)out, n, scale, gate);
+    k_convert<StoreF64, StoreDF><<<stream_grid(n, gate), 256, 0, s>>>((const float4*)in, (double2*)out, n, scale, gate);
   else if (from == to && !scale)
     return cudaMemcpyAsync(out, in, n * elem_bytes(to), cudaMemcpyDeviceToDevice, s);
   else

@@ -37,6 +37,13 @@ struct Gate {
   double thr;  // res_max threshold of GATE_RU_CHEAP / GATE_RU_FINE
 };
 
+// launches gated on a pending reliable update are off in most iterations;
+// their launchers use persistent grids (a few blocks per SM) so that a
+// gated-off launch retires quickly
+inline bool gate_mostly_off(const Gate& g) {
+  return g.st && (g.mode == GATE_RU || g.mode == GATE_RU_CHEAP || g.mode == GATE_RU_FINE);
+}
+
 __device__ __forceinline__ bool gate_closed(const Gate& g) {
   if (g.mode == GATE_ALWAYS || g.st == nullptr) return false;
   const volatile SolverStatus* s = g.st;

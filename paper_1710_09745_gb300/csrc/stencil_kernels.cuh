@@ -728,6 +728,8 @@ static bool launch_async_t(const void* links, const void* in, void* out, const v
   long long total = (long long)g.Vh * T;
   long long want = (total + ASYNC_TPB - 1) / ASYNC_TPB;
   unsigned blocks = (unsigned)(want < 152 * 16 ? want : 152 * 16);
+  if (gate_mostly_off(gate) && blocks > (unsigned)stencil_sms() * 4)
+    blocks = (unsigned)stencil_sms() * 4;  // reliable-update stencil: persistent grid
   kern<<<blocks, ASYNC_TPB, sm, s>>>((const E*)links, (const E*)in, (E*)out, (const E*)c1,
                                      (const E*)c2, m2, g, parity, N, T, gate);
   return true;
@@ -791,6 +793,11 @@ static void launch_dslash_t(const void* links, const void* in, void* out, const 
   long long want = (threads_total + threads - 1) / threads;
   unsigned blocks = (unsigned)(want < 152 * 32 ? want : 152 * 32);
   long long span = 0;
+  if (gate_mostly_off(gate)) {
+    // a reliable-update stencil: a persistent grid (see gate_mostly_off)
+    const long long cap = (long long)stencil_sms() * 4;
+    if (blocks > cap) blocks = (unsigned)cap;
+  }
   if (blocked) {
     // a persistent grid of the resident blocks, each owning one contiguous
     // range of (site, slot) pairs, a whole number of blocks of threads long
