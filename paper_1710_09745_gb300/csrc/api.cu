@@ -423,7 +423,15 @@ int stencil_R(blockcg_ctx* h, FieldKind k, int N, const void* links, const void*
 struct BlasTiles {
   int upd, gram, wgram;
 };
-BlasTiles unpack_tiles(int v) { return {v & 0xff, (v >> 8) & 0xff, (v >> 16) & 0xff}; }
+// packed: update tile in bits 0..7 (UPD_TC as bit 24), Gram tile in bits
+// 8..15, fused W + Gram tile in bits 16..23
+BlasTiles unpack_tiles(int v) {
+  return {(v & 0xff) | ((v >> 24) & 1 ? UPD_TC : 0), (v >> 8) & 0xff, (v >> 16) & 0xff};
+}
+int pack_tiles(const BlasTiles& t) {
+  return (t.upd & 0xff) | ((t.upd & UPD_TC) ? 1 << 24 : 0) | ((t.gram & 0xff) << 8) |
+         ((t.wgram & 0xff) << 16);
+}
 
 BlasTiles cached_tiles(const blockcg_ctx* h, FieldKind k, int N) {
   auto it = h->tuned_blas.find((int)k * 128 + N);
@@ -491,6 +499,13 @@ void tune_blas(blockcg_ctx* h, const Ws& w, int N) {
       if (t < t_upd) t_upd = t, best_upd = tile;
     }
   }
+  if (bcg_update_tc_supported(k, h->upd, N)) {
+    float t = time3([&] {
+      return bcg_update(k, h->upd, w.AP, w.Ts, w.R, mat(w, M_SINV, N), mat(w, M_BC, N),
+                        mat(w, M_SH, N), N, Vh, g0, s, UPD_TC);
+    });
+    if (t < t_upd) t_upd = t, best_upd = UPD_TC;
+  }
   int base = 256 / N;
   if (base < 1) base = 1;
   for (int ts : {base, 2 * base, 4 * base}) {
@@ -504,7 +519,7 @@ void tune_blas(blockcg_ctx* h, const Ws& w, int N) {
     });
     if (t < t_wgram) t_wgram = t, best_wgram = ts;
   }
-  const int packed = best_upd | (best_gram << 8) | (best_wgram << 16);
+  const int packed = pack_tiles({best_upd, best_gram, best_wgram});
   h->tuned_blas[key] = packed;
   cache_put(h, blas_key(h, k, N), packed);
 }

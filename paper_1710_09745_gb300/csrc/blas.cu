@@ -915,6 +915,9 @@ static cudaError_t launch_bcg_update(void* Q, void* P, void* X, const double2* S
 cudaError_t bcg_update(FieldKind sk, FieldKind xk, void* Q, void* P, void* X, const double2* Sinv,
                        const double2* BC, const double2* SH, int N, int Vh, Gate gate,
                        cudaStream_t s, int tile) {
+  if ((tile & UPD_TC) && bcg_update_tc_supported(sk, xk, N))
+    return bcg_update_tc(sk, Q, P, X, Sinv, BC, SH, N, Vh, gate, s);
+  tile &= ~UPD_TC;
   if (sk == FK_DF && xk == FK_DF)
     return launch_bcg_update<StoreDF, StoreDF>(Q, P, X, Sinv, BC, SH, N, Vh, gate, tile, s);
   if (sk == FK_F32 && xk == FK_DF)

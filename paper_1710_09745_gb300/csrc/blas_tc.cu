@@ -1,0 +1,311 @@
+// Tensor-core form of the fused blockCGrQ update (Algorithm 1: Q = W S^-1,
+// X += P (beta C), P = Q + P S^dag) for the 16-bit storage kinds, where the
+// streaming multi-BLAS of Sec. 6.3 is a dense contraction once N >= 16:
+// every row (site, colour) of W and P is multiplied by three N x N complex
+// coefficient matrices.  On the FP32 pipes that costs 8 N^2 multiply-adds
+// per row, read from shared memory; here each warp runs them as
+// mma.sync m16n8k16 products with FP32 accumulation.
+//
+// Real form.  A complex row a (N entries, stored re/im-interleaved) times a
+// complex N x N matrix M is the real row [re_0, im_0, re_1, ...] (2N) times
+// the 2N x 2N real matrix M' with
+//   M'[2i][2j] = Re M_ij,  M'[2i+1][2j] = -Im M_ij,
+//   M'[2i][2j+1] = Im M_ij, M'[2i+1][2j+1] = Re M_ij,
+// so the stored 16-bit rows are the MMA's A operand as they are (one 32-bit
+// (re, im) pair per A register) and M' is the B operand.
+//
+// Exactness.  The stored W and P are 16-bit numbers, exact MMA inputs.  Each
+// coefficient column j is scaled by a power of two s_j (its largest entry
+// lands near 2^13, inside FP16's range) and split into NSL 16-bit slices
+// (FP16: 2 slices, 22 significant bits; BF16: 3 slices, 24 bits); the slices
+// are multiplied with the same A fragments and accumulated in FP32, and s_j is
+// removed exactly in the epilogue.  The coefficient error is thus below
+// 2^-22 of the column's largest entry, at or below the FP32 rounding of the
+// FP32-pipe kernel, far below the 16-bit storage rounding of the results.
+//
+// Work split.  A warp owns 16 consecutive rows (a 16 x 2N A tile) and loops
+// over output column tiles of 4 complex columns (an 8-wide MMA n tile): for
+// each it forms Q (S^-1 is upper triangular: k blocks wholly below the
+// diagonal are skipped), then P = Q + P S^dag (lower triangular) seeded with
+// Q in the accumulator, then the increment P (beta C), which is added to
+// the double-float X.  The k order inside each 16-column k block is permuted
+// (consistently in A and B; a sum does not depend on its order) so that a
+// thread's A registers for two k steps are 4 consecutive complex numbers of
+// its row: one 128-bit load.  B fragments of all three matrices are built
+// once per CTA in shared memory in fragment order (one 64-bit load per MMA,
+// conflict-free).
+#include <type_traits>
+
+#include "internal.h"
+
+namespace bcg {
+
+namespace {
+
+template <class SS>
+struct TcKind;
+template <>
+struct TcKind<StoreH16> {
+  static constexpr int NSL = 2;
+  static __device__ __forceinline__ uint32_t pack(double a, double b, double* ra, double* rb) {
+    __half ha = __double2half(a), hb = __double2half(b);
+    *ra = a - (double)__half2float(ha);
+    *rb = b - (double)__half2float(hb);
+    __half2 h = __halves2half2(ha, hb);
+    return *reinterpret_cast<uint32_t*>(&h);
+  }
+  static __device__ __forceinline__ uint32_t out(float a, float b) {
+    __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+  }
+  static __device__ __forceinline__ void mma(float (&d)[4], const uint32_t (&a)[4], uint2 b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y));
+  }
+};
+template <>
+struct TcKind<StoreBF16> {
+  static constexpr int NSL = 3;
+  static __device__ __forceinline__ uint32_t pack(double a, double b, double* ra, double* rb) {
+    __nv_bfloat16 ha = __double2bfloat16(a), hb = __double2bfloat16(b);
+    *ra = a - (double)__bfloat162float(ha);
+    *rb = b - (double)__bfloat162float(hb);
+    __nv_bfloat162 h = __halves2bfloat162(ha, hb);
+    return *reinterpret_cast<uint32_t*>(&h);
+  }
+  static __device__ __forceinline__ uint32_t out(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+  }
+  static __device__ __forceinline__ void mma(float (&d)[4], const uint32_t (&a)[4], uint2 b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y));
+  }
+};
+
+constexpr int TC_WARPS = 8;  // warps per CTA
+
+// coefficient entry (i, j) of matrix m in its triangular pattern: 0 = S^-1
+// (upper), 1 = beta C (full), 2 = S^dag (lower)
+__device__ __forceinline__ bool tc_in_pattern(int m, int i, int j) {
+  return m == 1 || (m == 0 ? i <= j : i >= j);
+}
+
+}  // namespace
+
+// Shared memory: B fragments [3][NSL][KS][NT][32] uint2, then the inverse
+// column scales [3][N] float.  KS = N / 8 k steps of 16 reals, NT = N / 4
+// n tiles of 8 reals.
+template <class SS, int N>
+__global__ void __launch_bounds__(TC_WARPS * 32, N >= 32 ? 3 : 4)
+    k_bcg_update_tc(typename SS::elem* __restrict__ Q, typename SS::elem* __restrict__ P,
+                    StoreDF::elem* __restrict__ X, const double2* __restrict__ Sinv,
+                    const double2* __restrict__ BC, const double2* __restrict__ SH, int Vh,
+                    Gate gate) {
+  using K = TcKind<SS>;
+  constexpr int NSL = K::NSL;
+  constexpr int KS = N / 8, NT = N / 4, MB = N / 16;
+  constexpr int FR = KS * NT * 32;  // fragments per slice of one matrix
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint2* sB = reinterpret_cast<uint2*>(smem_raw);
+  float* sInv = reinterpret_cast<float*>(sB + 3 * NSL * FR);
+  __shared__ double sScale[3 * N];
+  if (gate_closed(gate)) return;
+  const bool keepP = gate.st != nullptr && ((const volatile SolverStatus*)gate.st)->ru_pending;
+  auto Ms = [&](int m) { return m == 0 ? Sinv : m == 1 ? BC : SH; };
+
+  // column scales: a power of two that takes the column's largest entry to
+  // [2^12, 2^13) (1 for an all-zero column)
+  for (int c = threadIdx.x; c < 3 * N; c += blockDim.x) {
+    const int m = c / N, j = c - m * N;
+    double mx = 0.0;
+    for (int i = 0; i < N; ++i) {
+      if (!tc_in_pattern(m, i, j)) continue;
+      const double2 v = Ms(m)[i * N + j];
+      mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+    }
+    int e = 0;
+    if (mx > 0.0) frexp(mx, &e);  // mx in [2^(e-1), 2^e)
+    const int sh = mx > 0.0 ? 13 - e : 0;
+    sScale[c] = ldexp(1.0, sh);
+    sInv[c] = (float)ldexp(1.0, -sh);
+  }
+  __syncthreads();
+  // B fragments.  For k step ks (k block mb = ks / 2, half hh = ks % 2) and
+  // lane (g = lane / 4, t = lane % 4): register b0 holds rows (re, im) of
+  // input i0 = 16 mb + 4 t + 2 hh, b1 those of i0 + 1; the column is
+  // n = 8 nt + g, i.e. complex column j = n / 2, real part when n is even.
+  for (int idx = threadIdx.x; idx < 3 * FR; idx += blockDim.x) {
+    const int m = idx / FR;
+    int r = idx - m * FR;
+    const int ks = r / (NT * 32);
+    r -= ks * NT * 32;
+    const int nt = r / 32, lane = r - nt * 32;
+    const int g = lane >> 2, t = lane & 3;
+    const int i0 = 16 * (ks >> 1) + 4 * t + 2 * (ks & 1);
+    const int n = 8 * nt + g, j = n >> 1, part = n & 1;
+    const double sc = sScale[m * N + j];
+    double e[2][2];  // [input i0 / i0 + 1][re row, im row]
+    for (int q = 0; q < 2; ++q) {
+      const int i = i0 + q;
+      double re = 0.0, im = 0.0;
+      if (tc_in_pattern(m, i, j)) {
+        const double2 v = Ms(m)[i * N + j];
+        re = v.x * sc;
+        im = v.y * sc;
+      }
+      e[q][0] = part ? im : re;
+      e[q][1] = part ? re : -im;
+    }
+    for (int sl = 0; sl < NSL; ++sl) {
+      uint2 b;
+      b.x = K::pack(e[0][0], e[0][1], &e[0][0], &e[0][1]);
+      b.y = K::pack(e[1][0], e[1][1], &e[1][0], &e[1][1]);
+      sB[((m * NSL + sl) * KS + ks) * NT * 32 + nt * 32 + lane] = b;
+    }
+  }
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const long long nrows = 3LL * Vh;
+  const long long ntiles = (nrows + 15) / 16;
+  constexpr float unraw = 1.f / SS::RAW_SCALE;
+  const uint32_t* Qw = reinterpret_cast<const uint32_t*>(Q);
+  const uint32_t* Pw = reinterpret_cast<const uint32_t*>(P);
+  for (long long tile = (long long)blockIdx.x * TC_WARPS + (threadIdx.x >> 5); tile < ntiles;
+       tile += (long long)gridDim.x * TC_WARPS) {
+    const long long ra = tile * 16 + g, rb = ra + 8;
+    const bool va = ra < nrows, vb = rb < nrows;
+    // A fragments of W (held in the Q buffer) and P: per k block, the four
+    // complex numbers 16 mb + 4t .. + 3 of rows ra and rb
+    uint4 wa[MB], wb[MB], pa[MB], pb[MB];
+#pragma unroll
+    for (int mb = 0; mb < MB; ++mb) {
+      const int c0 = 16 * mb + 4 * t;
+      const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+      wa[mb] = va ? *reinterpret_cast<const uint4*>(Qw + ra * N + c0) : z;
+      wb[mb] = vb ? *reinterpret_cast<const uint4*>(Qw + rb * N + c0) : z;
+      pa[mb] = va ? *reinterpret_cast<const uint4*>(Pw + ra * N + c0) : z;
+      pb[mb] = vb ? *reinterpret_cast<const uint4*>(Pw + rb * N + c0) : z;
+    }
+    auto afrag = [&](const uint4* xa, const uint4* xb, int ks, uint32_t (&a)[4]) {
+      const uint4 ua = xa[ks >> 1], ub = xb[ks >> 1];
+      const bool hi = ks & 1;
+      a[0] = hi ? ua.z : ua.x;
+      a[1] = hi ? ub.z : ub.x;
+      a[2] = hi ? ua.w : ua.y;
+      a[3] = hi ? ub.w : ub.y;
+    };
+#pragma unroll 1
+    for (int nt = 0; nt < NT; ++nt) {
+      const int j = 4 * nt + t;  // this thread's complex output column
+      float q[4] = {0.f, 0.f, 0.f, 0.f};
+      // Q = W S^-1: k blocks with an entry i <= the tile's last column
+#pragma unroll
+      for (int ks = 0; ks < KS; ++ks) {
+        if (16 * (ks >> 1) > 4 * nt + 3) continue;
+        uint32_t a[4];
+        afrag(wa, wb, ks, a);
+#pragma unroll
+        for (int sl = 0; sl < NSL; ++sl) K::mma(q, a, sB[((0 * NSL + sl) * KS + ks) * NT * 32 + nt * 32 + lane]);
+      }
+      const float i0s = sInv[j];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) q[e] *= i0s;  // Q in the stored (raw) scale
+      const long long oa = ra * N + j, ob = rb * N + j;
+      uint32_t* Qo = reinterpret_cast<uint32_t*>(Q);
+      if (va) Qo[oa] = K::out(q[0], q[1]);
+      if (vb) Qo[ob] = K::out(q[2], q[3]);
+      if (!keepP) {
+        // P = Q + P S^dag, with Q seeding the accumulator in S^dag's scale
+        const float s2 = (float)sScale[2 * N + j];
+        float p[4] = {q[0] * s2, q[1] * s2, q[2] * s2, q[3] * s2};
+#pragma unroll
+        for (int ks = 0; ks < KS; ++ks) {
+          if (16 * (ks >> 1) + 15 < 4 * nt) continue;
+          uint32_t a[4];
+          afrag(pa, pb, ks, a);
+#pragma unroll
+          for (int sl = 0; sl < NSL; ++sl) K::mma(p, a, sB[((2 * NSL + sl) * KS + ks) * NT * 32 + nt * 32 + lane]);
+        }
+        const float i2s = sInv[2 * N + j];
+        uint32_t* Po = reinterpret_cast<uint32_t*>(P);
+        if (va) Po[oa] = K::out(p[0] * i2s, p[1] * i2s);
+        if (vb) Po[ob] = K::out(p[2] * i2s, p[3] * i2s);
+      }
+      // X += P (beta C), the increment from the old P (still in registers)
+      float x[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int ks = 0; ks < KS; ++ks) {
+        uint32_t a[4];
+        afrag(pa, pb, ks, a);
+#pragma unroll
+        for (int sl = 0; sl < NSL; ++sl) K::mma(x, a, sB[((1 * NSL + sl) * KS + ks) * NT * 32 + nt * 32 + lane]);
+      }
+      const float i1s = sInv[N + j] * unraw;
+#pragma unroll
+      for (int hrow = 0; hrow < 2; ++hrow) {
+        if (!(hrow ? vb : va)) continue;
+        StoreDF::elem* xp = X + (hrow ? ob : oa);
+        cpx<dfacc> xa = cacc_from<CompDF>(StoreDF::load_nc(xp));
+        CompDF::add(xa.re, df{x[2 * hrow] * i1s, 0.f});
+        CompDF::add(xa.im, df{x[2 * hrow + 1] * i1s, 0.f});
+        StoreDF::store(xp, cfin<CompDF>(xa));
+      }
+    }
+  }
+}
+
+template <class SS, int N>
+static cudaError_t launch_bcg_update_tc(void* Q, void* P, void* X, const double2* Sinv,
+                                        const double2* BC, const double2* SH, int Vh, Gate gate,
+                                        cudaStream_t s) {
+  constexpr int NSL = TcKind<SS>::NSL;
+  const size_t sm = (size_t)3 * NSL * (N / 8) * (N / 4) * 32 * sizeof(uint2) + 3 * N * sizeof(float);
+  auto kern = k_bcg_update_tc<SS, N>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TC_WARPS * 32, sm) != cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    cudaGetLastError();
+  if (gate_mostly_off(gate) && per_sm > 2) per_sm = 2;
+  const long long tiles = (3LL * Vh + 15) / 16;
+  long long blocks = (tiles + TC_WARPS - 1) / TC_WARPS;
+  if (blocks > (long long)sms * per_sm) blocks = (long long)sms * per_sm;
+  if (blocks < 1) blocks = 1;
+  kern<<<(unsigned)blocks, TC_WARPS * 32, sm, s>>>((typename SS::elem*)Q, (typename SS::elem*)P,
+                                                  (StoreDF::elem*)X, Sinv, BC, SH, Vh, gate);
+  return cudaGetLastError();
+}
+
+bool bcg_update_tc_supported(FieldKind sk, FieldKind xk, int N) {
+  return (sk == FK_H16 || sk == FK_BF16) && xk == FK_DF && (N == 16 || N == 32);
+}
+
+cudaError_t bcg_update_tc(FieldKind sk, void* Q, void* P, void* X, const double2* Sinv,
+                          const double2* BC, const double2* SH, int N, int Vh, Gate gate,
+                          cudaStream_t s) {
+  if (sk == FK_H16) {
+    if (N == 16) return launch_bcg_update_tc<StoreH16, 16>(Q, P, X, Sinv, BC, SH, Vh, gate, s);
+    if (N == 32) return launch_bcg_update_tc<StoreH16, 32>(Q, P, X, Sinv, BC, SH, Vh, gate, s);
+  } else if (sk == FK_BF16) {
+    if (N == 16) return launch_bcg_update_tc<StoreBF16, 16>(Q, P, X, Sinv, BC, SH, Vh, gate, s);
+    if (N == 32) return launch_bcg_update_tc<StoreBF16, 32>(Q, P, X, Sinv, BC, SH, Vh, gate, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace bcg

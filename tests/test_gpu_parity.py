@@ -513,3 +513,32 @@ def test_forced_blas_tiles_converge(tmp_path, prec, kind, upd):
     assert info["status"] == 0
     assert _oracle_rel_res(dims, fat, lng, mass, b, gh.to_np(X)).max() <= 1e-10
     assert f'"blas/8.8.8.8/kind{kind}/N{N}/{dev}": {packed}' in cache.read_text()
+
+
+@pytest.mark.parametrize("prec,kind", [("mixed_f16", 3), ("mixed_bf16", 4)])
+@pytest.mark.parametrize("N", [16, 32])
+@pytest.mark.parametrize("dims", [(8, 8, 8, 8), (6, 6, 6, 2)])
+def test_tensor_core_update_converges(tmp_path, prec, kind, N, dims):
+    """The tensor-core fused update (tile flag bit 24 of the cached BLAS
+    choice), forced through the tuning cache for the 16-bit forms; 6x6x6x2
+    has 3 V_h = 648 rows, a ragged last 16-row tile.  Each solve meets tol on
+    the oracle's residual, in about as many iterations as with the FP32-pipe
+    update."""
+    import json
+    torch = gh.torch_mod()
+    mass = 0.05
+    dev = torch.cuda.get_device_name(0).replace(" ", "_").replace('"', "_").replace("\\", "_")
+    tag = ".".join(str(d) for d in dims)
+    b = hi.gaussian_sources(dims, N, seed=2026)
+    iters = {}
+    for name, upd in (("tc", 1 << 24), ("pipes", 8)):
+        cache = tmp_path / f"tiles_{name}.json"
+        packed = upd | (16 << 8) | (32 << 16)
+        cache.write_text(json.dumps({f"blas/{tag}/kind{kind}/N{N}/{dev}": packed}))
+        s, fat, lng = gh.make_solver(dims, mass, prec=prec, seed=1026, max_rhs=N)
+        s.set_tune_cache(cache)
+        X, info = s.solve(b, tol=1e-10)
+        assert info["status"] == 0, name
+        assert _oracle_rel_res(dims, fat, lng, mass, b, gh.to_np(X)).max() <= 1e-10, name
+        iters[name] = info["iters"]
+    assert abs(iters["tc"] - iters["pipes"]) <= max(3, iters["pipes"] // 10), iters
