@@ -424,13 +424,14 @@ struct BlasTiles {
   int upd, gram, wgram;
 };
 // packed: update tile in bits 0..7 (UPD_TC as bit 24), Gram tile in bits
-// 8..15, fused W + Gram tile in bits 16..23
+// 8..15, fused W + Gram tile in bits 16..23 (WG_TC as bit 25)
 BlasTiles unpack_tiles(int v) {
-  return {(v & 0xff) | ((v >> 24) & 1 ? UPD_TC : 0), (v >> 8) & 0xff, (v >> 16) & 0xff};
+  return {(v & 0xff) | ((v >> 24) & 1 ? UPD_TC : 0), (v >> 8) & 0xff,
+          ((v >> 16) & 0xff) | ((v >> 25) & 1 ? WG_TC : 0)};
 }
 int pack_tiles(const BlasTiles& t) {
   return (t.upd & 0xff) | ((t.upd & UPD_TC) ? 1 << 24 : 0) | ((t.gram & 0xff) << 8) |
-         ((t.wgram & 0xff) << 16);
+         ((t.wgram & 0xff) << 16) | ((t.wgram & WG_TC) ? 1 << 25 : 0);
 }
 
 BlasTiles cached_tiles(const blockcg_ctx* h, FieldKind k, int N) {
@@ -518,6 +519,13 @@ void tune_blas(blockcg_ctx* h, const Ws& w, int N) {
       return w_update_gram(k, w.AP, w.Ts, mat(w, M_BETA, N), N, Vh, w.partials, w.nblocks, g0, s, ts);
     });
     if (t < t_wgram) t_wgram = t, best_wgram = ts;
+  }
+  if (w_gram_tc_supported(k, N)) {
+    float t = time3([&] {
+      return w_update_gram(k, w.AP, w.Ts, mat(w, M_BETA, N), N, Vh, w.partials, w.nblocks, g0, s,
+                           WG_TC);
+    });
+    if (t < t_wgram) t_wgram = t, best_wgram = WG_TC;
   }
   const int packed = pack_tiles({best_upd, best_gram, best_wgram});
   h->tuned_blas[key] = packed;

@@ -520,6 +520,9 @@ static void launch_w_gram(void* Q, const void* AP, const double2* beta, int N, i
 
 cudaError_t w_update_gram(FieldKind k, void* Q, const void* AP, const double2* beta, int N, int Vh,
                           double2* partials, int nblocks, Gate gate, cudaStream_t s, int tile) {
+  if ((tile & WG_TC) && w_gram_tc_supported(k, N))
+    return w_update_gram_tc(k, Q, AP, beta, N, Vh, partials, nblocks, gate, s);
+  tile &= ~WG_TC;
   switch (k) {
     case FK_DF: launch_w_gram<StoreDF>(Q, AP, beta, N, Vh, partials, nblocks, gate, tile, s); break;
     case FK_F32: launch_w_gram<StoreF32>(Q, AP, beta, N, Vh, partials, nblocks, gate, tile, s); break;

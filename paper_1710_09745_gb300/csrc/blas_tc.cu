@@ -58,6 +58,9 @@ struct TcKind<StoreH16> {
     __half2 h = __floats2half2_rn(a, b);
     return *reinterpret_cast<uint32_t*>(&h);
   }
+  static __device__ __forceinline__ float2 in(uint32_t u) {
+    return __half22float2(*reinterpret_cast<const __half2*>(&u));
+  }
   static __device__ __forceinline__ void mma(float (&d)[4], const uint32_t (&a)[4], uint2 b) {
     asm volatile(
         "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
@@ -79,6 +82,9 @@ struct TcKind<StoreBF16> {
   static __device__ __forceinline__ uint32_t out(float a, float b) {
     __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
     return *reinterpret_cast<uint32_t*>(&h);
+  }
+  static __device__ __forceinline__ float2 in(uint32_t u) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u));
   }
   static __device__ __forceinline__ void mma(float (&d)[4], const uint32_t (&a)[4], uint2 b) {
     asm volatile(
@@ -289,6 +295,275 @@ static cudaError_t launch_bcg_update_tc(void* Q, void* P, void* X, const double2
   kern<<<(unsigned)blocks, TC_WARPS * 32, sm, s>>>((typename SS::elem*)Q, (typename SS::elem*)P,
                                                   (StoreDF::elem*)X, Sinv, BC, SH, Vh, gate);
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// W = Q - AP beta and the Gram W^dag W of the thin QR (Algorithm 2) in one
+// pass, on the tensor cores, for the 16-bit kinds.  A CTA tile is
+// TC_WARPS x 16 rows.  Phase 1: each warp forms W for its 16 rows as the
+// update kernel forms Q (A = AP, B = -beta split and column-scaled, the
+// accumulator seeded with Q), stores W (in place of Q, rounded to the storage
+// format) and copies the rounded rows into a padded shared-memory tile.
+// Phase 2: the real Gram G = W_r^T W_r of the tile's real rows (2N columns)
+// is taken with the rows as the MMA's k dimension: ldmatrix.trans turns the
+// row-major tile into the transposed A and B fragments.  The complex Gram is
+//   K_ij = G[2i][2j] + G[2i+1][2j+1] + i (G[2i][2j+1] - G[2i+1][2j]),
+// Hermitian, so only 16 x 8 blocks of G that hold an entry i <= j are
+// formed, spread over the CTA's warps.  Each block's sum over a tile (128
+// rows) is exact up to FP32 rounding of its 128 products (16-bit inputs),
+// then added to a double-float accumulator; the CTA writes its upper-triangle
+// partial sums, which the fixed-order FP64 reduction of the FP32-pipe path
+// combines.  The Gram is that of the stored (rounded) W, the block whose
+// columns Q = W S^-1 orthonormalises.
+__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void* p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x2_t(uint32_t (&r)[2], const void* p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n"
+               : "=r"(r[0]), "=r"(r[1])
+               : "r"(a));
+}
+
+// Gram blocks (mt, nt) of G holding an entry i <= j: G rows 16 mt .. + 15
+// (complex i = 8 mt .. + 7), columns 8 nt .. + 7 (complex j = 4 nt .. + 3)
+template <int N>
+struct GramBlocks {
+  static constexpr int MT = N / 8, NT = N / 4;
+  static constexpr int count() {
+    int c = 0;
+    for (int mt = 0; mt < MT; ++mt)
+      for (int nt = 0; nt < NT; ++nt)
+        if (8 * mt <= 4 * nt + 3) ++c;
+    return c;
+  }
+  static constexpr int COUNT = count();
+  static constexpr int PER_WARP = (COUNT + TC_WARPS - 1) / TC_WARPS;
+  // the b-th block in row-major order
+  static __device__ __forceinline__ void at(int b, int& mt, int& nt) {
+    int c = 0;
+    for (int m = 0; m < MT; ++m)
+      for (int n = 0; n < NT; ++n)
+        if (8 * m <= 4 * n + 3) {
+          if (c == b) {
+            mt = m;
+            nt = n;
+            return;
+          }
+          ++c;
+        }
+    mt = nt = 0;
+  }
+};
+
+template <class SS, int N>
+__global__ void __launch_bounds__(TC_WARPS * 32, N >= 32 ? 3 : 4)
+    k_w_gram_tc(typename SS::elem* __restrict__ Q, const typename SS::elem* __restrict__ AP,
+                const double2* __restrict__ beta, int Vh, double2* __restrict__ partials,
+                Gate gate) {
+  using K = TcKind<SS>;
+  using GB = GramBlocks<N>;
+  constexpr int NSL = K::NSL;
+  constexpr int KS = N / 8, NT = N / 4, MB = N / 16;
+  constexpr int FR = KS * NT * 32;
+  constexpr int TR = TC_WARPS * 16;  // rows per CTA tile
+  constexpr int RW = N + 4;          // shared tile row stride in 32-bit words (16 B pad)
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint2* sB = reinterpret_cast<uint2*>(smem_raw);
+  float* sInv = reinterpret_cast<float*>(sB + NSL * FR);
+  uint32_t* sW = reinterpret_cast<uint32_t*>(sInv + N);  // [TR][RW] (re, im) pairs
+  __shared__ double sScale[N];
+  if (gate_closed(gate)) return;
+
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    double mx = 0.0;
+    for (int i = 0; i < N; ++i) {
+      const double2 v = beta[i * N + j];
+      mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+    }
+    int e = 0;
+    if (mx > 0.0) frexp(mx, &e);
+    const int sh = mx > 0.0 ? 13 - e : 0;
+    sScale[j] = ldexp(1.0, sh);
+    sInv[j] = (float)ldexp(1.0, -sh);
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < FR; idx += blockDim.x) {
+    const int ks = idx / (NT * 32);
+    const int r = idx - ks * NT * 32;
+    const int nt = r / 32, lane = r - nt * 32;
+    const int g = lane >> 2, t = lane & 3;
+    const int i0 = 16 * (ks >> 1) + 4 * t + 2 * (ks & 1);
+    const int n = 8 * nt + g, j = n >> 1, part = n & 1;
+    const double sc = -sScale[j];  // B = -beta
+    double e[2][2];
+    for (int q = 0; q < 2; ++q) {
+      const double2 v = beta[(i0 + q) * N + j];
+      const double re = v.x * sc, im = v.y * sc;
+      e[q][0] = part ? im : re;
+      e[q][1] = part ? re : -im;
+    }
+    for (int sl = 0; sl < NSL; ++sl) {
+      uint2 b;
+      b.x = K::pack(e[0][0], e[0][1], &e[0][0], &e[0][1]);
+      b.y = K::pack(e[1][0], e[1][1], &e[1][0], &e[1][1]);
+      sB[(sl * KS + ks) * NT * 32 + nt * 32 + lane] = b;
+    }
+  }
+  __syncthreads();
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const long long nrows = 3LL * Vh;
+  constexpr float unraw = 1.f / SS::RAW_SCALE;
+  const uint32_t* APw = reinterpret_cast<const uint32_t*>(AP);
+  uint32_t* Qw = reinterpret_cast<uint32_t*>(Q);
+  dfacc gacc[GB::PER_WARP][4];
+#pragma unroll
+  for (int b = 0; b < GB::PER_WARP; ++b)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) gacc[b][e] = CompDF::zero();
+
+  for (long long tile = blockIdx.x; tile * TR < nrows; tile += gridDim.x) {
+    // phase 1: W for rows tile * TR + 16 warp + (g, g + 8)
+    const int la = 16 * warp + g, lb = la + 8;  // rows in the shared tile
+    const long long ra = tile * TR + la, rb = tile * TR + lb;
+    const bool va = ra < nrows, vb = rb < nrows;
+    uint4 apa[MB], apb[MB];
+#pragma unroll
+    for (int mb = 0; mb < MB; ++mb) {
+      const int c0 = 16 * mb + 4 * t;
+      const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+      apa[mb] = va ? *reinterpret_cast<const uint4*>(APw + ra * N + c0) : z;
+      apb[mb] = vb ? *reinterpret_cast<const uint4*>(APw + rb * N + c0) : z;
+    }
+#pragma unroll 1
+    for (int nt = 0; nt < NT; ++nt) {
+      const int j = 4 * nt + t;
+      const float sj = (float)sScale[j];
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      if (va) {
+        const float2 qa = TcKind<SS>::in(Qw[ra * N + j]);
+        acc[0] = qa.x * sj;
+        acc[1] = qa.y * sj;
+      }
+      if (vb) {
+        const float2 qb = TcKind<SS>::in(Qw[rb * N + j]);
+        acc[2] = qb.x * sj;
+        acc[3] = qb.y * sj;
+      }
+#pragma unroll
+      for (int ks = 0; ks < KS; ++ks) {
+        const uint4 ua = apa[ks >> 1], ub = apb[ks >> 1];
+        const bool hi = ks & 1;
+        const uint32_t a[4] = {hi ? ua.z : ua.x, hi ? ub.z : ub.x, hi ? ua.w : ua.y,
+                               hi ? ub.w : ub.y};
+#pragma unroll
+        for (int sl = 0; sl < NSL; ++sl) K::mma(acc, a, sB[(sl * KS + ks) * NT * 32 + nt * 32 + lane]);
+      }
+      const float ij = sInv[j];
+      const uint32_t wa = va ? K::out(acc[0] * ij, acc[1] * ij) : 0u;
+      const uint32_t wb = vb ? K::out(acc[2] * ij, acc[3] * ij) : 0u;
+      if (va) Qw[ra * N + j] = wa;
+      if (vb) Qw[rb * N + j] = wb;
+      sW[la * RW + j] = wa;  // rows past the end hold zeros
+      sW[lb * RW + j] = wb;
+    }
+    __syncthreads();
+    // phase 2: this warp's Gram blocks over the tile's TR rows
+#pragma unroll
+    for (int bb = 0; bb < GB::PER_WARP; ++bb) {
+      const int b = warp + bb * TC_WARPS;
+      if (b >= GB::COUNT) break;
+      int mt, nt;
+      GB::at(b, mt, nt);
+      float d[4] = {0.f, 0.f, 0.f, 0.f};
+      const int q = lane >> 3, rr = lane & 7;
+#pragma unroll 2
+      for (int ks = 0; ks < TR / 16; ++ks) {
+        // A = W^T (rows 16 mt.. of G, k = tile rows 16 ks..): matrices
+        // (rows +0/+8) x (columns +0/+8 halves); B = W (k rows, columns 8 nt..)
+        const int arow = 16 * ks + (q >> 1) * 8 + rr;
+        const int acol = 8 * mt + (q & 1) * 4;  // in 32-bit words: 16 mt halves
+        uint32_t a[4];
+        ldsm_x4_t(a, sW + arow * RW + acol);
+        // ldmatrix.x4 matrix order: 0 = (rows +0, cols +0), 1 = (rows +0, cols
+        // +8), 2 = (rows +8, cols +0), 3 = (rows +8, cols +8); the A fragment
+        // wants (m +0, k +0), (m +8, k +0), (m +0, k +8), (m +8, k +8) with
+        // m = G row (tile column) and k = tile row
+        const uint32_t af[4] = {a[0], a[1], a[2], a[3]};
+        const int brow = 16 * ks + (q & 1) * 8 + rr;
+        uint32_t bf[2];
+        ldsm_x2_t(bf, sW + brow * RW + 4 * nt);
+        K::mma(d, af, make_uint2(bf[0], bf[1]));
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) CompDF::add(gacc[bb][e], df{d[e], 0.f});
+    }
+    __syncthreads();
+  }
+
+  // partial sums of the upper triangle: combine the lane pair (g even, g + 1)
+  // that holds G rows (2i, 2i + 1)
+  double2* out = partials + (long long)blockIdx.x * N * N;
+  const double s2 = (double)unraw * (double)unraw;
+#pragma unroll
+  for (int bb = 0; bb < GB::PER_WARP; ++bb) {
+    const int b = warp + bb * TC_WARPS;
+    if (b >= GB::COUNT) break;  // uniform per warp
+    int mt, nt;
+    GB::at(b, mt, nt);
+    double v[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[e] = (double)gacc[bb][e].s + (double)gacc[bb][e].e;
+    double p[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) p[e] = __shfl_xor_sync(0xffffffffu, v[e], 4);
+    if ((g & 1) == 0) {
+      const int j = 4 * nt + t;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int i = 8 * mt + (g >> 1) + 4 * h;
+        if (i <= j) {
+          const double kre = v[2 * h] + p[2 * h + 1];
+          const double kim = v[2 * h + 1] - p[2 * h];
+          out[i * N + j] = make_double2(kre * s2, kim * s2);
+        }
+      }
+    }
+  }
+}
+
+template <class SS, int N>
+static cudaError_t launch_w_gram_tc(void* Q, const void* AP, const double2* beta, int Vh,
+                                    double2* partials, int nblocks, Gate gate, cudaStream_t s) {
+  constexpr int NSL = TcKind<SS>::NSL;
+  const size_t sm = (size_t)NSL * (N / 8) * (N / 4) * 32 * sizeof(uint2) + N * sizeof(float) +
+                    (size_t)TC_WARPS * 16 * (N + 4) * sizeof(uint32_t);
+  auto kern = k_w_gram_tc<SS, N>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  kern<<<nblocks, TC_WARPS * 32, sm, s>>>((typename SS::elem*)Q, (const typename SS::elem*)AP,
+                                          beta, Vh, partials, gate);
+  return cudaGetLastError();
+}
+
+bool w_gram_tc_supported(FieldKind k, int N) {
+  return (k == FK_H16 || k == FK_BF16) && (N == 16 || N == 32);
+}
+
+cudaError_t w_update_gram_tc(FieldKind k, void* Q, const void* AP, const double2* beta, int N,
+                             int Vh, double2* partials, int nblocks, Gate gate, cudaStream_t s) {
+  if (k == FK_H16) {
+    if (N == 16) return launch_w_gram_tc<StoreH16, 16>(Q, AP, beta, Vh, partials, nblocks, gate, s);
+    if (N == 32) return launch_w_gram_tc<StoreH16, 32>(Q, AP, beta, Vh, partials, nblocks, gate, s);
+  } else if (k == FK_BF16) {
+    if (N == 16) return launch_w_gram_tc<StoreBF16, 16>(Q, AP, beta, Vh, partials, nblocks, gate, s);
+    if (N == 32) return launch_w_gram_tc<StoreBF16, 32>(Q, AP, beta, Vh, partials, nblocks, gate, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 bool bcg_update_tc_supported(FieldKind sk, FieldKind xk, int N) {

@@ -518,12 +518,13 @@ def test_forced_blas_tiles_converge(tmp_path, prec, kind, upd):
 @pytest.mark.parametrize("prec,kind", [("mixed_f16", 3), ("mixed_bf16", 4)])
 @pytest.mark.parametrize("N", [16, 32])
 @pytest.mark.parametrize("dims", [(8, 8, 8, 8), (6, 6, 6, 2)])
-def test_tensor_core_update_converges(tmp_path, prec, kind, N, dims):
-    """The tensor-core fused update (tile flag bit 24 of the cached BLAS
-    choice), forced through the tuning cache for the 16-bit forms; 6x6x6x2
-    has 3 V_h = 648 rows, a ragged last 16-row tile.  Each solve meets tol on
+def test_tensor_core_blas_converge(tmp_path, prec, kind, N, dims):
+    """The tensor-core fused update (bit 24 of the cached BLAS choice) and
+    fused W + Gram (bit 25), each alone and together, forced through the
+    tuning cache for the 16-bit forms; 6x6x6x2 has 3 V_h = 648 rows, a ragged
+    last 16-row tile and a ragged 128-row Gram tile.  Each solve meets tol on
     the oracle's residual, in about as many iterations as with the FP32-pipe
-    update."""
+    kernels."""
     import json
     torch = gh.torch_mod()
     mass = 0.05
@@ -531,9 +532,10 @@ def test_tensor_core_update_converges(tmp_path, prec, kind, N, dims):
     tag = ".".join(str(d) for d in dims)
     b = hi.gaussian_sources(dims, N, seed=2026)
     iters = {}
-    for name, upd in (("tc", 1 << 24), ("pipes", 8)):
+    for name, flags in (("pipes", 0), ("upd", 1 << 24), ("wgram", 1 << 25),
+                        ("both", (1 << 24) | (1 << 25))):
         cache = tmp_path / f"tiles_{name}.json"
-        packed = upd | (16 << 8) | (32 << 16)
+        packed = 8 | (16 << 8) | (32 << 16) | flags
         cache.write_text(json.dumps({f"blas/{tag}/kind{kind}/N{N}/{dev}": packed}))
         s, fat, lng = gh.make_solver(dims, mass, prec=prec, seed=1026, max_rhs=N)
         s.set_tune_cache(cache)
@@ -541,4 +543,5 @@ def test_tensor_core_update_converges(tmp_path, prec, kind, N, dims):
         assert info["status"] == 0, name
         assert _oracle_rel_res(dims, fat, lng, mass, b, gh.to_np(X)).max() <= 1e-10, name
         iters[name] = info["iters"]
-    assert abs(iters["tc"] - iters["pipes"]) <= max(3, iters["pipes"] // 10), iters
+    for name in ("upd", "wgram", "both"):
+        assert abs(iters[name] - iters["pipes"]) <= max(3, iters["pipes"] // 10), iters
