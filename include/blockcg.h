@@ -120,10 +120,8 @@ typedef struct {
                           plus one of: 256 for the bulk-copy (TMA) pipelined
                           kernel, 512 for the per-thread cp.async prefetch
                           kernel, 4096 for the plain kernel on a persistent
-                          grid of contiguous site ranges, 8192 for the plain
-                          kernel with a two-hop register pipeline (32- and
-                          16-bit forms; the plain kernel otherwise).  Other
-                          values: BLOCKCG_ERR_ARG */
+                          grid of contiguous site ranges.  Other values:
+                          BLOCKCG_ERR_ARG */
   int link_recon;      /* iteration links of the 32- and 16-bit forms: 0 = all 18
                           reals per link (default); 12 = the first two rows only,
                           the third rebuilt in the stencil as conj(row0 x row1)

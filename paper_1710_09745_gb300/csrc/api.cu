@@ -371,17 +371,14 @@ int stencil_R(blockcg_ctx* h, FieldKind k, int N, const void* links, const void*
     return best;
   }
   Gate g0{nullptr, GATE_ALWAYS};
-  const int cands[15] = {1, 2, 4, 8, 1 | DSLASH_TMA, 2 | DSLASH_TMA, 4 | DSLASH_TMA, 8 | DSLASH_TMA,
-                         1 | DSLASH_ASYNC, 2 | DSLASH_ASYNC, 4 | DSLASH_ASYNC, 8 | DSLASH_ASYNC,
-                         2 | DSLASH_PIPE, 4 | DSLASH_PIPE, 8 | DSLASH_PIPE};
+  const int cands[12] = {1, 2, 4, 8, 1 | DSLASH_TMA, 2 | DSLASH_TMA, 4 | DSLASH_TMA, 8 | DSLASH_TMA,
+                         1 | DSLASH_ASYNC, 2 | DSLASH_ASYNC, 4 | DSLASH_ASYNC, 8 | DSLASH_ASYNC};
   for (int R : cands) {
     if ((R & 0xff) > 1 && (R & 0xff) > N) continue;
     if (rf) {  // two-row links: the plain kernel only
-      if (R & (DSLASH_TMA | DSLASH_ASYNC | DSLASH_PIPE)) continue;
+      if (R & (DSLASH_TMA | DSLASH_ASYNC)) continue;
       R |= rf;
     }
-    // the register pipeline exists for the 32- and 16-bit kinds only
-    if ((R & DSLASH_PIPE) && (k == FK_DF || k == FK_F64)) continue;
     // double-float with N >= 2: the cp.async kernel only.  Timed alone the
     // plain kernel looks up to 4 % faster, but inside the solve (between the
     // Gram, N x N and update kernels) it ran 12-15 % slower than that timing
@@ -841,7 +838,7 @@ blockcg_status blockcg_create(blockcg_t* out, const int dims[4], double mass,
       prm.check_every < 0 || (int)prm.prec < 0 || (int)prm.prec > 4)
     return BLOCKCG_ERR_ARG;
   {
-    int r = prm.dslash_variant & ~(DSLASH_TMA | DSLASH_ASYNC | DSLASH_BLOCKED | DSLASH_PIPE);
+    int r = prm.dslash_variant & ~(DSLASH_TMA | DSLASH_ASYNC | DSLASH_BLOCKED);
     if (prm.dslash_variant != 0 && r != 1 && r != 2 && r != 4 && r != 8) return BLOCKCG_ERR_ARG;
   }
   if (prm.link_recon != 0 && prm.link_recon != 12) return BLOCKCG_ERR_ARG;

@@ -86,10 +86,6 @@ static constexpr int DSLASH_RECON = 0x400;
 // R | DSLASH_BLOCKED: the plain kernel on a persistent grid whose blocks each
 // walk one contiguous range of sites (cache reuse of neighbours in L1)
 static constexpr int DSLASH_BLOCKED = 0x1000;
-// R | DSLASH_PIPE: the plain kernel with a two-hop register pipeline (the
-// loads of the next hop issued before the arithmetic of the current one);
-// 32- and 16-bit kinds with complete links, else the plain kernel
-static constexpr int DSLASH_PIPE = 0x2000;
 cudaError_t dslash(FieldKind k, int R, int epi, const void* links, const void* in, void* out,
                    const void* c1, const void* c2, double m2, const Geom& g, int out_parity,
                    int N, Gate gate, cudaStream_t s);

@@ -153,16 +153,8 @@ __device__ __forceinline__ void unscale_raw(cpx<A>& v) {
   }
 }
 
-// The two-hop register pipeline (UNROLL_HOPS = 3) holds two hops of operands:
-// resident blocks per SM requested for it by right-hand sides per thread
-template <int R>
-struct PipeBounds {
-  static constexpr int minb = R <= 2 ? 5 : R <= 4 ? 4 : 2;
-};
-
 template <class S, int RV, int V, int EPI, int UNROLL_HOPS, bool RC = false>
-__global__ void __launch_bounds__(BCG_DSLASH_TPB, (UNROLL_HOPS == 3 ? PipeBounds<RV * V>::minb
-                                                                     : PlainBounds<S, RV>::minb))
+__global__ void __launch_bounds__(BCG_DSLASH_TPB, (PlainBounds<S, RV>::minb))
     k_dslash(const typename S::elem* __restrict__ links, const typename S::elem* __restrict__ in,
              typename S::elem* __restrict__ out, const typename S::elem* __restrict__ c1,
              const typename S::elem* __restrict__ c2, double m2d, Geom g, int parity, int N,
@@ -243,21 +235,7 @@ __global__ void __launch_bounds__(BCG_DSLASH_TPB, (UNROLL_HOPS == 3 ? PipeBounds
       fetch(d, U, v);
       apply(U, v);
     };
-    if (UNROLL_HOPS == 3) {
-      // two-hop register pipeline: the loads of hop d + 1 are issued before
-      // the arithmetic of hop d, so every warp keeps two hops of gathers in
-      // flight (the kernel is latency-bound on them)
-      cpx<real> U0[9], U1[9];
-      cpx<real> v0[RV][3][V], v1[RV][3][V];
-      fetch(0, U0, v0);
-#pragma unroll 1
-      for (int d = 0; d < 16; d += 2) {
-        fetch(d + 1, U1, v1);
-        apply(U0, v0);
-        if (d + 2 < 16) fetch(d + 2, U0, v0);
-        apply(U1, v1);
-      }
-    } else if (UNROLL_HOPS == 2) {
+    if (UNROLL_HOPS == 2) {
 #pragma unroll
       for (int d = 0; d < 16; ++d) hop(d);
     } else if (UNROLL_HOPS == 1) {
@@ -811,7 +789,7 @@ static bool launch_async_s(int R, int epi, const void* links, const void* in, vo
 template <class S, int RV, int V, int EPI, bool RC = false>
 static void launch_dslash_t(const void* links, const void* in, void* out, const void* c1,
                             const void* c2, double m2, const Geom& g, int parity, int N,
-                            Gate gate, bool blocked, bool pipe, cudaStream_t s) {
+                            Gate gate, bool blocked, cudaStream_t s) {
   using E = typename S::elem;
 #ifndef BCG_UNROLL_DF
 #define BCG_UNROLL_DF 0
@@ -845,16 +823,6 @@ static void launch_dslash_t(const void* links, const void* in, void* out, const 
     span = per * threads;
     blocks = (unsigned)((threads_total + span - 1) / span);
   }
-  // the register pipeline: 32- and 16-bit kinds with complete links
-  constexpr bool PIPE_OK = !RC && std::is_same<typename S::comp::real, float>::value;
-  if constexpr (PIPE_OK) {
-    if (pipe) {
-      k_dslash<S, RV, V, EPI, 3, RC><<<blocks, threads, 0, s>>>(
-          (const E*)links, (const E*)in, (E*)out, (const E*)c1, (const E*)c2, m2, g, parity, N, T,
-          span, gate);
-      return;
-    }
-  }
   k_dslash<S, RV, V, EPI, UNROLL, RC><<<blocks, threads, 0, s>>>(
       (const E*)links, (const E*)in, (E*)out, (const E*)c1, (const E*)c2, m2, g, parity, N, T, span,
       gate);
@@ -863,16 +831,16 @@ static void launch_dslash_t(const void* links, const void* in, void* out, const 
 template <class S, int RV, int V, bool RC = false>
 static void launch_dslash_r(int epi, const void* links, const void* in, void* out, const void* c1,
                             const void* c2, double m2, const Geom& g, int parity, int N,
-                            Gate gate, bool blocked, bool pipe, cudaStream_t s) {
+                            Gate gate, bool blocked, cudaStream_t s) {
   switch (epi) {
     case EPI_NONE:
-      launch_dslash_t<S, RV, V, EPI_NONE, RC>(links, in, out, c1, c2, m2, g, parity, N, gate, blocked, pipe, s);
+      launch_dslash_t<S, RV, V, EPI_NONE, RC>(links, in, out, c1, c2, m2, g, parity, N, gate, blocked, s);
       break;
     case EPI_NORMAL:
-      launch_dslash_t<S, RV, V, EPI_NORMAL, RC>(links, in, out, c1, c2, m2, g, parity, N, gate, blocked, pipe, s);
+      launch_dslash_t<S, RV, V, EPI_NORMAL, RC>(links, in, out, c1, c2, m2, g, parity, N, gate, blocked, s);
       break;
     default:
-      launch_dslash_t<S, RV, V, EPI_RESIDUAL, RC>(links, in, out, c1, c2, m2, g, parity, N, gate, blocked, pipe, s);
+      launch_dslash_t<S, RV, V, EPI_RESIDUAL, RC>(links, in, out, c1, c2, m2, g, parity, N, gate, blocked, s);
       break;
   }
 }
@@ -882,7 +850,7 @@ static void launch_dslash_r(int epi, const void* links, const void* in, void* ou
 template <class S, bool RC = false>
 static void launch_dslash_s(int R, int epi, const void* links, const void* in, void* out,
                      const void* c1, const void* c2, double m2, const Geom& g, int parity,
-                     int N, Gate gate, bool blocked, bool pipe, cudaStream_t s) {
+                     int N, Gate gate, bool blocked, cudaStream_t s) {
   // vector width V: complex numbers per load (FP32: 2 per 128 bits; 16-bit
   // kinds: 4 per 128 bits or 2 per 64 bits); RV = R / V slots per thread
   constexpr bool F32 = std::is_same<S, StoreF32>::value;
@@ -890,21 +858,21 @@ static void launch_dslash_s(int R, int epi, const void* links, const void* in, v
   constexpr int V2 = (F32 || H) ? 2 : 1;
   constexpr int V4 = H ? 4 : 1;
   if (H && (N % 4) == 0 && R >= 4) {
-    if (R == 4) return launch_dslash_r<S, 1, V4, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, blocked, pipe, s);
-    return launch_dslash_r<S, 2, V4, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, blocked, pipe, s);
+    if (R == 4) return launch_dslash_r<S, 1, V4, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, blocked, s);
+    return launch_dslash_r<S, 2, V4, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, blocked, s);
   }
   if ((F32 || H) && (N % 2) == 0 && R >= 2) {
     switch (R) {
-      case 2: return launch_dslash_r<S, 1, V2, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, blocked, pipe, s);
-      case 4: return launch_dslash_r<S, 2, V2, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, blocked, pipe, s);
-      default: return launch_dslash_r<S, 4, V2, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, blocked, pipe, s);
+      case 2: return launch_dslash_r<S, 1, V2, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, blocked, s);
+      case 4: return launch_dslash_r<S, 2, V2, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, blocked, s);
+      default: return launch_dslash_r<S, 4, V2, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, blocked, s);
     }
   }
   switch (R) {
-    case 1: return launch_dslash_r<S, 1, 1, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, blocked, pipe, s);
-    case 2: return launch_dslash_r<S, 2, 1, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, blocked, pipe, s);
-    case 4: return launch_dslash_r<S, 4, 1, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, blocked, pipe, s);
-    default: return launch_dslash_r<S, 8, 1, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, blocked, pipe, s);
+    case 1: return launch_dslash_r<S, 1, 1, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, blocked, s);
+    case 2: return launch_dslash_r<S, 2, 1, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, blocked, s);
+    case 4: return launch_dslash_r<S, 4, 1, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, blocked, s);
+    default: return launch_dslash_r<S, 8, 1, RC>(epi, links, in, out, c1, c2, m2, g, parity, N, gate, blocked, s);
   }
 }
 
@@ -919,7 +887,7 @@ static cudaError_t dslash_kind(int R, int epi, const void* links, const void* in
   if (R & DSLASH_RECON) {  // two-row links: plain kernel, 32- and 16-bit kinds only
     if constexpr (std::is_same<typename S::comp::real, float>::value) {
       launch_dslash_s<S, true>(R & 0xff, epi, links, in, out, c1, c2, m2, g, out_parity, N, gate,
-                               (R & DSLASH_BLOCKED) != 0, false, s);
+                               (R & DSLASH_BLOCKED) != 0, s);
       return cudaGetLastError();
     } else {
       return cudaErrorInvalidValue;
@@ -941,7 +909,7 @@ static cudaError_t dslash_kind(int R, int epi, const void* links, const void* in
     R = r;
   }
   launch_dslash_s<S>(R & 0xff, epi, links, in, out, c1, c2, m2, g, out_parity, N, gate,
-                     (R & DSLASH_BLOCKED) != 0, (R & DSLASH_PIPE) != 0, s);
+                     (R & DSLASH_BLOCKED) != 0, s);
   return cudaGetLastError();
 }
 

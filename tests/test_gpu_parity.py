@@ -30,14 +30,12 @@ def test_dslash_parity(prec, N, parity):
 TMA = 256
 ASYNC = 512
 BLOCKED = 4096  # plain kernel, persistent grid of contiguous site ranges
-PIPE = 8192  # plain kernel, two-hop register pipeline
 
 
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("variant", [1, 2, 4, 8, TMA + 1, TMA + 2, TMA + 4, TMA + 8,
                                      ASYNC + 1, ASYNC + 2, ASYNC + 4, ASYNC + 8,
-                                     BLOCKED + 1, BLOCKED + 4, BLOCKED + 8,
-                                     PIPE + 2, PIPE + 4, PIPE + 8])
+                                     BLOCKED + 1, BLOCKED + 4, BLOCKED + 8])
 @pytest.mark.parametrize("N,parity", [(2, 0), (5, 1), (16, 0), (16, 1), (33, 1)])
 def test_dslash_every_kernel_variant(prec, variant, N, parity):
     """Each stencil kernel (register tile R; plain, bulk-copy pipelined or
@@ -67,7 +65,7 @@ PRECS16 = ["mixed_f16", "mixed_bf16"]
 
 
 @pytest.mark.parametrize("prec", PRECS16)
-@pytest.mark.parametrize("variant", [0, 1, 2, 4, 8, TMA + 4, ASYNC + 4, PIPE + 4, PIPE + 8,
+@pytest.mark.parametrize("variant", [0, 1, 2, 4, 8, TMA + 4, ASYNC + 4,
                                      BLOCKED + 4])
 @pytest.mark.parametrize("N,parity", [(1, 0), (3, 1), (8, 0), (16, 1)])
 def test_dslash_16bit(prec, variant, N, parity):
