@@ -421,14 +421,16 @@ struct BlasTiles {
   int upd, gram, wgram;
 };
 // packed: update tile in bits 0..7 (UPD_TC as bit 24), Gram tile in bits
-// 8..15, fused W + Gram tile in bits 16..23 (WG_TC as bit 25)
+// 8..15 (GR_TC as bit 26), fused W + Gram tile in bits 16..23 (WG_TC as
+// bit 25)
 BlasTiles unpack_tiles(int v) {
-  return {(v & 0xff) | ((v >> 24) & 1 ? UPD_TC : 0), (v >> 8) & 0xff,
+  return {(v & 0xff) | ((v >> 24) & 1 ? UPD_TC : 0), ((v >> 8) & 0xff) | ((v >> 26) & 1 ? GR_TC : 0),
           ((v >> 16) & 0xff) | ((v >> 25) & 1 ? WG_TC : 0)};
 }
 int pack_tiles(const BlasTiles& t) {
   return (t.upd & 0xff) | ((t.upd & UPD_TC) ? 1 << 24 : 0) | ((t.gram & 0xff) << 8) |
-         ((t.wgram & 0xff) << 16) | ((t.wgram & WG_TC) ? 1 << 25 : 0);
+         ((t.gram & GR_TC) ? 1 << 26 : 0) | ((t.wgram & 0xff) << 16) |
+         ((t.wgram & WG_TC) ? 1 << 25 : 0);
 }
 
 BlasTiles cached_tiles(const blockcg_ctx* h, FieldKind k, int N) {
@@ -523,6 +525,10 @@ void tune_blas(blockcg_ctx* h, const Ws& w, int N) {
                            WG_TC);
     });
     if (t < t_wgram) t_wgram = t, best_wgram = WG_TC;
+    t = time3([&] {
+      return gram_partials(k, w.AP, w.Ts, N, Vh, 1, w.partials, w.nblocks, g0, s, GR_TC);
+    });
+    if (t < t_gram) t_gram = t, best_gram = GR_TC;
   }
   const int packed = pack_tiles({best_upd, best_gram, best_wgram});
   h->tuned_blas[key] = packed;

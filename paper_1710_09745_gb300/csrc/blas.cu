@@ -320,6 +320,9 @@ static void launch_gram(const void* X, const void* Y, int N, int Vh, int herm, d
 
 cudaError_t gram_partials(FieldKind k, const void* X, const void* Y, int N, int Vh, int hermitian,
                           double2* partials, int nblocks, Gate gate, cudaStream_t s, int tile) {
+  if ((tile & GR_TC) && hermitian && w_gram_tc_supported(k, N))
+    return gram_partials_tc(k, X, Y, N, Vh, partials, nblocks, gate, s);
+  tile &= ~GR_TC;
   switch (k) {
     case FK_DF: launch_gram<StoreDF>(X, Y, N, Vh, hermitian, partials, nblocks, gate, tile, s); break;
     case FK_F32: launch_gram<StoreF32>(X, Y, N, Vh, hermitian, partials, nblocks, gate, tile, s); break;

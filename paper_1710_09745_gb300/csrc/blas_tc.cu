@@ -328,16 +328,20 @@ __device__ __forceinline__ void ldsm_x2_t(uint32_t (&r)[2], const void* p) {
                : "r"(a));
 }
 
-// Gram blocks (mt, nt) of G holding an entry i <= j: G rows 16 mt .. + 15
-// (complex i = 8 mt .. + 7), columns 8 nt .. + 7 (complex j = 4 nt .. + 3)
-template <int N>
+// Gram blocks (mt, nt) of G: rows 16 mt .. + 15 (complex i = 8 mt .. + 7),
+// columns 8 nt .. + 7 (complex j = 4 nt .. + 3); HERM: only blocks holding an
+// entry i <= j
+template <int N, bool HERM>
 struct GramBlocks {
   static constexpr int MT = N / 8, NT = N / 4;
+  static constexpr __host__ __device__ bool used(int mt, int nt) {
+    return !HERM || 8 * mt <= 4 * nt + 3;
+  }
   static constexpr int count() {
     int c = 0;
     for (int mt = 0; mt < MT; ++mt)
       for (int nt = 0; nt < NT; ++nt)
-        if (8 * mt <= 4 * nt + 3) ++c;
+        if (used(mt, nt)) ++c;
     return c;
   }
   static constexpr int COUNT = count();
@@ -347,7 +351,7 @@ struct GramBlocks {
     int c = 0;
     for (int m = 0; m < MT; ++m)
       for (int n = 0; n < NT; ++n)
-        if (8 * m <= 4 * n + 3) {
+        if (used(m, n)) {
           if (c == b) {
             mt = m;
             nt = n;
@@ -359,13 +363,84 @@ struct GramBlocks {
   }
 };
 
+// One CTA tile's contribution to this warp's Gram blocks: G += X_r^T Y_r
+// over the TR rows of the shared tiles sX and sY (row stride RW words);
+// X_r^T and Y_r fragments by ldmatrix.trans.  FP32 sums of 16 x TR products,
+// added to the double-float accumulators.
+template <class K, int N, bool HERM, int TR, int RW>
+__device__ __forceinline__ void gram_tc_tile(const uint32_t* sX, const uint32_t* sY,
+                                             dfacc (&gacc)[GramBlocks<N, HERM>::PER_WARP][4],
+                                             int warp, int lane) {
+  using GB = GramBlocks<N, HERM>;
+#pragma unroll
+  for (int bb = 0; bb < GB::PER_WARP; ++bb) {
+    const int b = warp + bb * TC_WARPS;
+    if (b >= GB::COUNT) break;
+    int mt, nt;
+    GB::at(b, mt, nt);
+    float d[4] = {0.f, 0.f, 0.f, 0.f};
+    const int q = lane >> 3, rr = lane & 7;
+#pragma unroll 2
+    for (int ks = 0; ks < TR / 16; ++ks) {
+      // A = X^T: ldmatrix.x4 matrices (tile rows +0/+8) x (tile columns
+      // +0/+8 halves) in the order (m +0, k +0), (m +8, k +0), (m +0, k +8),
+      // (m +8, k +8) of the A fragment (m = G row = tile column, k = tile row)
+      const int arow = 16 * ks + (q >> 1) * 8 + rr;
+      const int acol = 8 * mt + (q & 1) * 4;  // 32-bit words: 16 mt halves
+      uint32_t a[4];
+      ldsm_x4_t(a, sX + arow * RW + acol);
+      // B = Y (k = tile rows 16 ks .. + 15, n = tile columns 8 nt .. + 7)
+      const int brow = 16 * ks + (q & 1) * 8 + rr;
+      uint32_t bf[2];
+      ldsm_x2_t(bf, sY + brow * RW + 4 * nt);
+      K::mma(d, a, make_uint2(bf[0], bf[1]));
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) CompDF::add(gacc[bb][e], df{d[e], 0.f});
+  }
+}
+
+// The CTA's partial sums of K = X^dag Y (HERM: the entries i <= j) from the
+// warps' blocks of G: the lane pair (g even, g + 1) holds G rows (2i, 2i + 1)
+template <int N, bool HERM>
+__device__ __forceinline__ void gram_tc_write(double2* out,
+                                              const dfacc (&gacc)[GramBlocks<N, HERM>::PER_WARP][4],
+                                              double scale, int warp, int lane) {
+  using GB = GramBlocks<N, HERM>;
+  const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int bb = 0; bb < GB::PER_WARP; ++bb) {
+    const int b = warp + bb * TC_WARPS;
+    if (b >= GB::COUNT) break;  // uniform per warp
+    int mt, nt;
+    GB::at(b, mt, nt);
+    double v[4], p[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[e] = (double)gacc[bb][e].s + (double)gacc[bb][e].e;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) p[e] = __shfl_xor_sync(0xffffffffu, v[e], 4);
+    if ((g & 1) == 0) {
+      const int j = 4 * nt + t;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int i = 8 * mt + (g >> 1) + 4 * h;
+        if (!HERM || i <= j) {
+          const double kre = v[2 * h] + p[2 * h + 1];
+          const double kim = v[2 * h + 1] - p[2 * h];
+          out[i * N + j] = make_double2(kre * scale, kim * scale);
+        }
+      }
+    }
+  }
+}
+
 template <class SS, int N>
 __global__ void __launch_bounds__(TC_WARPS * 32, N >= 32 ? 3 : 4)
     k_w_gram_tc(typename SS::elem* __restrict__ Q, const typename SS::elem* __restrict__ AP,
                 const double2* __restrict__ beta, int Vh, double2* __restrict__ partials,
                 Gate gate) {
   using K = TcKind<SS>;
-  using GB = GramBlocks<N>;
+  using GB = GramBlocks<N, true>;
   constexpr int NSL = K::NSL;
   constexpr int KS = N / 8, NT = N / 4, MB = N / 16;
   constexpr int FR = KS * NT * 32;
@@ -473,67 +548,12 @@ __global__ void __launch_bounds__(TC_WARPS * 32, N >= 32 ? 3 : 4)
     }
     __syncthreads();
     // phase 2: this warp's Gram blocks over the tile's TR rows
-#pragma unroll
-    for (int bb = 0; bb < GB::PER_WARP; ++bb) {
-      const int b = warp + bb * TC_WARPS;
-      if (b >= GB::COUNT) break;
-      int mt, nt;
-      GB::at(b, mt, nt);
-      float d[4] = {0.f, 0.f, 0.f, 0.f};
-      const int q = lane >> 3, rr = lane & 7;
-#pragma unroll 2
-      for (int ks = 0; ks < TR / 16; ++ks) {
-        // A = W^T (rows 16 mt.. of G, k = tile rows 16 ks..): matrices
-        // (rows +0/+8) x (columns +0/+8 halves); B = W (k rows, columns 8 nt..)
-        const int arow = 16 * ks + (q >> 1) * 8 + rr;
-        const int acol = 8 * mt + (q & 1) * 4;  // in 32-bit words: 16 mt halves
-        uint32_t a[4];
-        ldsm_x4_t(a, sW + arow * RW + acol);
-        // ldmatrix.x4 matrix order: 0 = (rows +0, cols +0), 1 = (rows +0, cols
-        // +8), 2 = (rows +8, cols +0), 3 = (rows +8, cols +8); the A fragment
-        // wants (m +0, k +0), (m +8, k +0), (m +0, k +8), (m +8, k +8) with
-        // m = G row (tile column) and k = tile row
-        const uint32_t af[4] = {a[0], a[1], a[2], a[3]};
-        const int brow = 16 * ks + (q & 1) * 8 + rr;
-        uint32_t bf[2];
-        ldsm_x2_t(bf, sW + brow * RW + 4 * nt);
-        K::mma(d, af, make_uint2(bf[0], bf[1]));
-      }
-#pragma unroll
-      for (int e = 0; e < 4; ++e) CompDF::add(gacc[bb][e], df{d[e], 0.f});
-    }
+    gram_tc_tile<K, N, true, TR, RW>(sW, sW, gacc, warp, lane);
     __syncthreads();
   }
 
-  // partial sums of the upper triangle: combine the lane pair (g even, g + 1)
-  // that holds G rows (2i, 2i + 1)
-  double2* out = partials + (long long)blockIdx.x * N * N;
-  const double s2 = (double)unraw * (double)unraw;
-#pragma unroll
-  for (int bb = 0; bb < GB::PER_WARP; ++bb) {
-    const int b = warp + bb * TC_WARPS;
-    if (b >= GB::COUNT) break;  // uniform per warp
-    int mt, nt;
-    GB::at(b, mt, nt);
-    double v[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) v[e] = (double)gacc[bb][e].s + (double)gacc[bb][e].e;
-    double p[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) p[e] = __shfl_xor_sync(0xffffffffu, v[e], 4);
-    if ((g & 1) == 0) {
-      const int j = 4 * nt + t;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int i = 8 * mt + (g >> 1) + 4 * h;
-        if (i <= j) {
-          const double kre = v[2 * h] + p[2 * h + 1];
-          const double kim = v[2 * h + 1] - p[2 * h];
-          out[i * N + j] = make_double2(kre * s2, kim * s2);
-        }
-      }
-    }
-  }
+  gram_tc_write<N, true>(partials + (long long)blockIdx.x * N * N, gacc,
+                        (double)unraw * (double)unraw, warp, lane);
 }
 
 template <class SS, int N>
@@ -548,6 +568,80 @@ static cudaError_t launch_w_gram_tc(void* Q, const void* AP, const double2* beta
   kern<<<nblocks, TC_WARPS * 32, sm, s>>>((typename SS::elem*)Q, (const typename SS::elem*)AP,
                                           beta, Vh, partials, gate);
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// K = X^dag Y (the reduction multi-BLAS of Sec. 6.4; P^dag AP in Algorithm 1)
+// on the tensor cores for the 16-bit kinds: each CTA tile of TR rows of X and
+// Y is copied into padded shared-memory tiles with 128-bit loads, then the
+// warps form their blocks of the real Gram as in the fused W + Gram kernel.
+// HERM: only the entries i <= j (a Hermitian Gram; the reduction mirrors);
+// the iteration's P^dag AP is the one user, so only HERM is instantiated.
+template <class SS, int N, bool HERM>
+__global__ void __launch_bounds__(TC_WARPS * 32, 4)
+    k_gram_tc(const typename SS::elem* __restrict__ X, const typename SS::elem* __restrict__ Y,
+              int Vh, double2* __restrict__ partials, Gate gate) {
+  using K = TcKind<SS>;
+  using GB = GramBlocks<N, HERM>;
+  constexpr int TR = TC_WARPS * 16;
+  constexpr int RW = N + 4;
+  constexpr int CH = N / 4;  // 16-byte chunks per row
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint32_t* sX = reinterpret_cast<uint32_t*>(smem_raw);
+  uint32_t* sY = sX + TR * RW;
+  if (gate_closed(gate)) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long nrows = 3LL * Vh;
+  const uint32_t* Xw = reinterpret_cast<const uint32_t*>(X);
+  const uint32_t* Yw = reinterpret_cast<const uint32_t*>(Y);
+  dfacc gacc[GB::PER_WARP][4];
+#pragma unroll
+  for (int b = 0; b < GB::PER_WARP; ++b)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) gacc[b][e] = CompDF::zero();
+  for (long long tile = blockIdx.x; tile * TR < nrows; tile += gridDim.x) {
+    for (int idx = threadIdx.x; idx < TR * CH; idx += blockDim.x) {
+      const int row = idx / CH, c = idx - row * CH;
+      const long long r = tile * TR + row;
+      uint4 x = make_uint4(0u, 0u, 0u, 0u), y = x;  // rows past the end: zeros
+      if (r < nrows) {
+        x = *reinterpret_cast<const uint4*>(Xw + r * N + 4 * c);
+        y = *reinterpret_cast<const uint4*>(Yw + r * N + 4 * c);
+      }
+      *reinterpret_cast<uint4*>(sX + row * RW + 4 * c) = x;
+      *reinterpret_cast<uint4*>(sY + row * RW + 4 * c) = y;
+    }
+    __syncthreads();
+    gram_tc_tile<K, N, HERM, TR, RW>(sX, sY, gacc, warp, lane);
+    __syncthreads();
+  }
+  constexpr double unraw = 1.0 / SS::RAW_SCALE;
+  gram_tc_write<N, HERM>(partials + (long long)blockIdx.x * N * N, gacc, unraw * unraw, warp, lane);
+}
+
+template <class SS, int N>
+static cudaError_t launch_gram_tc(const void* X, const void* Y, int Vh, double2* partials,
+                                  int nblocks, Gate gate, cudaStream_t s) {
+  const size_t sm = 2 * (size_t)TC_WARPS * 16 * (N + 4) * sizeof(uint32_t);
+  using E = typename SS::elem;
+  auto kern = k_gram_tc<SS, N, true>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  kern<<<nblocks, TC_WARPS * 32, sm, s>>>((const E*)X, (const E*)Y, Vh, partials, gate);
+  return cudaGetLastError();
+}
+
+// Hermitian Grams only (P^dag AP of the iteration)
+cudaError_t gram_partials_tc(FieldKind k, const void* X, const void* Y, int N, int Vh,
+                             double2* partials, int nblocks, Gate gate, cudaStream_t s) {
+  if (k == FK_H16) {
+    if (N == 16) return launch_gram_tc<StoreH16, 16>(X, Y, Vh, partials, nblocks, gate, s);
+    if (N == 32) return launch_gram_tc<StoreH16, 32>(X, Y, Vh, partials, nblocks, gate, s);
+  } else if (k == FK_BF16) {
+    if (N == 16) return launch_gram_tc<StoreBF16, 16>(X, Y, Vh, partials, nblocks, gate, s);
+    if (N == 32) return launch_gram_tc<StoreBF16, 32>(X, Y, Vh, partials, nblocks, gate, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 bool w_gram_tc_supported(FieldKind k, int N) {

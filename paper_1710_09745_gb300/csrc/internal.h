@@ -128,6 +128,9 @@ static constexpr int UPD_TC = 256;
 // tile | WG_TC for w_update_gram: the tensor-core fused W + Gram (16-bit
 // kinds, N = 16 or 32; the FP32-pipe kernel otherwise)
 static constexpr int WG_TC = 256;
+// tile | GR_TC for gram_partials: the tensor-core Gram (Hermitian Grams of
+// the 16-bit kinds, N = 16 or 32; the FP32-pipe kernel otherwise)
+static constexpr int GR_TC = 256;
 // Q <- W Sinv ; X += P BC ; P <- Q + P SH unless st->ru_pending
 cudaError_t bcg_update(FieldKind sk, FieldKind xk, void* Q, void* P, void* X, const double2* Sinv,
                        const double2* BC, const double2* SH, int N, int Vh, Gate gate,
@@ -138,6 +141,9 @@ cudaError_t bcg_update_tc(FieldKind sk, void* Q, void* P, void* X, const double2
                           const double2* BC, const double2* SH, int N, int Vh, Gate gate,
                           cudaStream_t s);
 bool w_gram_tc_supported(FieldKind k, int N);
+// Hermitian K = X^dag Y on the tensor cores (the pairs of w_gram_tc_supported)
+cudaError_t gram_partials_tc(FieldKind k, const void* X, const void* Y, int N, int Vh,
+                             double2* partials, int nblocks, Gate gate, cudaStream_t s);
 cudaError_t w_update_gram_tc(FieldKind k, void* Q, const void* AP, const double2* beta, int N,
                              int Vh, double2* partials, int nblocks, Gate gate, cudaStream_t s);
 // Q <- R Cinv (converted to Q's kind) ; P <- Q + P SH (or P <- Q when init)

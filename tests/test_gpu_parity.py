@@ -517,8 +517,9 @@ def test_forced_blas_tiles_converge(tmp_path, prec, kind, upd):
 @pytest.mark.parametrize("N", [16, 32])
 @pytest.mark.parametrize("dims", [(8, 8, 8, 8), (6, 6, 6, 6)])
 def test_tensor_core_blas_converge(tmp_path, prec, kind, N, dims):
-    """The tensor-core fused update (bit 24 of the cached BLAS choice) and
-    fused W + Gram (bit 25), each alone and together, forced through the
+    """The tensor-core fused update (bit 24 of the cached BLAS choice), fused
+    W + Gram (bit 25) and Gram P^dag AP (bit 26), each alone and all
+    together, forced through the
     tuning cache for the 16-bit forms; 6^4 has 3 V_h = 1944 rows, a ragged
     last 16-row tile (8 rows) and a ragged 128-row Gram tile (24 rows).
     Each solve meets tol on the oracle's residual, in about as many
@@ -530,8 +531,8 @@ def test_tensor_core_blas_converge(tmp_path, prec, kind, N, dims):
     tag = ".".join(str(d) for d in dims)
     b = hi.gaussian_sources(dims, N, seed=2026)
     iters = {}
-    for name, flags in (("pipes", 0), ("upd", 1 << 24), ("wgram", 1 << 25),
-                        ("both", (1 << 24) | (1 << 25))):
+    for name, flags in (("pipes", 0), ("upd", 1 << 24), ("wgram", 1 << 25), ("gram", 1 << 26),
+                        ("all", (1 << 24) | (1 << 25) | (1 << 26))):
         cache = tmp_path / f"tiles_{name}.json"
         packed = 8 | (16 << 8) | (32 << 16) | flags
         cache.write_text(json.dumps({f"blas/{tag}/kind{kind}/N{N}/{dev}": packed}))
@@ -544,5 +545,5 @@ def test_tensor_core_blas_converge(tmp_path, prec, kind, N, dims):
         assert info["status"] == 0, name
         assert _oracle_rel_res(dims, fat, lng, mass, b, gh.to_np(X)).max() <= 1e-10, name
         iters[name] = info["iters"]
-    for name in ("upd", "wgram", "both"):
+    for name in ("upd", "wgram", "gram", "all"):
         assert abs(iters[name] - iters["pipes"]) <= max(3, iters["pipes"] // 10), iters
