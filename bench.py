@@ -62,7 +62,8 @@ def parse_args():
                     help="only the stencil sweep (Fig. 1 analogue) for --prec over --sweep")
     ap.add_argument("--sweep", type=int, nargs="+", default=[1, 4, 8, 16, 32])
     ap.add_argument("--dslash-variant", type=int, default=0,
-                    help="with --dslash-only: force a stencil kernel (blockcg_params.dslash_variant)")
+                    help="force a stencil kernel (blockcg_params.dslash_variant) for the "
+                         "headline solve and --dslash-only; 0 = autotuned")
     ap.add_argument("--batched-only", action="store_true",
                     help="only the batched leg (64 small problems, one CUDA graph)")
     ap.add_argument("--autograd-only", action="store_true",
@@ -408,7 +409,8 @@ def main():
     fat = fat_c.to(dev)
     lng = lng_c.to(dev)
     B = torch.as_tensor(b_np).to(dev)
-    s = BlockCG(dims, fat, lng, a.mass, prec=a.prec, max_rhs=max(N, 32), profile=True, device=dev)
+    s = BlockCG(dims, fat, lng, a.mass, prec=a.prec, max_rhs=max(N, 32), profile=True,
+                dslash_variant=a.dslash_variant, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def barrier():

@@ -120,7 +120,11 @@ typedef struct {
                           plus one of: 256 for the bulk-copy (TMA) pipelined
                           kernel, 512 for the per-thread cp.async prefetch
                           kernel, 4096 for the plain kernel on a persistent
-                          grid of contiguous site ranges.  Other values:
+                          grid of contiguous site ranges, 8192 for the
+                          tensor-core stencil of the F64 form (double-float
+                          values split into bf16 slices with exact products
+                          on mma.sync, N = 16 or 32 with a workspace set; the
+                          cp.async kernel otherwise).  Other values:
                           BLOCKCG_ERR_ARG */
   int link_recon;      /* iteration links of the 32- and 16-bit forms: 0 = all 18
                           reals per link (default); 12 = the first two rows only,
@@ -339,6 +343,16 @@ blockcg_status blockcg_tune(blockcg_t h, int n_rhs);
  * synchronises the stream.  Errors: ERR_ARG (null output), ERR_CUDA. */
 blockcg_status blockcg_bench_alu(void* stream, double* fp32_fma_per_s, double* fp64_fma_per_s,
                                  int* sm_count);
+
+/* Measured rate of the warp-level bf16 tensor-core product (mma.sync
+ * m16n8k16 with FP32 accumulation) that the tensor-core double-float stencil
+ * issues (its split-operand products, Sec. 6.2 stencil): 4 independent
+ * accumulator chains per warp on register operands, 8 blocks of 256 threads
+ * per SM, timed with CUDA events on `stream` (cudaStream_t, NULL = legacy
+ * default).  Output (host): *bf16_flop_per_s = 4096 flops per instruction
+ * times instructions per second.  Needs no handle; allocates nothing;
+ * synchronises the stream.  Errors: ERR_ARG (null output), ERR_CUDA. */
+blockcg_status blockcg_bench_mma(void* stream, double* bf16_flop_per_s);
 
 /* K = X^dag Y, the same block inner product as blockcg_block_cdot, for
  * callers that cannot allocate device memory: code running inside a memory

@@ -30,7 +30,7 @@ ABI_SYMBOLS = [
     "blockcg_solve_cg", "blockcg_bench_dslash", "blockcg_destroy", "blockcg_status_string",
     "blockcg_last_error", "blockcg_block_cdot_noalloc", "blockcg_batch_create",
     "blockcg_batch_solve", "blockcg_batch_destroy", "blockcg_batch_last_error",
-    "blockcg_link_grad", "blockcg_tune", "blockcg_bench_alu", "blockcg_solve_many",
+    "blockcg_link_grad", "blockcg_tune", "blockcg_bench_alu", "blockcg_bench_mma", "blockcg_solve_many",
     "blockcg_set_tune_cache",
 ]
 
@@ -113,6 +113,7 @@ def load_library(path: str = LIB_PATH):
         "blockcg_link_grad": (I, [P, P, P, I, P, P]),
         "blockcg_tune": (I, [P, I]),
         "blockcg_bench_alu": (I, [P, ct.POINTER(D), ct.POINTER(D), ct.POINTER(I)]),
+        "blockcg_bench_mma": (I, [P, ct.POINTER(D)]),
         "blockcg_solve_many": (I, [P, P, P, I, D, I, ct.POINTER(ManyStats)]),
         "blockcg_set_tune_cache": (I, [P, ct.c_char_p]),
         "blockcg_batch_last_error": (ct.c_char_p, [P]),
@@ -393,6 +394,20 @@ def bench_alu(stream=None):
     if rc != 0:
         raise BlockCGError(rc, "blockcg_bench_alu failed")
     return f32.value, f64.value, sms.value
+
+
+def bench_mma(stream=None):
+    """Measured bf16 mma.sync m16n8k16 flops per second of the current device
+    (blockcg_bench_mma)."""
+    torch = _torch()
+    L = load_library()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    r = ct.c_double()
+    rc = L.blockcg_bench_mma(ct.c_void_p(stream.cuda_stream), ct.byref(r))
+    if rc != 0:
+        raise BlockCGError(rc, "blockcg_bench_mma failed")
+    return r.value
 
 
 class BlockCGBatch:

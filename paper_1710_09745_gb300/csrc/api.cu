@@ -111,6 +111,9 @@ Ws carve(const blockcg_ctx* h, int N, char* base) {
     off += up(bytes);
     return p;
   };
+  // first: the tensor-core stencil's column maxima, at an offset that does
+  // not depend on N (Geom::tc_colmax points here once the workspace is set)
+  take(64 * sizeof(unsigned));
   size_t nel = (size_t)h->g.Vh * N * 3;
   size_t fb = nel * elem_bytes(h->fine), rb = nel * elem_bytes(h->ru),
          sb = nel * elem_bytes(h->sloppy);
@@ -371,10 +374,13 @@ int stencil_R(blockcg_ctx* h, FieldKind k, int N, const void* links, const void*
     return best;
   }
   Gate g0{nullptr, GATE_ALWAYS};
-  const int cands[12] = {1, 2, 4, 8, 1 | DSLASH_TMA, 2 | DSLASH_TMA, 4 | DSLASH_TMA, 8 | DSLASH_TMA,
-                         1 | DSLASH_ASYNC, 2 | DSLASH_ASYNC, 4 | DSLASH_ASYNC, 8 | DSLASH_ASYNC};
+  const int cands[13] = {1, 2, 4, 8, 1 | DSLASH_TMA, 2 | DSLASH_TMA, 4 | DSLASH_TMA, 8 | DSLASH_TMA,
+                         1 | DSLASH_ASYNC, 2 | DSLASH_ASYNC, 4 | DSLASH_ASYNC, 8 | DSLASH_ASYNC,
+                         1 | DSLASH_TC};
   for (int R : cands) {
     if ((R & 0xff) > 1 && (R & 0xff) > N) continue;
+    // the tensor-core stencil: double-float with N = 16 or 32 only
+    if ((R & DSLASH_TC) && (k != FK_DF || rf || !dslash_tc_supported(h->g, N))) continue;
     if (rf) {  // two-row links: the plain kernel only
       if (R & (DSLASH_TMA | DSLASH_ASYNC)) continue;
       R |= rf;
@@ -384,7 +390,7 @@ int stencil_R(blockcg_ctx* h, FieldKind k, int N, const void* links, const void*
     // Gram, N x N and update kernels) it ran 12-15 % slower than that timing
     // in repeated 32^4 N = 16 measurements, while the cp.async kernel ran as
     // timed.
-    if (k == FK_DF && N >= 2 && !(R & DSLASH_ASYNC)) continue;
+    if (k == FK_DF && N >= 2 && !(R & (DSLASH_ASYNC | DSLASH_TC))) continue;
     const double m2 = h->mass * h->mass;
     auto run = [&]() {
       cudaError_t e = dslash(k, R, EPI_NONE, links, in, out, nullptr, nullptr, 0.0, h->g, 1, N, g0,
@@ -844,7 +850,7 @@ blockcg_status blockcg_create(blockcg_t* out, const int dims[4], double mass,
       prm.check_every < 0 || (int)prm.prec < 0 || (int)prm.prec > 4)
     return BLOCKCG_ERR_ARG;
   {
-    int r = prm.dslash_variant & ~(DSLASH_TMA | DSLASH_ASYNC | DSLASH_BLOCKED);
+    int r = prm.dslash_variant & ~(DSLASH_TMA | DSLASH_ASYNC | DSLASH_BLOCKED | DSLASH_TC);
     if (prm.dslash_variant != 0 && r != 1 && r != 2 && r != 4 && r != 8) return BLOCKCG_ERR_ARG;
   }
   if (prm.link_recon != 0 && prm.link_recon != 12) return BLOCKCG_ERR_ARG;
@@ -862,6 +868,7 @@ blockcg_status blockcg_create(blockcg_t* out, const int dims[4], double mass,
   h->g.antiperiodic = prm.antiperiodic_t ? 1 : 0;
   h->g.inv_c[0] = h->g.inv_c[1] = 0.f;
   h->g.wait_ns = (unsigned long long)prm.wait_limit_ns;
+  h->g.tc_colmax = nullptr;
   h->mass = mass;
   h->p = prm;
   h->stream = (cudaStream_t)stream;
@@ -972,6 +979,7 @@ blockcg_status blockcg_set_workspace(blockcg_t h, void* ws, size_t bytes) {
   if (((uintptr_t)ws) % 16) return fail(h, BLOCKCG_ERR_ARG, "workspace not 16-byte aligned");
   h->ws = (char*)ws;
   h->ws_bytes = bytes;
+  h->g.tc_colmax = (unsigned*)ws;  // the first region of carve()
   return BLOCKCG_OK;
 }
 

@@ -354,6 +354,9 @@ struct Geom {
   float inv_c[2];
   // bounded device waits (bulk-copy stencil) give up after this many ns
   unsigned long long wait_ns;
+  // the tensor-core double-float stencil's per-column maxima (64 words of the
+  // handle's workspace; null until a workspace is set)
+  unsigned* tc_colmax;
 };
 
 // coordinates of the site with checkerboard index cb on parity p

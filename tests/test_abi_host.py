@@ -230,8 +230,8 @@ def test_dslash_variant_encoding(lib):
     """R in {1, 2, 4, 8} plus at most the documented kernel flags."""
     from paper_1710_09745_gb300.binding import Params
     d = (ct.c_int * 4)(4, 4, 4, 4)
-    for v, want in [(4, 0), (256 + 4, 0), (512 + 2, 0), (4096 + 8, 0),
-                    (3, 1), (2048 + 256 + 4, 1), (8192 + 4, 1), (4096, 1)]:
+    for v, want in [(4, 0), (256 + 4, 0), (512 + 2, 0), (4096 + 8, 0), (8192 + 2, 0),
+                    (3, 1), (2048 + 256 + 4, 1), (16384 + 4, 1), (4096, 1), (8192, 1)]:
         h = ct.c_void_p()
         p = Params()
         lib.blockcg_default_params(ct.byref(p))

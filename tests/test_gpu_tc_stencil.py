@@ -1,0 +1,138 @@
+"""GPU parity of the tensor-core double-float stencil (split bf16 products on
+mma.sync, Sec. 6.2 stencil of Eq. 2) against the CPU oracle: single halves,
+the normal operator, columns of very different magnitude, the fallback for
+unsupported widths, whole solves and a full-size sampled check."""
+import numpy as np
+import pytest
+
+import hisq_inputs as hi
+from oracle import hisq
+from tests import gpu_helpers as gh
+from tests import lattice_helpers as lh
+
+pytestmark = pytest.mark.gpu
+
+DIMS = (6, 8, 10, 12)   # Vh = 2880: 360 groups of 8 sites over many CTAs
+TC = 8192               # blockcg_params.dslash_variant: tensor-core stencil
+ASYNC = 512
+# the register-tile bits of the variant do not matter for this kernel
+TC_VARIANTS = [TC + 1]
+
+
+@pytest.mark.parametrize("variant", TC_VARIANTS)
+@pytest.mark.parametrize("N", [16, 32])
+@pytest.mark.parametrize("parity", [0, 1])
+def test_dslash_tc_parity(variant, N, parity):
+    s, fat, lng = gh.make_solver(DIMS, 0.1, prec="f64", seed=1011, max_rhs=N, dslash_variant=variant)
+    psi = hi.gaussian_sources(DIMS, N, seed=99 + N)
+    out = gh.to_np(s.dslash(psi, parity))
+    ref = hisq.dslash(DIMS, fat, lng, psi, parity)
+    assert gh.rel_err(out, ref) < gh.TOL["f64"]
+
+
+@pytest.mark.parametrize("variant", TC_VARIANTS)
+@pytest.mark.parametrize("N", [16, 32])
+def test_dslash_tc_column_scales(variant, N):
+    """Columns spanning 10^-6 .. 10^6: every column keeps its own relative
+    accuracy (one power-of-two scale per right-hand side)."""
+    s, fat, lng = gh.make_solver(DIMS, 0.1, prec="f64", seed=1012, max_rhs=N, dslash_variant=variant)
+    psi = hi.gaussian_sources(DIMS, N, seed=300 + N)
+    psi *= (10.0 ** (np.arange(N) % 13 - 6))[:, None, None]
+    out = gh.to_np(s.dslash(psi, 1))
+    ref = hisq.dslash(DIMS, fat, lng, psi, 1)
+    for j in range(N):
+        assert gh.rel_err(out[j], ref[j]) < gh.TOL["f64"], j
+
+
+def test_dslash_tc_zero_column_and_scaled_links():
+    """An all-zero right-hand side, and links scaled by 37 (no longer below 1):
+    the per-site link scale follows them."""
+    N = 16
+    fat, lng = hi.random_links(DIMS, 1013)
+    fat, lng = 37.0 * fat, 37.0 * lng
+    s, _, _ = gh.make_solver(DIMS, 0.1, prec="f64", links=(fat, lng), max_rhs=N,
+                             dslash_variant=TC + 1)
+    psi = hi.gaussian_sources(DIMS, N, seed=301)
+    psi[5] = 0.0
+    out = gh.to_np(s.dslash(psi, 0))
+    ref = hisq.dslash(DIMS, fat, lng, psi, 0)
+    assert gh.rel_err(out, ref) < gh.TOL["f64"]
+    assert np.all(out[5] == 0.0)
+
+
+@pytest.mark.parametrize("N", [1, 5, 8, 33])
+def test_dslash_tc_fallback_widths(N):
+    """Widths the tensor-core kernel does not take run the cp.async kernel."""
+    s, fat, lng = gh.make_solver(DIMS, 0.1, prec="f64", seed=1014, max_rhs=max(N, 16),
+                                 dslash_variant=TC + 1)
+    psi = hi.gaussian_sources(DIMS, N, seed=400 + N)
+    out = gh.to_np(s.dslash(psi, 1))
+    ref = hisq.dslash(DIMS, fat, lng, psi, 1)
+    assert gh.rel_err(out, ref) < gh.TOL["f64"]
+
+
+@pytest.mark.parametrize("variant", TC_VARIANTS)
+@pytest.mark.parametrize("N", [16, 32])
+def test_apply_MdagM_tc(variant, N):
+    s, fat, lng = gh.make_solver(DIMS, 0.1, prec="f64", seed=1015, max_rhs=N, dslash_variant=variant)
+    v = hi.gaussian_sources(DIMS, N, seed=500 + N)
+    out = gh.to_np(s.apply_MdagM(v))
+    ref = hisq.apply_A(DIMS, fat, lng, 0.1, v)
+    assert gh.rel_err(out, ref) < gh.TOL["f64"]
+
+
+def test_apply_tc_antiperiodic_tiny_lattice():
+    """4^4 with antiperiodic t: the +-3 hops wrap onto coincident sites."""
+    dims = (4, 4, 4, 4)
+    N = 16
+    s, fat, lng = gh.make_solver(dims, 0.2, prec="f64", seed=1016, max_rhs=N, dslash_variant=TC + 1,
+                                 antiperiodic_t=1)
+    v = hi.gaussian_sources(dims, N, seed=501)
+    out = gh.to_np(s.apply_MdagM(v))
+    ref = hisq.apply_A(dims, fat, lng, 0.2, v, antiperiodic_t=True)
+    assert gh.rel_err(out, ref) < gh.TOL["f64"]
+
+
+@pytest.mark.parametrize("variant,N", [(TC + 1, 16), (TC + 1, 32)])
+def test_solve_tc_against_oracle(variant, N):
+    """Whole block-CGrQ solves with the tensor-core stencil: the true residual
+    meets tol, the solution matches the oracle's, and the iteration count
+    stays within a few percent of the CUDA-core double-float stencil's."""
+    dims = (8, 8, 8, 12)
+    mass = 0.05
+    b = hi.gaussian_sources(dims, N, seed=2007 + N)
+    s, fat, lng = gh.make_solver(dims, mass, prec="f64", seed=1017, max_rhs=N, dslash_variant=variant)
+    X, info = s.solve(b, tol=1e-12)
+    assert info["status"] == 0, info
+    X = gh.to_np(X)
+    r = b - hisq.apply_A(dims, fat, lng, mass, X)
+    rel = np.linalg.norm(r.reshape(N, -1), axis=1) / np.linalg.norm(b.reshape(N, -1), axis=1)
+    assert rel.max() <= 1e-12 * 1.01, rel
+    xo = np.stack([hisq.cg(dims, fat, lng, mass, b[j:j + 1], tol=1e-13, max_iter=20000)[0][0]
+                   for j in range(0, N, 7)])
+    err = np.linalg.norm((X[::7] - xo).reshape(len(xo), -1), axis=1) / \
+        np.linalg.norm(xo.reshape(len(xo), -1), axis=1)
+    assert err.max() < 1e-8, err
+    s2, _, _ = gh.make_solver(dims, mass, prec="f64", links=(fat, lng), max_rhs=N,
+                              dslash_variant=ASYNC + 2)
+    _, info2 = s2.solve(b, tol=1e-12)
+    assert info["iters"] <= 1.05 * info2["iters"] + 2, (info["iters"], info2["iters"])
+
+
+def test_apply_tc_full_size_sampled():
+    """32^4, N = 16 (the benchmark workload) with the tensor-core stencil:
+    sampled output sites against the oracle."""
+    dims = (32, 32, 32, 32)
+    N = 16
+    fat, lng = hi.random_links_torch(dims, 1001, "cpu")
+    fat, lng = fat.numpy(), lng.numpy()
+    b = hi.gaussian_sources(dims, N, 2100)
+    s, _, _ = gh.make_solver(dims, 0.01, prec="f64", links=(fat, lng), max_rhs=N,
+                             dslash_variant=TC + 1)
+    out = gh.to_np(s.apply_MdagM(b))
+    rng = np.random.default_rng(9)
+    sites = np.sort(rng.choice(lh.even_sites(dims), size=48, replace=False))
+    for j in (0, 7, 15):
+        ref = hisq.apply_A_sites(dims, fat, lng, 0.01, b[j], sites)
+        got = out[j][sites >> 1]
+        assert np.abs(got - ref).max() < gh.TOL["f64"] * np.abs(ref).max()
