@@ -661,12 +661,14 @@ cudaError_t w_update_gram_tc(FieldKind k, void* Q, const void* AP, const double2
 }
 
 bool bcg_update_tc_supported(FieldKind sk, FieldKind xk, int N) {
+  if (sk == FK_DF) return xk == FK_DF && bcg_update_tc_df_supported(N);
   return (sk == FK_H16 || sk == FK_BF16) && xk == FK_DF && (N == 16 || N == 32);
 }
 
 cudaError_t bcg_update_tc(FieldKind sk, void* Q, void* P, void* X, const double2* Sinv,
                           const double2* BC, const double2* SH, int N, int Vh, Gate gate,
                           cudaStream_t s) {
+  if (sk == FK_DF) return bcg_update_tc_df(Q, P, X, Sinv, BC, SH, N, Vh, gate, s);
   if (sk == FK_H16) {
     if (N == 16) return launch_bcg_update_tc<StoreH16, 16>(Q, P, X, Sinv, BC, SH, Vh, gate, s);
     if (N == 32) return launch_bcg_update_tc<StoreH16, 32>(Q, P, X, Sinv, BC, SH, Vh, gate, s);

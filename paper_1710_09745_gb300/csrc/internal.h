@@ -129,8 +129,8 @@ cudaError_t w_update_gram(FieldKind k, void* Q, const void* AP, const double2* b
 // thread and UPD_X_GLOBAL for the old X read from global memory (not staged)
 static constexpr int UPD_TWO_ROWS = 64;
 static constexpr int UPD_X_GLOBAL = 128;
-// tile | UPD_TC: the tensor-core form (16-bit kinds, N = 16 or 32; the
-// FP32-pipe kernel otherwise)
+// tile | UPD_TC: the tensor-core form (16-bit kinds with N = 16 or 32, the
+// double-float kind with N = 16; the CUDA-core kernel otherwise)
 static constexpr int UPD_TC = 256;
 // tile | WG_TC for w_update_gram: the tensor-core fused W + Gram (16-bit
 // kinds, N = 16 or 32; the FP32-pipe kernel otherwise)
@@ -142,6 +142,11 @@ static constexpr int GR_TC = 256;
 cudaError_t bcg_update(FieldKind sk, FieldKind xk, void* Q, void* P, void* X, const double2* Sinv,
                        const double2* BC, const double2* SH, int N, int Vh, Gate gate,
                        cudaStream_t s, int tile = 0);
+// the tensor-core fused update of the double-float kind (blas_tc_df.cu,
+// exact split bf16 products), N = 16
+bool bcg_update_tc_df_supported(int N);
+cudaError_t bcg_update_tc_df(void* Q, void* P, void* X, const double2* Sinv, const double2* BC,
+                             const double2* SH, int N, int Vh, Gate gate, cudaStream_t s);
 // the tensor-core fused update (blas_tc.cu): supported (kind, N) pairs
 bool bcg_update_tc_supported(FieldKind sk, FieldKind xk, int N);
 cudaError_t bcg_update_tc(FieldKind sk, void* Q, void* P, void* X, const double2* Sinv,

@@ -1,7 +1,8 @@
-"""GPU parity of the tensor-core double-float stencil (split bf16 products on
-mma.sync, Sec. 6.2 stencil of Eq. 2) against the CPU oracle: single halves,
+"""GPU parity of the tensor-core double-float kernels (split bf16 products on
+mma.sync): the stencil of Eq. 2 (Sec. 6.2) against the CPU oracle in single halves,
 the normal operator, columns of very different magnitude, the fallback for
-unsupported widths, whole solves and a full-size sampled check."""
+unsupported widths, whole solves and a full-size sampled check; the fused
+block update of Algorithm 1 (Sec. 6.3) through whole solves."""
 import numpy as np
 import pytest
 
@@ -136,3 +137,45 @@ def test_apply_tc_full_size_sampled():
         ref = hisq.apply_A_sites(dims, fat, lng, 0.01, b[j], sites)
         got = out[j][sites >> 1]
         assert np.abs(got - ref).max() < gh.TOL["f64"] * np.abs(ref).max()
+
+
+def _oracle_rel_res(dims, fat, lng, mass, b, X):
+    r = b - hisq.apply_A(dims, fat, lng, mass, X)
+    return np.linalg.norm(r.reshape(len(b), -1), axis=1) / np.linalg.norm(b.reshape(len(b), -1), axis=1)
+
+
+@pytest.mark.parametrize("dims", [(8, 8, 8, 8), (6, 6, 6, 6)])
+@pytest.mark.parametrize("stencil", [ASYNC + 2, TC + 1])
+def test_tc_update_df_converges(tmp_path, dims, stencil):
+    """The tensor-core double-float fused update (Q = W S^-1, P = Q + P S^dag,
+    X += P beta C as exact split bf16 products; bit 24 of the cached BLAS
+    choice) forced through the tuning cache, with the CUDA-core and the
+    tensor-core stencil: 6^4 has 3 V_h = 1944 rows, a ragged last 16-row
+    tile.  Each solve to 1e-12 meets tol on the oracle's residual, matches
+    the oracle's solution, and takes about as many iterations as the
+    CUDA-core update."""
+    import json
+    torch = gh.torch_mod()
+    mass, N = 0.05, 16
+    dev = torch.cuda.get_device_name(0).replace(" ", "_").replace('"', "_").replace("\\", "_")
+    tag = ".".join(str(d) for d in dims)
+    b = hi.gaussian_sources(dims, N, seed=2031)
+    iters = {}
+    for name, flags in (("pipes", 0), ("upd", 1 << 24)):
+        cache = tmp_path / f"tiles_{name}.json"
+        packed = 8 | (16 << 8) | (32 << 16) | flags
+        cache.write_text(json.dumps({f"blas/{tag}/kind0/N{N}/{dev}": packed}))
+        s, fat, lng = gh.make_solver(dims, mass, prec="f64", seed=1031, max_rhs=N,
+                                     dslash_variant=stencil)
+        s.set_tune_cache(cache)
+        X, info = s.solve(b, tol=1e-12)
+        assert info["status"] == 0, name
+        X = gh.to_np(X)
+        assert _oracle_rel_res(dims, fat, lng, mass, b, X).max() <= 1.01e-12, name
+        iters[name] = info["iters"]
+        if name == "upd":
+            xo = hisq.cg(dims, fat, lng, mass, b[:2], tol=1e-13, max_iter=20000)[0]
+            err = np.linalg.norm((X[:2] - xo).reshape(2, -1), axis=1) / \
+                np.linalg.norm(xo.reshape(2, -1), axis=1)
+            assert err.max() < 1e-8, err
+    assert abs(iters["upd"] - iters["pipes"]) <= max(3, iters["pipes"] // 20), iters
