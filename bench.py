@@ -44,6 +44,10 @@ FP32_LANES = 128
 SM_MAX_MHZ = 2070.0
 DF_INSTR_PER_FLOP = 6.0   # 12 FP32 instructions per double-float multiply-add (2 flops)
 STENCIL_FLOPS = 1158      # per site per right-hand side (Sec. 6.2)
+TC_VARIANT = 8192         # blockcg_params.dslash_variant flag of the tensor-core stencil
+TC_PAIRS = 21             # bf16 slice products per double-float product (s + t <= 5)
+TC_USEFUL = 6.0 / 8.0     # output columns of the n8 MMA tile the stencil uses
+TC_TRAFFIC_32x4_N16 = 765.5e6 * 524288 / 165888  # ncu DRAM bytes at 24^4, scaled by sites
 
 
 def parse_args():
@@ -420,8 +424,9 @@ def main():
         torch.cuda.synchronize(dev)
 
     # measured FP32 / FP64 multiply-add rates of this GPU (the double-float roofline's basis)
-    from paper_1710_09745_gb300.binding import bench_alu
+    from paper_1710_09745_gb300.binding import bench_alu, bench_mma
     alu_f32, alu_f64, alu_sms = bench_alu(stream)
+    mma_bf16 = bench_mma(stream)
     for _ in range(a.warmup):
         X, info = s.solve(B, tol=a.tol)
     barrier()
@@ -451,7 +456,36 @@ def main():
     bytes_per_real = {"f64": 8, "f64_native": 8, "mixed_f32": 4, "mixed_f16": 2, "mixed_bf16": 2}[a.prec]
     alg_bytes = (288 + 12 * N) * bytes_per_real * Vh
     alg_flops = STENCIL_FLOPS * N * Vh
-    if a.prec == "f64":
+    variant = infos[-1]["stencil_variant"]
+    hbm_view = {"achieved_gbs": alg_bytes / (avg_launch_ms * 1e-3) / 1e9, "peak_gbs": hbm_peak,
+                "frac": alg_bytes / (avg_launch_ms * 1e-3) / 1e9 / hbm_peak}
+    if a.prec == "f64" and (variant & TC_VARIANT) and N in (16, 32):
+        # the tensor-core stencil: 6 chunks x 21 split products (m16n8k16, 4096 flops,
+        # 6 of 8 output columns used) per site and 16 right-hand sides
+        issued = 6 * 21 * (N // 16) * 4096.0 * Vh
+        peak = mma_bf16 * TC_USEFUL / TC_PAIRS / 1e12
+        achieved = alg_flops / (avg_launch_ms * 1e-3) / 1e12
+        full = tuple(dims) == (32, 32, 32, 32) and N == 16
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak,
+                "traffic": TC_TRAFFIC_32x4_N16 if full else None,
+                "traffic_note": "ncu DRAM read+write of one k_dslash_tc launch at 24^4 N=16 "
+                                "(765.5 MB, 1.20x its algorithmic bytes), scaled by sites to "
+                                "32^4; profiles/k_dslash_tc_df_24x4_N16.md" if full else None,
+                "kernel": "k_dslash_tc (tensor-core double-float stencil)",
+                "peak_note": "FP64-equivalent rate of the split-product scheme: measured "
+                             "mma.sync bf16 rate (blockcg_bench_mma, this run) x 6/8 used "
+                             "output columns / 21 slice products per double-float product",
+                "tensor_issued": {"tflops": issued / (avg_launch_ms * 1e-3) / 1e12,
+                                  "mma_sync_peak_tflops": mma_bf16 / 1e12,
+                                  "frac": issued / (avg_launch_ms * 1e-3) / mma_bf16},
+                "ncu": {"profile": "profiles/k_dslash_tc_df_24x4_N16.md (24^4, N = 16)",
+                        "tensor_pipe_active": 0.216, "issue_slots_active": 0.584,
+                        "dram_throughput": 0.146, "warps_active": 0.243},
+                "hbm_view": hbm_view,
+                "share_of_solve": ms_st / ms_total if ms_total else None,
+                "launches": n_st, "avg_launch_ms": avg_launch_ms, "variant": variant}
+    elif a.prec == "f64":
         peak = SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6 / DF_INSTR_PER_FLOP / 1e12
         achieved = alg_flops / (avg_launch_ms * 1e-3) / 1e12
         # ncu dram__bytes_read.sum + dram__bytes_write.sum of one 32^4 N=16 launch of the
@@ -477,12 +511,9 @@ def main():
                 "ncu": {"profile": "profiles/k_dslash_df_24x4_N16.md (24^4, N = 16, same kernel)",
                         "issue_slots_active": 0.809, "fma_pipe_active": 0.681,
                         "dram_throughput": 0.195, "achieved_occupancy": 0.287},
-                "hbm_view": {"achieved_gbs": alg_bytes / (avg_launch_ms * 1e-3) / 1e9,
-                             "peak_gbs": hbm_peak,
-                             "frac": alg_bytes / (avg_launch_ms * 1e-3) / 1e9 / hbm_peak},
+                "hbm_view": hbm_view,
                 "share_of_solve": ms_st / ms_total if ms_total else None,
-                "launches": n_st, "avg_launch_ms": avg_launch_ms,
-                "variant": infos[-1]["stencil_variant"]}
+                "launches": n_st, "avg_launch_ms": avg_launch_ms, "variant": variant}
     else:
         achieved = alg_bytes / (avg_launch_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",

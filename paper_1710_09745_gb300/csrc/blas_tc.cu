@@ -37,6 +37,7 @@
 #include <type_traits>
 
 #include "internal.h"
+#include "ozaki.cuh"
 
 namespace bcg {
 
@@ -631,9 +632,155 @@ static cudaError_t launch_gram_tc(const void* X, const void* Y, int Vh, double2*
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// K = X^dag Y for the double-float kind (N = 16) on the tensor cores, as exact
+// split products (ozaki.cuh): per CTA tile of TGD = 64 rows, every column of X
+// and of Y gets a power-of-two scale from its largest entry in the tile
+// (shared-memory maxima), each scaled value is split into six bf16 slices,
+// and slice s of a tile is stored like the 16-bit tiles above ([row][RW]
+// words of (re, im) pairs).  A warp's Gram block accumulates the products of
+// slices s, t with s + t = u in D_u: over the tile's 64 rows the terms share
+// the grid 2^(ei + ej - 14 - 8u) and stay below 2^24 units (at most
+// 64 x 7 x 2^14), so the FP32 sums are exact; after the tile D_0 .. D_5 are
+// added in double-float, the scales removed and the result added to the
+// warp's double-float accumulators.  Hermitian: only blocks holding an entry
+// i <= j; X == Y (a Gram of one block) stages one set of slices.
+constexpr int TGD = 64;  // rows per CTA tile
+
+template <int N, bool SAME>
+__global__ void __launch_bounds__(TC_WARPS * 32, SAME ? 3 : 2)
+    k_gram_tc_df(const float4* __restrict__ X, const float4* __restrict__ Y, int Vh,
+                 double2* __restrict__ partials, Gate gate) {
+  using GB = GramBlocks<N, true>;
+  constexpr int RW = N + 4;
+  constexpr int NSL = 6;
+  constexpr int PER = TGD * N / (TC_WARPS * 32);  // entries of a tile per thread
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint32_t* sX = reinterpret_cast<uint32_t*>(smem_raw);  // [NSL][TGD][RW]
+  uint32_t* sY = SAME ? sX : sX + NSL * TGD * RW;
+  __shared__ unsigned sMx[N], sMy[N];
+  __shared__ int sEx[N], sEy[N];
+  if (gate_closed(gate)) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long nrows = 3LL * Vh;
+  dfacc gacc[GB::PER_WARP][4];
+#pragma unroll
+  for (int b = 0; b < GB::PER_WARP; ++b)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) gacc[b][e] = CompDF::zero();
+  for (long long tile = blockIdx.x; tile * TGD < nrows; tile += gridDim.x) {
+    if (threadIdx.x < N) sMx[threadIdx.x] = sMy[threadIdx.x] = 0u;
+    __syncthreads();  // also: the previous tile's slices have been read
+    float4 xv[PER], yv[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int idx = threadIdx.x + k * TC_WARPS * 32;  // column idx % N (N divides 256)
+      const long long r = tile * TGD + idx / N;
+      const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+      xv[k] = r < nrows ? X[r * N + idx % N] : z;
+      yv[k] = SAME ? xv[k] : (r < nrows ? Y[r * N + idx % N] : z);
+    }
+    {
+      float mx = 0.f, my = 0.f;
+#pragma unroll
+      for (int k = 0; k < PER; ++k) {
+        mx = fmaxf(mx, fmaxf(fabsf(xv[k].x), fabsf(xv[k].y)));
+        my = fmaxf(my, fmaxf(fabsf(yv[k].x), fabsf(yv[k].y)));
+      }
+      atomicMax(&sMx[threadIdx.x % N], __float_as_uint(mx));
+      if (!SAME) atomicMax(&sMy[threadIdx.x % N], __float_as_uint(my));
+    }
+    __syncthreads();
+    if (threadIdx.x < N) {
+      sEx[threadIdx.x] = ozaki::pow2_above(sMx[threadIdx.x]);
+      sEy[threadIdx.x] = SAME ? sEx[threadIdx.x] : ozaki::pow2_above(sMy[threadIdx.x]);
+    }
+    __syncthreads();
+    {
+      const int c = threadIdx.x % N;
+      const float scx = ozaki::exp2i(-sEx[c]), scy = ozaki::exp2i(-sEy[c]);
+#pragma unroll
+      for (int k = 0; k < PER; ++k) {
+        const int row = (threadIdx.x + k * TC_WARPS * 32) / N;
+        float sr[NSL], si[NSL];
+        ozaki::split6(__fmul_rn(xv[k].x, scx), __fmul_rn(xv[k].z, scx), sr);
+        ozaki::split6(__fmul_rn(xv[k].y, scx), __fmul_rn(xv[k].w, scx), si);
+#pragma unroll
+        for (int sl = 0; sl < NSL; ++sl)
+          sX[(sl * TGD + row) * RW + c] = ozaki::pack_bf16(sr[sl], si[sl]);
+        if (!SAME) {
+          ozaki::split6(__fmul_rn(yv[k].x, scy), __fmul_rn(yv[k].z, scy), sr);
+          ozaki::split6(__fmul_rn(yv[k].y, scy), __fmul_rn(yv[k].w, scy), si);
+#pragma unroll
+          for (int sl = 0; sl < NSL; ++sl)
+            sY[(sl * TGD + row) * RW + c] = ozaki::pack_bf16(sr[sl], si[sl]);
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int bb = 0; bb < GB::PER_WARP; ++bb) {
+      const int b = warp + bb * TC_WARPS;
+      if (b >= GB::COUNT) break;  // uniform per warp
+      int mt, nt;
+      GB::at(b, mt, nt);
+      float d[6][4];
+#pragma unroll
+      for (int u = 0; u < 6; ++u)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) d[u][e] = 0.f;
+      const int q = lane >> 3, rr = lane & 7;
+#pragma unroll 1
+      for (int ks = 0; ks < TGD / 16; ++ks) {
+        // A = X^T, B = Y fragments of every slice (as in gram_tc_tile)
+        const int arow = 16 * ks + (q >> 1) * 8 + rr;
+        const int acol = 8 * mt + (q & 1) * 4;
+        const int brow = 16 * ks + (q & 1) * 8 + rr;
+        uint32_t a[NSL][4];
+#pragma unroll
+        for (int sl = 0; sl < NSL; ++sl) ldsm_x4_t(a[sl], sX + (sl * TGD + arow) * RW + acol);
+#pragma unroll
+        for (int tt = 0; tt < NSL; ++tt) {
+          uint32_t bf[2];
+          ldsm_x2_t(bf, sY + (tt * TGD + brow) * RW + 4 * nt);
+#pragma unroll
+          for (int sl = 0; sl + tt < NSL; ++sl) ozaki::mma_bf16(d[sl + tt], a[sl], bf[0], bf[1]);
+        }
+      }
+      // element e of the block: G row 16 mt + g (+ 8 for e >= 2), column
+      // 8 nt + 2 t (+ 1 for odd e); complex indices are half of those
+      const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int i = (16 * mt + g + 8 * (e >> 1)) >> 1, j = (8 * nt + 2 * t + (e & 1)) >> 1;
+        const dfacc v = ozaki::combine6(d[0][e], d[1][e], d[2][e], d[3][e], d[4][e], d[5][e]);
+        const float fa = ozaki::exp2i(sEx[i]), fb = ozaki::exp2i(sEy[j]);
+        const df w = CompDF::fin(dfacc{__fmul_rn(__fmul_rn(v.s, fa), fb),
+                                       __fmul_rn(__fmul_rn(v.e, fa), fb)});
+        CompDF::add(gacc[bb][e], w);
+      }
+    }
+  }
+  gram_tc_write<N, true>(partials + (long long)blockIdx.x * N * N, gacc, 1.0, warp, lane);
+}
+
+template <int N, bool SAME>
+static cudaError_t launch_gram_tc_df(const void* X, const void* Y, int Vh, double2* partials,
+                                     int nblocks, Gate gate, cudaStream_t s) {
+  const size_t sm = (SAME ? 1 : 2) * (size_t)6 * TGD * (N + 4) * sizeof(uint32_t);
+  auto kern = k_gram_tc_df<N, SAME>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  kern<<<nblocks, TC_WARPS * 32, sm, s>>>((const float4*)X, (const float4*)Y, Vh, partials, gate);
+  return cudaGetLastError();
+}
+
 // Hermitian Grams only (P^dag AP of the iteration)
 cudaError_t gram_partials_tc(FieldKind k, const void* X, const void* Y, int N, int Vh,
                              double2* partials, int nblocks, Gate gate, cudaStream_t s) {
+  if (k == FK_DF && N == 16)
+    return X == Y ? launch_gram_tc_df<16, true>(X, Y, Vh, partials, nblocks, gate, s)
+                  : launch_gram_tc_df<16, false>(X, Y, Vh, partials, nblocks, gate, s);
   if (k == FK_H16) {
     if (N == 16) return launch_gram_tc<StoreH16, 16>(X, Y, Vh, partials, nblocks, gate, s);
     if (N == 32) return launch_gram_tc<StoreH16, 32>(X, Y, Vh, partials, nblocks, gate, s);
@@ -645,11 +792,18 @@ cudaError_t gram_partials_tc(FieldKind k, const void* X, const void* Y, int N, i
 }
 
 bool w_gram_tc_supported(FieldKind k, int N) {
+  if (k == FK_DF) return N == 16;
   return (k == FK_H16 || k == FK_BF16) && (N == 16 || N == 32);
 }
 
 cudaError_t w_update_gram_tc(FieldKind k, void* Q, const void* AP, const double2* beta, int N,
                              int Vh, double2* partials, int nblocks, Gate gate, cudaStream_t s) {
+  if (k == FK_DF && N == 16) {
+    // double-float: W = Q - AP beta, then the Gram of the stored W (two passes)
+    cudaError_t e = w_update_tc_df(Q, AP, beta, N, Vh, gate, s);
+    if (e != cudaSuccess) return e;
+    return launch_gram_tc_df<16, true>(Q, Q, Vh, partials, nblocks, gate, s);
+  }
   if (k == FK_H16) {
     if (N == 16) return launch_w_gram_tc<StoreH16, 16>(Q, AP, beta, Vh, partials, nblocks, gate, s);
     if (N == 32) return launch_w_gram_tc<StoreH16, 32>(Q, AP, beta, Vh, partials, nblocks, gate, s);

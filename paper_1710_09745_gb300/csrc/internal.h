@@ -147,6 +147,9 @@ cudaError_t bcg_update(FieldKind sk, FieldKind xk, void* Q, void* P, void* X, co
 bool bcg_update_tc_df_supported(int N);
 cudaError_t bcg_update_tc_df(void* Q, void* P, void* X, const double2* Sinv, const double2* BC,
                              const double2* SH, int N, int Vh, Gate gate, cudaStream_t s);
+// W = Q - AP beta over Q for the double-float kind on the tensor cores, N = 16
+cudaError_t w_update_tc_df(void* Q, const void* AP, const double2* beta, int N, int Vh, Gate gate,
+                           cudaStream_t s);
 // the tensor-core fused update (blas_tc.cu): supported (kind, N) pairs
 bool bcg_update_tc_supported(FieldKind sk, FieldKind xk, int N);
 cudaError_t bcg_update_tc(FieldKind sk, void* Q, void* P, void* X, const double2* Sinv,

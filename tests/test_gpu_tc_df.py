@@ -146,14 +146,16 @@ def _oracle_rel_res(dims, fat, lng, mass, b, X):
 
 @pytest.mark.parametrize("dims", [(8, 8, 8, 8), (6, 6, 6, 6)])
 @pytest.mark.parametrize("stencil", [ASYNC + 2, TC + 1])
-def test_tc_update_df_converges(tmp_path, dims, stencil):
-    """The tensor-core double-float fused update (Q = W S^-1, P = Q + P S^dag,
-    X += P beta C as exact split bf16 products; bit 24 of the cached BLAS
-    choice) forced through the tuning cache, with the CUDA-core and the
-    tensor-core stencil: 6^4 has 3 V_h = 1944 rows, a ragged last 16-row
-    tile.  Each solve to 1e-12 meets tol on the oracle's residual, matches
-    the oracle's solution, and takes about as many iterations as the
-    CUDA-core update."""
+def test_tc_blas_df_converges(tmp_path, dims, stencil):
+    """The tensor-core double-float block BLAS as exact split bf16 products:
+    the fused update (Q = W S^-1, P = Q + P S^dag, X += P beta C; bit 24 of
+    the cached BLAS choice), W = Q - AP beta with the Gram W^dag W (bit 25)
+    and the Gram P^dag AP (bit 26), each alone and all together, forced
+    through the tuning cache, with the CUDA-core and the tensor-core stencil.
+    6^4 has 3 V_h = 1944 rows: a ragged last 16-row tile and a ragged 64-row
+    Gram tile (24 rows).  Each solve to 1e-12 meets tol on the oracle's
+    residual, the all-tensor-core solve matches the oracle's solution, and
+    every variant takes about as many iterations as the CUDA-core kernels."""
     import json
     torch = gh.torch_mod()
     mass, N = 0.05, 16
@@ -161,7 +163,8 @@ def test_tc_update_df_converges(tmp_path, dims, stencil):
     tag = ".".join(str(d) for d in dims)
     b = hi.gaussian_sources(dims, N, seed=2031)
     iters = {}
-    for name, flags in (("pipes", 0), ("upd", 1 << 24)):
+    for name, flags in (("pipes", 0), ("upd", 1 << 24), ("wgram", 1 << 25), ("gram", 1 << 26),
+                        ("all", (1 << 24) | (1 << 25) | (1 << 26))):
         cache = tmp_path / f"tiles_{name}.json"
         packed = 8 | (16 << 8) | (32 << 16) | flags
         cache.write_text(json.dumps({f"blas/{tag}/kind0/N{N}/{dev}": packed}))
@@ -173,9 +176,10 @@ def test_tc_update_df_converges(tmp_path, dims, stencil):
         X = gh.to_np(X)
         assert _oracle_rel_res(dims, fat, lng, mass, b, X).max() <= 1.01e-12, name
         iters[name] = info["iters"]
-        if name == "upd":
+        if name == "all":
             xo = hisq.cg(dims, fat, lng, mass, b[:2], tol=1e-13, max_iter=20000)[0]
             err = np.linalg.norm((X[:2] - xo).reshape(2, -1), axis=1) / \
                 np.linalg.norm(xo.reshape(2, -1), axis=1)
             assert err.max() < 1e-8, err
-    assert abs(iters["upd"] - iters["pipes"]) <= max(3, iters["pipes"] // 20), iters
+    for name in ("upd", "wgram", "gram", "all"):
+        assert abs(iters[name] - iters["pipes"]) <= max(3, iters["pipes"] // 20), iters
