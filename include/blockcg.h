@@ -121,11 +121,13 @@ typedef struct {
                           kernel, 512 for the per-thread cp.async prefetch
                           kernel, 4096 for the plain kernel on a persistent
                           grid of contiguous site ranges, 8192 for the
-                          tensor-core stencil of the F64 form (double-float
-                          values split into bf16 slices with exact products
-                          on mma.sync, N = 16 or 32 with a workspace set; the
-                          cp.async kernel otherwise).  Other values:
-                          BLOCKCG_ERR_ARG */
+                          tensor-core stencil (mma.sync): in the F64 form
+                          double-float values split into bf16 slices with
+                          exact products (N = 16 or 32 with a workspace set;
+                          the cp.async kernel otherwise), in the FP16 and
+                          bfloat16 forms the stored values themselves (N = 16
+                          or 32 with full links; the plain kernel
+                          otherwise).  Other values: BLOCKCG_ERR_ARG */
   int link_recon;      /* iteration links of the 32- and 16-bit forms: 0 = all 18
                           reals per link (default); 12 = the first two rows only,
                           the third rebuilt in the stencil as conj(row0 x row1)

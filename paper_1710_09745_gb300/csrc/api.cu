@@ -379,8 +379,12 @@ int stencil_R(blockcg_ctx* h, FieldKind k, int N, const void* links, const void*
                          1 | DSLASH_TC};
   for (int R : cands) {
     if ((R & 0xff) > 1 && (R & 0xff) > N) continue;
-    // the tensor-core stencil: double-float with N = 16 or 32 only
-    if ((R & DSLASH_TC) && (k != FK_DF || rf || !dslash_tc_supported(h->g, N))) continue;
+    // the tensor-core stencil: double-float, FP16 and bfloat16 with N = 16 or
+    // 32 and full links only
+    if ((R & DSLASH_TC) &&
+        (rf || !((k == FK_DF && dslash_tc_supported(h->g, N)) ||
+                 ((k == FK_H16 || k == FK_BF16) && dslash_tc16_supported(N)))))
+      continue;
     if (rf) {  // two-row links: the plain kernel only
       if (R & (DSLASH_TMA | DSLASH_ASYNC)) continue;
       R |= rf;

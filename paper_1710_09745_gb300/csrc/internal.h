@@ -86,10 +86,16 @@ static constexpr int DSLASH_RECON = 0x400;
 // R | DSLASH_BLOCKED: the plain kernel on a persistent grid whose blocks each
 // walk one contiguous range of sites (cache reuse of neighbours in L1)
 static constexpr int DSLASH_BLOCKED = 0x1000;
-// R | DSLASH_TC: the tensor-core double-float stencil (stencil_tc.cu; N = 16
-// or 32 with a workspace set, the cp.async kernel otherwise)
+// R | DSLASH_TC: the tensor-core stencil: double-float as split products
+// (stencil_tc.cu; N = 16 or 32 with a workspace set, the cp.async kernel
+// otherwise), FP16 / bfloat16 on the stored values (stencil_tc16.cu; N = 16
+// or 32 with full links, the plain kernel otherwise)
 static constexpr int DSLASH_TC = 0x2000;
 bool dslash_tc_supported(const Geom& g, int N);
+bool dslash_tc16_supported(int N);
+cudaError_t dslash_tc16(FieldKind k, int epi, const void* links, const void* in, void* out,
+                        const void* c1, const void* c2, double m2, const Geom& g, int out_parity,
+                        int N, Gate gate, cudaStream_t s);
 cudaError_t dslash_df_tc(int epi, const void* links, const void* in, void* out, const void* c1,
                          const void* c2, double m2, const Geom& g, int out_parity, int N,
                          Gate gate, cudaStream_t s);

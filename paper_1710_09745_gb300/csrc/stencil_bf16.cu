@@ -5,6 +5,11 @@
 namespace bcg {
 
 BCG_DSLASH_KIND_DECL(dslash_bf16) {
+  if (R & DSLASH_TC) {
+    if (dslash_tc16_supported(N) && !(R & DSLASH_RECON))
+      return dslash_tc16(FK_BF16, epi, links, in, out, c1, c2, m2, g, out_parity, N, gate, s);
+    R &= ~DSLASH_TC;  // other widths: the plain kernel
+  }
   return dslash_kind<StoreBF16>(R, epi, links, in, out, c1, c2, m2, g, out_parity, N, gate, s);
 }
 
