@@ -47,7 +47,7 @@ STENCIL_FLOPS = 1158      # per site per right-hand side (Sec. 6.2)
 TC_VARIANT = 8192         # blockcg_params.dslash_variant flag of the tensor-core stencil
 TC_PAIRS = 21             # bf16 slice products per double-float product (s + t <= 5)
 TC_USEFUL = 6.0 / 8.0     # output columns of the n8 MMA tile the stencil uses
-TC_TRAFFIC_32x4_N16 = 765.5e6 * 524288 / 165888  # ncu DRAM bytes at 24^4, scaled by sites
+TC_TRAFFIC_32x4_N16 = 767.6e6 * 524288 / 165888  # ncu DRAM bytes at 24^4, scaled by sites
 
 
 def parse_args():
@@ -470,7 +470,7 @@ def main():
                 "frac": achieved / peak,
                 "traffic": TC_TRAFFIC_32x4_N16 if full else None,
                 "traffic_note": "ncu DRAM read+write of one k_dslash_tc launch at 24^4 N=16 "
-                                "(765.5 MB, 1.20x its algorithmic bytes), scaled by sites to "
+                                "(767.6 MB, 1.21x its algorithmic bytes), scaled by sites to "
                                 "32^4; profiles/k_dslash_tc_df_24x4_N16.md" if full else None,
                 "kernel": "k_dslash_tc (tensor-core double-float stencil)",
                 "peak_note": "FP64-equivalent rate of the split-product scheme: measured "
