@@ -1,6 +1,8 @@
 // Tensor-core form of the fused blockCGrQ update (Algorithm 1: Q = W S^-1,
 // X += P (beta C), P = Q + P S^dag; the streaming multi-BLAS of Sec. 6.3) for
-// the double-float kind of the FP64-accurate form, N = 16.
+// the double-float kind of the FP64-accurate form, N = 16, and in its W mode
+// the W update W = Q - AP beta of Algorithm 1 (its Gram W^dag W follows in
+// k_gram_tc_df).
 //
 // On the FP32 pipes this update costs 12 instructions per double-float
 // multiply-add (24 N^2 multiply-adds per row) and is bound by instruction
