@@ -208,16 +208,20 @@ __global__ void __launch_bounds__(TC_SITES * 32, 2)
         if (q < 5) load_chunk(q + 1, vn);
 #pragma unroll
         for (int m = 0; m < MT; ++m) {
-          // scaled hi and lo of the 8 reals (re, im of the 4 values); rows gq
-          // (i even) and gq + 8 (i odd)
-          float h[8], l[8];
+          // raw hi and lo of the 8 reals (re, im of the 4 values) and their
+          // scales (rows gq for i even, gq + 8 for i odd); the scaling is
+          // folded into the first rounding and into the lo addition (fused
+          // multiply-adds by a power of two: the same roundings as scaling
+          // first)
+          float x[8], l[8], sc[8], h[8];
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
-            const float sc = ra[2 * m + (i & 1)];
-            h[2 * i] = __fmul_rn(v[m][i].x, sc);
-            l[2 * i] = __fmul_rn(v[m][i].z, sc);
-            h[2 * i + 1] = __fmul_rn(v[m][i].y, sc);
-            l[2 * i + 1] = __fmul_rn(v[m][i].w, sc);
+            const float c = ra[2 * m + (i & 1)];
+            x[2 * i] = v[m][i].x;
+            l[2 * i] = v[m][i].z;
+            x[2 * i + 1] = v[m][i].y;
+            l[2 * i + 1] = v[m][i].w;
+            sc[2 * i] = sc[2 * i + 1] = c;
           }
           // slice s of every value (the steps of split6, one slice at a
           // time), multiplied at once into D_{s+t} for t = 0 .. 5 - s
@@ -228,9 +232,16 @@ __global__ void __launch_bounds__(TC_SITES * 32, 2)
             float sl[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
-              sl[k] = rnd_grid(h[k], CS[s]);
-              if (s < 5) h[k] = __fsub_rn(h[k], sl[k]);
-              if (s == 2) h[k] = __fadd_rn(h[k], l[k]);
+              if (s == 0) {
+                sl[k] = __fsub_rn(__fmaf_rn(x[k], sc[k], CS[0]), CS[0]);
+                h[k] = __fmaf_rn(x[k], sc[k], -sl[k]);
+              } else {
+                sl[k] = rnd_grid(h[k], CS[s]);
+                if (s == 2)
+                  h[k] = __fmaf_rn(l[k], sc[k], __fsub_rn(h[k], sl[k]));
+                else if (s < 5)
+                  h[k] = __fsub_rn(h[k], sl[k]);
+              }
             }
             uint32_t a[4];
 #pragma unroll
