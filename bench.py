@@ -344,9 +344,17 @@ def autograd_leg(dev, tol=1e-10):
     e1.synchronize()
     lg = e0.elapsed_time(e1) / 10
     V = 16 ** 4
+    # blockcg_link_grad runs in native FP64: two D_oe halves (1158 N flops per
+    # site) and the outer products (2 link kinds x 4 V links x N x 9 entries x
+    # 8 multiply-adds); its roof is the FP64 rate, not HBM
+    from paper_1710_09745_gb300.binding import bench_alu
+    _, fp64_fma, _ = bench_alu(stream)
+    flops = 2 * STENCIL_FLOPS * N * (V // 2) + 2 * 2 * 4 * V * N * 9 * 8
     return {"workload": "16^4 m=0.05 N=8, L = sum phi^dag A^-1 phi, F64 form to 1e-10",
             "ms_forward_backward": fb, "ms_link_grad": lg,
             "link_grad_gbs": (2 * 2 * 6 * (V // 2) * N * 8 + 2 * 4 * V * 18 * 8) / (lg * 1e-3) / 1e9,
+            "link_grad_fp64_tflops": flops / (lg * 1e-3) / 1e12,
+            "link_grad_fp64_frac": flops / (lg * 1e-3) / (2 * fp64_fma),
             "grad_finite": bool(torch.isfinite(f.grad).all().item())}
 
 
