@@ -648,7 +648,7 @@ static cudaError_t launch_gram_tc(const void* X, const void* Y, int Vh, double2*
 constexpr int TGD = 64;  // rows per CTA tile
 
 template <int N, bool SAME>
-__global__ void __launch_bounds__(TC_WARPS * 32, SAME ? 3 : 2)
+__global__ void __launch_bounds__(TC_WARPS * 32, N == 16 ? (SAME ? 3 : 2) : 1)
     k_gram_tc_df(const float4* __restrict__ X, const float4* __restrict__ Y, int Vh,
                  double2* __restrict__ partials, Gate gate) {
   using GB = GramBlocks<N, true>;
@@ -781,6 +781,9 @@ cudaError_t gram_partials_tc(FieldKind k, const void* X, const void* Y, int N, i
   if (k == FK_DF && N == 16)
     return X == Y ? launch_gram_tc_df<16, true>(X, Y, Vh, partials, nblocks, gate, s)
                   : launch_gram_tc_df<16, false>(X, Y, Vh, partials, nblocks, gate, s);
+  if (k == FK_DF && N == 32)
+    return X == Y ? launch_gram_tc_df<32, true>(X, Y, Vh, partials, nblocks, gate, s)
+                  : launch_gram_tc_df<32, false>(X, Y, Vh, partials, nblocks, gate, s);
   if (k == FK_H16) {
     if (N == 16) return launch_gram_tc<StoreH16, 16>(X, Y, Vh, partials, nblocks, gate, s);
     if (N == 32) return launch_gram_tc<StoreH16, 32>(X, Y, Vh, partials, nblocks, gate, s);
@@ -792,17 +795,17 @@ cudaError_t gram_partials_tc(FieldKind k, const void* X, const void* Y, int N, i
 }
 
 bool w_gram_tc_supported(FieldKind k, int N) {
-  if (k == FK_DF) return N == 16;
-  return (k == FK_H16 || k == FK_BF16) && (N == 16 || N == 32);
+  return (k == FK_DF || k == FK_H16 || k == FK_BF16) && (N == 16 || N == 32);
 }
 
 cudaError_t w_update_gram_tc(FieldKind k, void* Q, const void* AP, const double2* beta, int N,
                              int Vh, double2* partials, int nblocks, Gate gate, cudaStream_t s) {
-  if (k == FK_DF && N == 16) {
+  if (k == FK_DF && (N == 16 || N == 32)) {
     // double-float: W = Q - AP beta, then the Gram of the stored W (two passes)
     cudaError_t e = w_update_tc_df(Q, AP, beta, N, Vh, gate, s);
     if (e != cudaSuccess) return e;
-    return launch_gram_tc_df<16, true>(Q, Q, Vh, partials, nblocks, gate, s);
+    return N == 16 ? launch_gram_tc_df<16, true>(Q, Q, Vh, partials, nblocks, gate, s)
+                   : launch_gram_tc_df<32, true>(Q, Q, Vh, partials, nblocks, gate, s);
   }
   if (k == FK_H16) {
     if (N == 16) return launch_w_gram_tc<StoreH16, 16>(Q, AP, beta, Vh, partials, nblocks, gate, s);

@@ -72,7 +72,7 @@ struct TcdGeom {
 // WMODE: the W update of Algorithm 1 instead, W = Q - AP beta over Q (AP
 // passed as P, beta as Sinv; one full coefficient matrix, phase 1 only)
 template <int N, bool WMODE>
-__global__ void __launch_bounds__(TCD_WARPS * 32, WMODE ? 3 : 2)
+__global__ void __launch_bounds__(TCD_WARPS * 32, N == 16 ? (WMODE ? 3 : 2) : 1)
     k_bcg_update_tc_df(float4* __restrict__ Q, float4* __restrict__ P, float4* __restrict__ X,
                        const double2* __restrict__ Sinv, const double2* __restrict__ BC,
                        const double2* __restrict__ SH, int Vh, Gate gate) {
@@ -323,12 +323,12 @@ __global__ void __launch_bounds__(TCD_WARPS * 32, WMODE ? 3 : 2)
 
 bool bcg_update_tc_df_supported(int N) { return N == 16; }
 
-template <bool WMODE>
+template <int N, bool WMODE>
 static cudaError_t launch_update_tc_df(void* Q, void* P, void* X, const double2* Sinv,
                                        const double2* BC, const double2* SH, int Vh, Gate gate,
                                        cudaStream_t s) {
-  using G = TcdGeom<16, WMODE ? 1 : 3>;
-  auto kern = k_bcg_update_tc_df<16, WMODE>;
+  using G = TcdGeom<N, WMODE ? 1 : 3>;
+  auto kern = k_bcg_update_tc_df<N, WMODE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)G::smem);
   if (e != cudaSuccess) return e;
@@ -356,14 +356,18 @@ static cudaError_t launch_update_tc_df(void* Q, void* P, void* X, const double2*
 cudaError_t bcg_update_tc_df(void* Q, void* P, void* X, const double2* Sinv, const double2* BC,
                              const double2* SH, int N, int Vh, Gate gate, cudaStream_t s) {
   if (N != 16) return cudaErrorInvalidValue;
-  return launch_update_tc_df<false>(Q, P, X, Sinv, BC, SH, Vh, gate, s);
+  return launch_update_tc_df<16, false>(Q, P, X, Sinv, BC, SH, Vh, gate, s);
 }
 
+// N = 32 too: one coefficient matrix (48 KB of fragments) and the A slices of
+// 8 warps (96 KB) fit one CTA per SM; the three matrices of the fused update
+// at N = 32 would not
 cudaError_t w_update_tc_df(void* Q, const void* AP, const double2* beta, int N, int Vh, Gate gate,
                            cudaStream_t s) {
-  if (N != 16) return cudaErrorInvalidValue;
-  return launch_update_tc_df<true>(Q, const_cast<void*>(AP), nullptr, beta, nullptr, nullptr, Vh,
-                                   gate, s);
+  void* A = const_cast<void*>(AP);
+  if (N == 16) return launch_update_tc_df<16, true>(Q, A, nullptr, beta, nullptr, nullptr, Vh, gate, s);
+  if (N == 32) return launch_update_tc_df<32, true>(Q, A, nullptr, beta, nullptr, nullptr, Vh, gate, s);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace bcg

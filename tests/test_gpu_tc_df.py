@@ -183,3 +183,38 @@ def test_tc_blas_df_converges(tmp_path, dims, stencil):
             assert err.max() < 1e-8, err
     for name in ("upd", "wgram", "gram", "all"):
         assert abs(iters[name] - iters["pipes"]) <= max(3, iters["pipes"] // 20), iters
+
+
+def test_tc_blas_df_width_32(tmp_path):
+    """N = 32: the tensor-core W = Q - AP beta with W^dag W (bit 25) and
+    P^dag AP (bit 26), alone and together (the fused update stays on the
+    CUDA cores at this width; bit 24 falls back to it), with the tensor-core
+    stencil: each solve to 1e-12 meets tol on the oracle's residual in about
+    as many iterations as the CUDA-core kernels, and the all-tensor-core
+    solve matches the oracle's solution."""
+    import json
+    torch = gh.torch_mod()
+    dims, mass, N = (8, 8, 8, 8), 0.05, 32
+    dev = torch.cuda.get_device_name(0).replace(" ", "_").replace('"', "_").replace("\\", "_")
+    b = hi.gaussian_sources(dims, N, seed=2032)
+    iters = {}
+    for name, flags in (("pipes", 0), ("wgram", 1 << 25), ("gram", 1 << 26),
+                        ("all", (1 << 24) | (1 << 25) | (1 << 26))):
+        cache = tmp_path / f"tiles32_{name}.json"
+        packed = 8 | (8 << 8) | (16 << 16) | flags
+        cache.write_text(json.dumps({f"blas/8.8.8.8/kind0/N{N}/{dev}": packed}))
+        s, fat, lng = gh.make_solver(dims, mass, prec="f64", seed=1032, max_rhs=N,
+                                     dslash_variant=TC + 1)
+        s.set_tune_cache(cache)
+        X, info = s.solve(b, tol=1e-12)
+        assert info["status"] == 0, name
+        X = gh.to_np(X)
+        assert _oracle_rel_res(dims, fat, lng, mass, b, X).max() <= 1.01e-12, name
+        iters[name] = info["iters"]
+        if name == "all":
+            xo = hisq.cg(dims, fat, lng, mass, b[:2], tol=1e-13, max_iter=20000)[0]
+            err = np.linalg.norm((X[:2] - xo).reshape(2, -1), axis=1) / \
+                np.linalg.norm(xo.reshape(2, -1), axis=1)
+            assert err.max() < 1e-8, err
+    for name in ("wgram", "gram", "all"):
+        assert abs(iters[name] - iters["pipes"]) <= max(3, iters["pipes"] // 20), iters
