@@ -365,8 +365,10 @@ cudaError_t bcg_update_tc_df(void* Q, void* P, void* X, const double2* Sinv, con
 cudaError_t w_update_tc_df(void* Q, const void* AP, const double2* beta, int N, int Vh, Gate gate,
                            cudaStream_t s) {
   void* A = const_cast<void*>(AP);
-  if (N == 16) return launch_update_tc_df<16, true>(Q, A, nullptr, beta, nullptr, nullptr, Vh, gate, s);
-  if (N == 32) return launch_update_tc_df<32, true>(Q, A, nullptr, beta, nullptr, nullptr, Vh, gate, s);
+  if (N == 16)
+    return launch_update_tc_df<16, true>(Q, A, nullptr, beta, nullptr, nullptr, Vh, gate, s);
+  if (N == 32)
+    return launch_update_tc_df<32, true>(Q, A, nullptr, beta, nullptr, nullptr, Vh, gate, s);
   return cudaErrorInvalidValue;
 }
 

@@ -173,11 +173,12 @@ cudaError_t dslash_tc16(FieldKind k, int epi, const void* links, const void* in,
                         const void* c1, const void* c2, double m2, const Geom& g, int out_parity,
                         int N, Gate gate, cudaStream_t s) {
   if (!dslash_tc16_supported(N) || (k != FK_H16 && k != FK_BF16)) return cudaErrorInvalidValue;
+  const int p = out_parity;
   if (k == FK_H16)
-    return N == 16 ? launch_tc16_epi<StoreH16, 1>(epi, links, in, out, c1, c2, m2, g, out_parity, gate, s)
-                   : launch_tc16_epi<StoreH16, 2>(epi, links, in, out, c1, c2, m2, g, out_parity, gate, s);
-  return N == 16 ? launch_tc16_epi<StoreBF16, 1>(epi, links, in, out, c1, c2, m2, g, out_parity, gate, s)
-                 : launch_tc16_epi<StoreBF16, 2>(epi, links, in, out, c1, c2, m2, g, out_parity, gate, s);
+    return N == 16 ? launch_tc16_epi<StoreH16, 1>(epi, links, in, out, c1, c2, m2, g, p, gate, s)
+                   : launch_tc16_epi<StoreH16, 2>(epi, links, in, out, c1, c2, m2, g, p, gate, s);
+  return N == 16 ? launch_tc16_epi<StoreBF16, 1>(epi, links, in, out, c1, c2, m2, g, p, gate, s)
+                 : launch_tc16_epi<StoreBF16, 2>(epi, links, in, out, c1, c2, m2, g, p, gate, s);
 }
 
 }  // namespace bcg
